@@ -1,0 +1,137 @@
+"""GPU parity of kpm_moments / kpm_dos against the FP64 oracle.
+
+Tolerances: FP64 moments <= 1e-12 absolute, FP32 moments <= 2e-4 absolute,
+Jackson DOS <= 1e-3 relative L1 (sum|rho_gpu - rho_oracle| / sum|rho_oracle|).
+The Hamiltonians here come from the oracle (packed into SELL-32 by the test)
+so that this file isolates the KPM kernels."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bounds as obo
+from oracle import dos as ods
+from oracle import hamiltonian as oha
+from oracle import kpm as okpm
+from oracle import neighbors as onb
+from oracle import teacher as ote
+from paper_2509_06525_gb300 import synth
+from tests.sell_helpers import sell_matrix
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-12
+TOL_F32 = 2e-4
+TOL_DOS = 1e-3
+
+
+def _teacher_csr(s, params):
+    indptr, idx, d = onb.neighbors(s.positions, s.box, s.pbc, params.rcut)
+    t, eps, _ = ote.teacher_elements(s.species, indptr, idx, d, params)
+    return indptr, idx, t, eps
+
+
+@pytest.fixture(scope="module")
+def gputb():
+    from paper_2509_06525_gb300 import build, gputb as g
+    build.build()
+    assert torch.cuda.is_available()
+    return g
+
+
+@pytest.fixture(scope="module")
+def cfg800():
+    w = synth.WORKLOADS["graphene-800-fp64"]
+    s = synth.graphene_primitive(w["n1"], w["n2"], w["sigma"], w["seed"])
+    indptr, idx, t, eps = _teacher_csr(s, synth.teacher_graphene())
+    H = oha.csr_hamiltonian(s.n, indptr, idx, t, eps)
+    emin, emax, a, b = obo.spectral_bounds(H, 64, synth.LANCZOS_SEED)
+    return s, indptr, idx, t, eps, H, a, b, w
+
+
+def test_fp64_moments_match_oracle(gputb, cfg800):
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    M, R = w["M"], w["R"]
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+    # bitwise reproducible
+    mu2 = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    assert np.array_equal(mu, mu2)
+
+
+def test_fp32_moments_match_oracle(gputb, cfg800):
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    M, R = w["M"], w["R"]
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float32)
+    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F32
+
+
+def test_dos_matches_oracle(gputb, cfg800):
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    M, R = w["M"], w["R"]
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED)
+    emin, emax = b - a, b + a
+    E = np.linspace(emin, emax, w["K"])
+    rho = gputb.kpm_dos(mu, a, b, torch.tensor(E, device="cuda")).cpu().numpy()
+    mu_ref, _ = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
+    rho_ref = ods.density_of_states(mu_ref, a, b, E)
+    assert np.sum(np.abs(rho - rho_ref)) / np.sum(np.abs(rho_ref)) <= TOL_DOS
+    # same moments into both DOS routines: agreement to rounding
+    rho_same = ods.density_of_states(mu.mean(0).cpu().numpy(), a, b, E)
+    np.testing.assert_allclose(rho, rho_same, rtol=1e-10, atol=1e-12)
+    for kernel, kind in (("lorentz", ods.LORENTZ), ("none", ods.NONE)):
+        r = gputb.kpm_dos(mu, a, b, torch.tensor(E, device="cuda"), kernel=kernel, lam=4.0).cpu().numpy()
+        np.testing.assert_allclose(r, ods.density_of_states(mu.mean(0).cpu().numpy(), a, b, E, kind, 4.0),
+                                   rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_all_block_widths_ragged_rows(gputb, R, dtype):
+    """Ragged N (not a multiple of 32), an h-BN junction with onsite terms
+    (diag present), every supported R."""
+    s = synth.hbn_graphene_junction(6, 7, sigma=0.1, seed=9)   # 168 atoms
+    s.positions = s.positions[:-5].copy()                          # ragged, still periodic-valid
+    s.species = s.species[:-5].copy()
+    p = synth.teacher_hbn_graphene()
+    indptr, idx, t, eps = _teacher_csr(s, p)
+    H = oha.csr_hamiltonian(s.n, indptr, idx, t, eps)
+    _, _, a, b = obo.spectral_bounds(H, 64, 7)
+    M = 96
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, dtype)
+    mu = gputb.kpm_moments(Hd, a, b, M, R, 1234).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, M, R, 1234)
+    tol = TOL_F64 if dtype == torch.float64 else TOL_F32
+    assert np.max(np.abs(mu - mu_ref)) <= tol
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33])
+def test_tiny_systems(gputb, n):
+    rng = np.random.default_rng(n)
+    dense = np.zeros((n, n))
+    if n > 1:
+        for i in range(n):
+            j = (i + 1) % n
+            if j != i:
+                dense[i, j] = dense[j, i] = rng.uniform(-1, 1)
+    onsite = rng.uniform(-0.5, 0.5, n)
+    import scipy.sparse as sp
+    off = sp.csr_matrix(dense)
+    H = oha.csr_hamiltonian(n, off.indptr, off.indices, off.data, onsite)
+    a, b = 3.0, 0.1
+    Hd = sell_matrix(off.indptr, off.indices, off.data, onsite, n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, 40, 2, 5).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, 40, 2, 5)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+
+
+def test_bounds_violation_reported(gputb, cfg800):
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
+    with pytest.raises(gputb.GputbError) as ei:
+        gputb.kpm_moments(Hd, 0.3 * a, b, 256, 1, 1)
+    assert ei.value.status in (gputb.TB_ERR_BOUNDS, gputb.TB_ERR_NOT_FINITE)
