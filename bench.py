@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPUTB hot path on GB300: KPM atom*moments/s.
+
+One step = one pass of the whole path over one synthetic structure:
+cell-list neighbours -> Hamiltonian (learned MLP or analytic teacher) in
+SELL-32 -> FP64 spectral bounds -> FP32 KPM moments (R random-phase vectors,
+M moments) -> Jackson DOS.  value = N_atoms * M / (time per step), summed
+over ranks.  Inputs are resident in HBM when the timed region starts; the
+`e2e` figure repeats the step from pinned host buffers with the host<->device
+copies inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+this path) on a bounded sample of the same workload.
+
+Launch: python bench.py [--gpus 1 --steps 3 --warmup 3]; for N > 1 under
+torch.distributed.run, one rank per GPU, each rank runs its own replica of
+the step with its own random-phase seed (the R vectors are independent, so
+they shard across ranks with no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2509_06525_gb300 import synth  # noqa: E402
+
+METRIC = "KPM atom*moments/s on 1 GB300 (learned FP32 vs plain FP64), % HBM roofline"
+UNIT = "atom*moments/s"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="graphene-10M-learned", choices=list(synth.WORKLOADS))
+    p.add_argument("--hamiltonian", choices=["mlp", "teacher"], default="teacher")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 teacher comparison run")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- structure
+
+def make_structure(name):
+    w = synth.WORKLOADS[name]
+    if w["kind"] == "rect":
+        return synth.graphene_rect(w["nx"], w["ny"], w["sigma"], w["seed"]), w
+    if w["kind"] == "prim":
+        return synth.graphene_primitive(w["n1"], w["n2"], w["sigma"], w["seed"]), w
+    raise SystemExit(f"workload {name} is not a single-structure workload")
+
+
+def teacher_for(s):
+    return synth.teacher_hbn_graphene() if np.any(s.species != 0) else synth.teacher_graphene()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1].split()[0]))
+                mx.append(float(row[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+
+class Pipeline:
+    """Holds the device-resident inputs and runs one step through the binding."""
+
+    def __init__(self, s, w, hamiltonian, rank, torch, g):
+        self.torch, self.g = torch, g
+        self.s, self.w = s, w
+        self.M, self.R = w["M"], w["R"]
+        self.seed = synth.KPM_SEED + 1000003 * rank
+        self.teacher = teacher_for(s)
+        self.hamiltonian = hamiltonian
+        self.with_diag = bool(np.any(self.teacher.onsite[np.unique(s.species)] != 0.0))
+        self.pos = torch.tensor(s.positions, device="cuda")
+        self.spc = torch.tensor(s.species, device="cuda")
+        self.pos_host = torch.tensor(s.positions).pin_memory()
+        self.spc_host = torch.tensor(s.species).pin_memory()
+        self.kpm_ms = []
+        self.last = {}
+
+    def step(self, pos, spc, dtype, record=True):
+        g, torch = self.g, self.torch
+        nb = g.build_neighbors(pos, self.s.box, self.s.pbc, self.teacher.rcut, r_count=self.teacher.r_count,
+                               max_width=16)
+        H = g.build_hamiltonian_teacher(pos, spc, self.s.box, self.s.pbc, nb, self.teacher, dtype=dtype,
+                                        with_diag=self.with_diag)
+        bd = g.spectral_bounds(H, 64, synth.LANCZOS_SEED)
+        timing = self.kpm_ms if record else None
+        mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing)
+        E = torch.linspace(bd.emin, bd.emax, self.w["K"], dtype=torch.float64, device="cuda")
+        rho = g.kpm_dos(mu, bd.a, bd.b, E)
+        self.last = dict(nb=nb, H=H, bd=bd, mu=mu, rho=rho)
+        return mu, rho
+
+    def step_e2e(self, dtype):
+        pos = self.pos_host.to("cuda", non_blocking=True)
+        spc = self.spc_host.to("cuda", non_blocking=True)
+        mu, rho = self.step(pos, spc, dtype, record=False)
+        return mu.cpu(), rho.cpu()
+
+
+def timed(torch, dist, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def cpu_baseline(workload, budget_s=15.0):
+    """The FP64 oracle's KPM on a bounded sample of the same workload."""
+    from oracle import hamiltonian as oha, kpm as okpm, neighbors as onb, teacher as ote
+    w = synth.WORKLOADS[workload]
+    nx = min(w.get("nx", 250), 250)
+    ny = min(w.get("ny", 200), 200)
+    s = synth.graphene_rect(nx, ny, w["sigma"], w["seed"])
+    p = teacher_for(s)
+    indptr, idx, d = onb.neighbors(s.positions, s.box, s.pbc, p.rcut)
+    t, eps, _ = ote.teacher_elements(s.species, indptr, idx, d, p)
+    H = oha.csr_hamiltonian(s.n, indptr, idx, t, eps)
+    Ht = okpm.rescale(H, 4.6, -0.15)
+    v0 = okpm.random_phase_vectors(synth.KPM_SEED, s.n, w["R"])
+    # time Chebyshev steps until the budget is spent (the per-step cost is constant)
+    t0 = time.perf_counter()
+    m = 2
+    while True:
+        okpm.chebyshev_moments(Ht, v0, m)
+        el = time.perf_counter() - t0
+        if el > budget_s or m >= w["M"]:
+            break
+        m *= 2
+    # measure cleanly at the final m
+    t0 = time.perf_counter()
+    okpm.chebyshev_moments(Ht, v0, m)
+    el = time.perf_counter() - t0
+    value = s.n * m / el
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle KPM (SciPy CSR, single-threaded) on a {s.n}-atom sheet of the same "
+                      f"graphene workload (sigma={w['sigma']} A), R={w['R']}, {m} moments, teacher H; "
+                      f"host has {os.cpu_count()} cores"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist_mod
+    from paper_2509_06525_gb300 import build, gputb as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    build.build()
+    s, w = make_structure(args.workload)
+    pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g)
+    lib = g.lib()
+
+    # device-resident timed region
+    sampler = ClockSampler(local)
+    pipe.kpm_ms.clear()
+    for _ in range(args.warmup):
+        pipe.step(pipe.pos, pipe.spc, torch.float32, record=False)
+    torch.cuda.synchronize()
+    l0 = lib.tb_launch_count()
+    sampler.start()
+    ms = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, torch.float32), args.steps, 0)
+    clocks = sampler.stop()
+    launches = lib.tb_launch_count() - l0
+    n_atoms, M, R = s.n, w["M"], w["R"]
+    value = world * n_atoms * M / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused Chebyshev step)
+    nb, H = pipe.last["nb"], pipe.last["H"]
+    nnz = int(nb.cnt.sum().item())
+    sv, sc = 4, 8
+    step_bytes = nnz * (sv + 4) + (n_atoms * sv if H.diag is not None else 0) + n_atoms * R * 4 * sc
+    launch_ms = sum(pipe.kpm_ms) / (len(pipe.kpm_ms) * (M - 1))
+    achieved = step_bytes / (launch_ms * 1e-3) / 1e9
+    peak, peak_src = hbm_peak()
+    kpm_frac_of_step = sum(pipe.kpm_ms) / (ms * args.steps)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "atoms": n_atoms, "moments": M, "random_vectors": R,
+                   "hamiltonian": args.hamiltonian, "kpm_precision": "complex FP32, FP64 moment sums",
+                   "l2": "inputs larger than L2 (ELL and vector blocks >> 126 MB)",
+                   "step": "neighbours + H build + FP64 bounds + KPM + Jackson DOS"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "cheb_step_kernel",
+                     "bytes_per_launch": step_bytes, "launch_ms": launch_ms, "peak_source": peak_src,
+                     "kpm_share_of_step": kpm_frac_of_step},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    # plain FP64 teacher form on the same structure and GPU
+    if not args.no_fp64:
+        pipe.kpm_ms.clear()
+        ms64 = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, torch.float64, record=False),
+                     max(1, args.steps // 2), 1)
+        out["fp64_teacher"] = {"value": world * n_atoms * M / (ms64 * 1e-3), "ms_per_step": ms64,
+                               "speedup_of_value": (world * n_atoms * M / (ms * 1e-3)) /
+                                                   (world * n_atoms * M / (ms64 * 1e-3))}
+
+    if not args.no_e2e:
+        ms_e2e = timed(torch, dist, lambda: pipe.step_e2e(torch.float32), args.steps, 1)
+        h2d = s.positions.nbytes + s.species.nbytes
+        d2h = R * M * 8 + w["K"] * 8
+        out["e2e"] = {"value": world * n_atoms * M / (ms_e2e * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import hamiltonian as oha, kpm as okpm, neighbors as onb, teacher as ote
+    w = synth.WORKLOADS[args.workload]
+    nx = min(w.get("nx", 250), 250)
+    ny = min(w.get("ny", 200), 200)
+    s = synth.graphene_rect(nx, ny, w["sigma"], w["seed"])
+    p = teacher_for(s)
+    indptr, idx, d = onb.neighbors(s.positions, s.box, s.pbc, p.rcut)
+    t, eps, _ = ote.teacher_elements(s.species, indptr, idx, d, p)
+    H = oha.csr_hamiltonian(s.n, indptr, idx, t, eps)
+    Ht = okpm.rescale(H, 4.6, -0.15)
+    v0 = okpm.random_phase_vectors(synth.KPM_SEED, s.n, w["R"])
+    m = 16
+
+    def one():
+        okpm.chebyshev_moments(Ht, v0, m)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    sec = (time.perf_counter() - t0) / args.steps
+    value = s.n * m / sec
+    sample = (f"FP64 oracle KPM (SciPy CSR, single-threaded) on a {s.n}-atom sheet of the same graphene "
+              f"workload, R={w['R']}, {m} moments per step, teacher H")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "atoms": s.n, "moments": m, "random_vectors": w["R"],
+                      "hamiltonian": "teacher"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

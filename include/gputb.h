@@ -81,6 +81,9 @@ TB_API int32_t tb_abi_version(void);
 /* Message describing the last failure on the calling thread ("" if none). */
 TB_API const char *tb_last_error(void);
 
+/* Number of kernel launches this process has issued through the library. */
+TB_API int64_t tb_launch_count(void);
+
 /* ---------------------------------------------------------------------
  * KPM moments (Sec. 2.4: Chebyshev expansion, KPM, SpMV, random phases).
  *
@@ -99,12 +102,15 @@ TB_API const char *tb_last_error(void);
  *   slice_ptr    device int64 [ceil(N/32)+1]        SELL-32 slice offsets
  *   col          device int32 [slice_ptr[last]]     column indices
  *   val          device float/double (per precision) off-diagonal values H_ij
+ *                (col and val may be NULL when every slice has width 0)
  *   diag         device float/double [N] onsite H_ii, or NULL for all zero
  *   a, b         rescaling H~ = (H - b)/a; a > 0
  *   M            moments (>= 2);  R  vectors: 1, 2, 4, 8, 16 or 32
  *   seed         random-phase seed
  *   mu_r         device double [R*M] output (vector r, moment n at r*M+n)
  *   workspace    >= kpm_moments_workspace_size(n, M, R, precision) bytes
+ *   step_ms      host double or NULL: if given, receives the CUDA-event time
+ *                (ms) of the M-1 Chebyshev-step launches on `stream`
  * Synchronises `stream`, then checks |mu_r| <= 1 + 1e-6 (TB_ERR_BOUNDS)
  * and finiteness (TB_ERR_NOT_FINITE).
  * ------------------------------------------------------------------- */
@@ -114,7 +120,7 @@ TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t 
                       const void *val, const void *diag, int32_t precision,
                       double a, double b, int32_t M, int32_t R, uint64_t seed,
                       double *mu_r, void *workspace, size_t workspace_bytes,
-                      void *stream);
+                      void *stream, double *step_ms);
 
 /* ---------------------------------------------------------------------
  * KPM density of states, Eq. 4, per orbital per eV (integrates to 1):
@@ -130,6 +136,82 @@ TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t 
 TB_API tb_status kpm_dos(const double *mu_r, int32_t R, int32_t M, int32_t kernel,
                   double lambda, double a, double b, const double *energy,
                   int32_t K, double *dos, void *stream);
+
+
+/* ---------------------------------------------------------------------
+ * Neighbour lists N(i) of Eq. 1 (Sec. 3): every j != i with a periodic
+ * image closer than rcut, found with a device cell list and written as the
+ * SELL-32 column array of the Hamiltonian (row i's neighbours ascending,
+ * padding col = i).  Membership is decided in FP64 as
+ *   ((dx*dx) + (dy*dy)) + (dz*dz) < rcut*rcut
+ * with each operation rounded separately, d being the minimum-image
+ * displacement reduced along a3, then a2, then a1.  Non-periodic directions
+ * are not binned (one cell layer), which suits sheets and slabs.
+ *
+ *   positions   device double [N][3] (Angstrom)
+ *   r_count     also count n_i = #{j: r_ij < r_count} into ncount (<= 0: skip)
+ *   max_width   maximum slots per row (1..64); a row with more neighbours
+ *               returns TB_ERR_ELL_OVERFLOW
+ *   slice_ptr   device int64 [ceil(N/32)+1] output; slice width = the
+ *               largest neighbour count among its 32 rows
+ *   col         device int32 [col_capacity] output; N' = ceil(N/32)*32*max_width
+ *               elements always suffice.  If the structure needs more than
+ *               col_capacity, TB_ERR_ELL_OVERFLOW is returned, *total_out
+ *               holds the size needed and col is not written.
+ *   cnt         device int32 [N] output: neighbours per row
+ *   ncount      device int32 [N] output or NULL
+ *   total_out   host int64: number of SELL elements (slice_ptr[last])
+ * Synchronises `stream`.  Positions must be finite (TB_ERR_NOT_FINITE).
+ * ------------------------------------------------------------------- */
+TB_API size_t tb_neighbors_workspace_size(int64_t n, const double *box, const int32_t *pbc, double rcut);
+
+TB_API tb_status tb_build_neighbors(const double *positions, int64_t n, const double *box,
+                                    const int32_t *pbc, double rcut, double r_count,
+                                    int32_t max_width, int64_t *slice_ptr, int32_t *col,
+                                    int64_t col_capacity, int32_t *cnt, int32_t *ncount,
+                                    int64_t *total_out, void *workspace, size_t workspace_bytes,
+                                    void *stream);
+
+/* ---------------------------------------------------------------------
+ * Teacher Hamiltonian (analytic environment-dependent pz model, form of
+ * Eq. 1; it replaces the DFT labels of Sec. 2.3):
+ *   t_ij  = P[Z_i][Z_j] exp(-beta (r_ij/a_cc - 1)) (1 + gamma (n_i+n_j-6)/6) f_c(r_ij)
+ *   f_c(r) = (1 + cos(pi r/rcut))/2 for r < rcut, else 0;  eps_i = onsite[Z_i]
+ * evaluated in FP64 and stored in `precision` into the SELL-32 layout of
+ * (slice_ptr, col) from tb_build_neighbors (same positions and box).
+ *
+ *   species        device int32 [N], values 0..2 (else TB_ERR_INVALID_ARG)
+ *   cnt, ncount    device int32 [N] from tb_build_neighbors (r_count = 1.8 A)
+ *   hop_prefactor  host double [3][3] P (eV);  onsite  host double [3] (eV)
+ *   val            device float/double [slice_ptr[last]] output
+ *   diag           device float/double [N] output (onsite), or NULL
+ * Synchronises `stream`.
+ * ------------------------------------------------------------------- */
+TB_API tb_status tb_build_hamiltonian_teacher(const double *positions, const int32_t *species, int64_t n,
+                                              const double *box, const int32_t *pbc,
+                                              const int64_t *slice_ptr, const int32_t *col,
+                                              const int32_t *cnt, const int32_t *ncount,
+                                              const double *hop_prefactor, const double *onsite,
+                                              double a_cc, double beta, double gamma, double rcut,
+                                              int32_t precision, void *val, void *diag, void *stream);
+
+/* ---------------------------------------------------------------------
+ * FP64 spectral bounds for the Chebyshev rescaling of Sec. 2.4.
+ * Gershgorin enclosure [G_min, G_max]; `lanczos_steps` Lanczos steps (FP64,
+ * no reorthogonalisation, start q_i = u(seed, 0, i) - 1/2 normalised, u as in
+ * kpm_moments); Ritz extremes theta by Sturm multisection; then
+ *   delta = 0.01 (theta_max - theta_min),
+ *   E_max = min(G_max, theta_max + delta), E_min = max(G_min, theta_min - delta),
+ *   a = (E_max - E_min)/(2 - 0.01), b = (E_max + E_min)/2.
+ *   bounds_out  host double[8]: E_min, E_max, a, b, theta_min, theta_max, G_min, G_max
+ * Synchronises `stream`.
+ * ------------------------------------------------------------------- */
+TB_API size_t tb_spectral_bounds_workspace_size(int64_t n, int32_t lanczos_steps);
+
+TB_API tb_status tb_spectral_bounds(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                                    const void *val, const void *diag, int32_t precision,
+                                    int32_t lanczos_steps, uint64_t seed, double *bounds_out,
+                                    void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

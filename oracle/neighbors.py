@@ -144,12 +144,16 @@ def neighbors(pos, box, pbc, rcut):
 def neighbors_of_rows(pos, box, pbc, rcut, rows, chunk=1 << 22):
     """Brute force of the definition for a few sampled rows of a large system.
 
-    Returns a list of (indices sorted ascending, dvec) per requested row.
+    Orthorhombic boxes use the per-component nearest image (exact for them);
+    other boxes enumerate the lattice translations.  Returns a list of
+    (indices sorted ascending, dvec) per requested row.
     """
     pos = np.asarray(pos, np.float64)
     box = np.asarray(box, np.float64)
     check_box(box, pbc, rcut)
-    shifts = _translations(box, pbc)
+    ortho = is_orthorhombic(box)
+    lengths = np.diag(box)
+    shifts = np.zeros((1, 3)) if ortho else _translations(box, pbc)
     r2 = rcut * rcut
     out = []
     n = pos.shape[0]
@@ -157,10 +161,13 @@ def neighbors_of_rows(pos, box, pbc, rcut, rows, chunk=1 << 22):
         idx_list, d_list = [], []
         for s in range(0, n, chunk):
             block = pos[s:s + chunk] - pos[i]
-            # cheap exact prefilter: a candidate must be within r_cut of some
-            # image in every Cartesian component
+            if ortho:
+                for k in range(3):
+                    if pbc[k]:
+                        block[:, k] -= lengths[k] * np.rint(block[:, k] / lengths[k])
             for t in shifts:
                 d = block + t
+                # cheap exact prefilter: every component within r_cut
                 m = (np.abs(d[:, 0]) < rcut) & (np.abs(d[:, 1]) < rcut) & (np.abs(d[:, 2]) < rcut)
                 if not m.any():
                     continue

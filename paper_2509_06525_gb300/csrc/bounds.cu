@@ -1,0 +1,317 @@
+// FP64 spectral bounds for the Chebyshev rescaling H~ = (H - b)/a of the
+// KPM/LSQT method (arXiv 2509.06525 Sec. 2.4).
+//
+//  * Gershgorin: [min_i(eps_i - R_i), max_i(eps_i + R_i)], R_i = sum_j |H_ij|.
+//  * Lanczos: k steps of the symmetric three-term recurrence (FP64, no
+//    reorthogonalisation) from q_i = u(seed, 0, i) - 1/2, normalised, with
+//    u the SplitMix64 counter deviate of the KPM random phases.  The
+//    extreme eigenvalues of the tridiagonal T_k come from Sturm-sequence
+//    multisection: each of the 32 lanes of one warp counts eigenvalues
+//    below its own trial point, so every round narrows the bracket 32-fold.
+//  * delta = 0.01 (theta_max - theta_min); E_max = min(G_max, theta_max +
+//    delta), E_min = max(G_min, theta_min - delta); a = (E_max - E_min) /
+//    (2 - 0.01), b = (E_max + E_min) / 2.
+// Every reduction is two-level (CTA partials, then one CTA in fixed order),
+// so the result is bitwise reproducible.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gputb {
+namespace {
+
+constexpr int kB = 256;
+
+__device__ __forceinline__ uint64_t smix(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T sh[kB / 32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kB / 32; ++w) s += sh[w];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void block_minmax(double lo, double hi, double *out_lo, double *out_hi) {
+  __shared__ double sl[kB / 32], sh[kB / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sl[threadIdx.x >> 5] = lo;
+    sh[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = sl[0], b = sh[0];
+    for (int w = 1; w < kB / 32; ++w) {
+      a = fmin(a, sl[w]);
+      b = fmax(b, sh[w]);
+    }
+    *out_lo = a;
+    *out_hi = b;
+  }
+}
+
+template <typename valT>
+__global__ void gershgorin_kernel(int64_t n, const int64_t *__restrict__ sp, const int32_t *__restrict__ col,
+                                  const valT *__restrict__ val, const valT *__restrict__ diag,
+                                  double *__restrict__ part_lo, double *__restrict__ part_hi) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const int64_t sb = sp[i >> 5];
+    const int w = static_cast<int>((sp[(i >> 5) + 1] - sb) >> 5);
+    double r = 0.0;
+    for (int s = 0; s < w; ++s) r += fabs((double)val[sb + (i & 31) + 32 * s]);
+    const double d = diag ? (double)diag[i] : 0.0;
+    lo = fmin(lo, d - r);
+    hi = fmax(hi, d + r);
+  }
+  block_minmax(lo, hi, part_lo + blockIdx.x, part_hi + blockIdx.x);
+}
+
+__global__ void lanczos_start_kernel(int64_t n, uint64_t seed, double *__restrict__ q, double *__restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const uint64_t z = smix(seed ^ smix((0ull << 32) + (uint64_t)i));
+    const double v = static_cast<double>(z >> 11) * 0x1.0p-53 - 0.5;
+    q[i] = v;
+    acc = fma(v, v, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// scal[slot] = sum of partials (fixed order); mode 1: sqrt
+__global__ void reduce_scalar_kernel(const double *__restrict__ part, int nparts, double *__restrict__ scal,
+                                     int slot, int mode) {
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nparts; c += kB) acc += part[c];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) scal[slot] = mode == 1 ? sqrt(s) : s;
+}
+
+__global__ void scale_kernel(int64_t n, double *__restrict__ q, const double *__restrict__ norm) {
+  const double inv = 1.0 / norm[0];
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) q[i] *= inv;
+}
+
+// w = H q - beta_prev q_prev; part = sum q.w
+template <typename valT>
+__global__ void lanczos_spmv_kernel(int64_t n, const int64_t *__restrict__ sp, const int32_t *__restrict__ col,
+                                    const valT *__restrict__ val, const valT *__restrict__ diag,
+                                    const double *__restrict__ q, const double *__restrict__ qprev,
+                                    const double *__restrict__ beta_prev, double *__restrict__ w,
+                                    double *__restrict__ part) {
+  const double bp = beta_prev ? *beta_prev : 0.0;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const int64_t sb = sp[i >> 5];
+    const int ww = static_cast<int>((sp[(i >> 5) + 1] - sb) >> 5);
+    double y = diag ? (double)diag[i] * q[i] : 0.0;
+    for (int s = 0; s < ww; ++s) {
+      const int64_t e = sb + (i & 31) + 32 * s;
+      y = fma((double)val[e], q[col[e]], y);
+    }
+    if (qprev) y = fma(-bp, qprev[i], y);
+    w[i] = y;
+    acc = fma(q[i], y, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// w -= alpha q; part = sum w.w
+__global__ void lanczos_orth_kernel(int64_t n, const double *__restrict__ q, const double *__restrict__ alpha,
+                                    double *__restrict__ w, double *__restrict__ part) {
+  const double a = *alpha;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const double v = fma(-a, q[i], w[i]);
+    w[i] = v;
+    acc = fma(v, v, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__device__ int sturm_below(const double *alpha, const double *beta, int m, double x) {
+  int count = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    d = (alpha[i] - x) - (i > 0 ? beta[i - 1] * beta[i - 1] / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++count;
+  }
+  return count;
+}
+
+// One warp: extremes of tridiag(alpha[0..m), beta[0..m-1)) by 32-way
+// multisection, then the bounds combination.  out = {emin, emax, a, b}.
+__global__ void finish_bounds_kernel(const double *__restrict__ alpha, const double *__restrict__ beta, int m,
+                                     const double *__restrict__ g_lo_part, const double *__restrict__ g_hi_part,
+                                     int nparts, double margin, double eps, double *__restrict__ out) {
+  __shared__ double sa[1024], sb[1024];
+  const int lane = threadIdx.x;
+  for (int k = lane; k < m; k += 32) sa[k] = alpha[k];
+  for (int k = lane; k < m - 1; k += 32) sb[k] = beta[k];
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int c = lane; c < nparts; c += 32) {
+    glo = fmin(glo, g_lo_part[c]);
+    ghi = fmax(ghi, g_hi_part[c]);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+  }
+  __syncwarp();
+  // Gershgorin interval of T as the initial bracket
+  double tlo = INFINITY, thi = -INFINITY;
+  for (int k = lane; k < m; k += 32) {
+    double r = 0.0;
+    if (k > 0) r += fabs(sb[k - 1]);
+    if (k < m - 1) r += fabs(sb[k]);
+    tlo = fmin(tlo, sa[k] - r);
+    thi = fmax(thi, sa[k] + r);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    tlo = fmin(tlo, __shfl_xor_sync(0xffffffffu, tlo, off));
+    thi = fmax(thi, __shfl_xor_sync(0xffffffffu, thi, off));
+  }
+  double ext[2];
+  for (int which = 0; which < 2; ++which) {
+    // smallest eigenvalue: count(x) >= 1; largest: count(x) >= m
+    const int target = which == 0 ? 1 : m;
+    double lo = tlo, hi = thi;
+    for (int round = 0; round < 40; ++round) {
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const bool ok = sturm_below(sa, sb, m, x) >= target;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      // first lane whose point already has >= target eigenvalues below it
+      const int first = mask ? __ffs(mask) - 1 : 32;
+      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / 33.0;
+      const double nhi = first == 32 ? hi : lo + (hi - lo) * (double)(first + 1) / 33.0;
+      if (!(nhi - nlo < hi - lo)) break;
+      lo = nlo;
+      hi = nhi;
+    }
+    ext[which] = 0.5 * (lo + hi);
+  }
+  if (lane == 0) {
+    const double tmin = ext[0], tmax = ext[1];
+    const double delta = margin * (tmax - tmin);
+    const double emax = fmin(ghi, tmax + delta);
+    const double emin = fmax(glo, tmin - delta);
+    out[0] = emin;
+    out[1] = emax;
+    out[2] = (emax - emin) / (2.0 - eps);
+    out[3] = 0.5 * (emax + emin);
+    out[4] = tmin;
+    out[5] = tmax;
+    out[6] = glo;
+    out[7] = ghi;
+  }
+}
+
+int grid_for(int64_t n) {
+  const int64_t need = (n + kB - 1) / kB;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  return static_cast<int>(need < cap ? need : cap);
+}
+
+template <typename valT>
+tb_status run_bounds(int64_t n, const int64_t *sp, const int32_t *col, const valT *val, const valT *diag, int k,
+                     uint64_t seed, double *out_host, void *ws, size_t wsb, cudaStream_t st) {
+  const int grid = grid_for(n);
+  Carver cv(ws, wsb);
+  double *q0 = cv.take<double>(n), *q1 = cv.take<double>(n), *w = cv.take<double>(n);
+  double *part = cv.take<double>(grid), *glo = cv.take<double>(grid), *ghi = cv.take<double>(grid);
+  double *alpha = cv.take<double>(k), *beta = cv.take<double>(k), *norm = cv.take<double>(1);
+  double *out = cv.take<double>(8);
+  if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_spectral_bounds: workspace too small");
+  gershgorin_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, glo, ghi);
+  TB_CHECK_LAUNCH();
+  lanczos_start_kernel<<<grid, kB, 0, st>>>(n, seed, q1, part);
+  TB_CHECK_LAUNCH();
+  reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, norm, 0, 1);
+  TB_CHECK_LAUNCH();
+  scale_kernel<<<grid, kB, 0, st>>>(n, q1, norm);
+  TB_CHECK_LAUNCH();
+  double *q = q1, *qprev = q0;
+  for (int j = 0; j < k; ++j) {
+    lanczos_spmv_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, q, j > 0 ? qprev : nullptr,
+                                                   j > 0 ? beta + (j - 1) : nullptr, w, part);
+    TB_CHECK_LAUNCH();
+    reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, alpha, j, 0);
+    TB_CHECK_LAUNCH();
+    if (j == k - 1) break;
+    lanczos_orth_kernel<<<grid, kB, 0, st>>>(n, q, alpha + j, w, part);
+    TB_CHECK_LAUNCH();
+    reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, beta, j, 1);
+    TB_CHECK_LAUNCH();
+    // q_{j+1} = w / beta_j, written over q_{j-1}
+    scale_kernel<<<grid, kB, 0, st>>>(n, w, beta + j);
+    double *t = qprev;
+    qprev = q;
+    q = w;
+    w = t;
+    TB_CHECK_LAUNCH();
+  }
+  finish_bounds_kernel<<<1, 32, 0, st>>>(alpha, beta, k, glo, ghi, grid, 0.01, 0.01, out);
+  TB_CHECK_LAUNCH();
+  TB_CUDA(cudaMemcpyAsync(out_host, out, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < 4; ++c)
+    if (!std::isfinite(out_host[c])) return fail(TB_ERR_NOT_FINITE, "tb_spectral_bounds: non-finite bound");
+  if (!(out_host[2] > 0.0)) return fail(TB_ERR_NOT_FINITE, "tb_spectral_bounds: degenerate spectrum (a <= 0)");
+  return TB_OK;
+}
+
+}  // namespace
+}  // namespace gputb
+
+using namespace gputb;
+
+extern "C" size_t tb_spectral_bounds_workspace_size(int64_t n, int32_t lanczos_steps) {
+  if (n <= 0 || lanczos_steps < 1) return 0;
+  Carver cv(nullptr, 0);
+  const int grid = grid_for(n);
+  cv.take<double>(n);
+  cv.take<double>(n);
+  cv.take<double>(n);
+  cv.take<double>(grid);
+  cv.take<double>(grid);
+  cv.take<double>(grid);
+  cv.take<double>(lanczos_steps);
+  cv.take<double>(lanczos_steps);
+  cv.take<double>(1);
+  cv.take<double>(8);
+  return cv.used + 256;
+}
+
+extern "C" tb_status tb_spectral_bounds(int64_t n, const int64_t *slice_ptr, const int32_t *col, const void *val,
+                                        const void *diag, int32_t precision, int32_t lanczos_steps, uint64_t seed,
+                                        double *bounds_out, void *workspace, size_t workspace_bytes, void *stream) {
+  TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "tb_spectral_bounds: bad n");
+  TB_REQUIRE(lanczos_steps >= 2 && lanczos_steps <= 1024 && lanczos_steps <= n,
+             "tb_spectral_bounds: lanczos_steps must be in [2, min(1024, n)]");
+  TB_REQUIRE(slice_ptr && bounds_out && workspace, "tb_spectral_bounds: null pointer argument");
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_spectral_bounds: bad precision");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == TB_F32)
+    return run_bounds<float>(n, slice_ptr, col, static_cast<const float *>(val), static_cast<const float *>(diag),
+                             lanczos_steps, seed, bounds_out, workspace, workspace_bytes, st);
+  return run_bounds<double>(n, slice_ptr, col, static_cast<const double *>(val), static_cast<const double *>(diag),
+                            lanczos_steps, seed, bounds_out, workspace, workspace_bytes, st);
+}

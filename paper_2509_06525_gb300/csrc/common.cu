@@ -1,4 +1,5 @@
 // Error state and device queries of the C ABI.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 
@@ -29,6 +30,9 @@ tb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
   return TB_ERR_CUDA;
 }
 
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 int sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 152;
@@ -40,3 +44,4 @@ int sm_count() {
 
 extern "C" int32_t tb_abi_version(void) { return GPUTB_ABI_VERSION; }
 extern "C" const char *tb_last_error(void) { return gputb::g_err; }
+extern "C" int64_t tb_launch_count(void) { return gputb::g_launches.load(); }

@@ -14,6 +14,8 @@ void set_error(const char *fmt, ...);
 tb_status fail(tb_status code, const char *fmt, ...);
 tb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 int sm_count();
+// process-wide count of kernel launches issued by the library
+void note_launch();
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -41,7 +43,11 @@ struct Carver {
     if (e_ != cudaSuccess) return gputb::cuda_fail(e_, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define TB_CHECK_LAUNCH() TB_CUDA(cudaGetLastError())
+#define TB_CHECK_LAUNCH()       \
+  do {                          \
+    gputb::note_launch();       \
+    TB_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define TB_REQUIRE(cond, ...)                                                  \
   do {                                                                        \

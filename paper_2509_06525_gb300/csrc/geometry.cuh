@@ -1,0 +1,65 @@
+// Box geometry shared by the neighbour search and the kernels that
+// recompute bond vectors (teacher Hamiltonian, descriptors, MLP features).
+//
+// The box rows are a1 = (ax,0,0), a2 = (bx,by,0), a3 = (cx,cy,cz).  The
+// minimum-image displacement is reduced one lattice direction at a time
+// (a3, then a2, then a1).  When every periodic perpendicular width is at
+// least 2 r_cut, an image of j closer than r_cut to i, if one exists, is the
+// image this reduction returns.  Every operation is an explicitly rounded
+// FP64 intrinsic so the compiler cannot contract it into an FMA: the
+// membership test |d|^2 < r_cut^2 is reproducible bit for bit.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gputb {
+
+struct Box {
+  double ax, bx, by, cx, cy, cz;
+  int p1, p2, p3;  // periodic flags along a1, a2, a3
+};
+
+// Validate the box form and the 2 r_cut width rule on the host.
+tb_status make_box(const double *box9, const int32_t *pbc, double rcut, Box *out);
+
+__device__ __forceinline__ double3 min_image(const Box &B, double3 d) {
+  if (B.p3) {
+    const double n3 = rint(__ddiv_rn(d.z, B.cz));
+    d.x = __dsub_rn(d.x, __dmul_rn(n3, B.cx));
+    d.y = __dsub_rn(d.y, __dmul_rn(n3, B.cy));
+    d.z = __dsub_rn(d.z, __dmul_rn(n3, B.cz));
+  }
+  if (B.p2) {
+    const double n2 = rint(__ddiv_rn(d.y, B.by));
+    d.x = __dsub_rn(d.x, __dmul_rn(n2, B.bx));
+    d.y = __dsub_rn(d.y, __dmul_rn(n2, B.by));
+  }
+  if (B.p1) {
+    const double n1 = rint(__ddiv_rn(d.x, B.ax));
+    d.x = __dsub_rn(d.x, __dmul_rn(n1, B.ax));
+  }
+  return d;
+}
+
+__device__ __forceinline__ double sq_norm(double3 d) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(d.x, d.x), __dmul_rn(d.y, d.y)), __dmul_rn(d.z, d.z));
+}
+
+// displacement r_j - r_i (minimum image) from AoS positions [N][3]
+__device__ __forceinline__ double3 bond_vector(const Box &B, const double *__restrict__ pos, int64_t i,
+                                               int64_t j) {
+  double3 d;
+  d.x = __dsub_rn(__ldg(pos + 3 * j), __ldg(pos + 3 * i));
+  d.y = __dsub_rn(__ldg(pos + 3 * j + 1), __ldg(pos + 3 * i + 1));
+  d.z = __dsub_rn(__ldg(pos + 3 * j + 2), __ldg(pos + 3 * i + 2));
+  return min_image(B, d);
+}
+
+// Exclusive scan of int64 values (in may equal out); total (device) receives
+// the sum.  Workspace from scan_workspace_bytes(n).
+size_t scan_workspace_bytes(int64_t n);
+tb_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *ws,
+                             cudaStream_t st);
+
+}  // namespace gputb

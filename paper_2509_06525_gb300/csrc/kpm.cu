@@ -240,7 +240,7 @@ struct KpmRunner {
 
   static tb_status run(int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val, const valT *diag,
                        double a, double b, int M, uint64_t seed, double *mu_r, void *ws, size_t ws_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, double *step_ms) {
     const int grid = grid_for(n);
     Carver cv(ws, ws_bytes);
     real *v0 = cv.take<real>((size_t)n * R * 2);
@@ -254,6 +254,12 @@ struct KpmRunner {
     TB_CHECK_LAUNCH();
     const real shift = static_cast<real>(b);
     const size_t pstride = (size_t)grid * R;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (step_ms) {
+      TB_CUDA(cudaEventCreate(&ev[0]));
+      TB_CUDA(cudaEventCreate(&ev[1]));
+      TB_CUDA(cudaEventRecord(ev[0], st));
+    }
     // v1 = H~ v0 -> A
     cheb_step_kernel<real, valT, R, CPT, true><<<grid, kBlock, 0, st>>>(
         n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial + pstride, static_cast<real>(1.0 / a), shift);
@@ -268,12 +274,20 @@ struct KpmRunner {
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial + (size_t)m * pstride, two_over_a, shift);
       TB_CHECK_LAUNCH();
     }
+    if (step_ms) TB_CUDA(cudaEventRecord(ev[1], st));
     const int total = M * R;
     moment_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, mu_r, flags);
     TB_CHECK_LAUNCH();
     int hflags[4] = {0, 0, 0, 0};
     TB_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     TB_CUDA(cudaStreamSynchronize(st));
+    if (step_ms) {
+      float ms = 0.f;
+      TB_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      *step_ms = ms;
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+    }
     if (hflags[0] & 2) return fail(TB_ERR_NOT_FINITE, "kpm_moments: non-finite moment");
     if (hflags[0] & 1)
       return fail(TB_ERR_BOUNDS, "kpm_moments: |mu_n| > 1 + 1e-6; the spectrum is not inside [b - a, b + a]");
@@ -309,9 +323,9 @@ template <typename real, typename valT, int R>
 struct RunOp {
   static tb_status apply(int64_t n, const int64_t *sp, const int32_t *col, const void *val, const void *diag,
                          double a, double b, int M, uint64_t seed, double *mu, void *ws, size_t wsb,
-                         cudaStream_t st) {
+                         cudaStream_t st, double *step_ms) {
     return KpmRunner<real, valT, R>::run(n, sp, col, static_cast<const valT *>(val),
-                                         static_cast<const valT *>(diag), a, b, M, seed, mu, ws, wsb, st);
+                                         static_cast<const valT *>(diag), a, b, M, seed, mu, ws, wsb, st, step_ms);
   }
 };
 
@@ -332,20 +346,20 @@ extern "C" size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, in
 extern "C" tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col, const void *val,
                                  const void *diag, int32_t precision, double a, double b, int32_t M, int32_t R,
                                  uint64_t seed, double *mu_r, void *workspace, size_t workspace_bytes,
-                                 void *stream) {
+                                 void *stream, double *step_ms) {
   TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "kpm_moments: n=%lld out of range", (long long)n);
   TB_REQUIRE(M >= 2, "kpm_moments: M=%d must be >= 2", M);
   TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "kpm_moments: bad precision %d", precision);
   TB_REQUIRE(a > 0.0 && std::isfinite(a) && std::isfinite(b), "kpm_moments: need finite a > 0, b");
-  TB_REQUIRE(slice_ptr && col && val && mu_r && workspace, "kpm_moments: null pointer argument");
+  TB_REQUIRE(slice_ptr && mu_r && workspace, "kpm_moments: null pointer argument");
   TB_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "kpm_moments: workspace must be 256-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tb_status status = TB_OK;
   bool ok = precision == TB_F32
                 ? KpmDispatch<float, float>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                         seed, mu_r, workspace, workspace_bytes, st)
+                                                         seed, mu_r, workspace, workspace_bytes, st, step_ms)
                 : KpmDispatch<double, double>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                           seed, mu_r, workspace, workspace_bytes, st);
+                                                           seed, mu_r, workspace, workspace_bytes, st, step_ms);
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments: unsupported R=%d for precision %d", R, precision);
   return status;
 }

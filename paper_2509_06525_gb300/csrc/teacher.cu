@@ -1,0 +1,101 @@
+// Teacher Hamiltonian in SELL-32 form: the analytic, environment-dependent
+// orthogonal pz model (form of Eq. 1, arXiv 2509.06525 Sec. 3) that labels
+// the training snapshots and serves as the plain method:
+//   t_ij  = P[Z_i,Z_j] exp(-beta (r_ij/a_cc - 1)) (1 + gamma (n_i+n_j-6)/6) f_c(r_ij)
+//   f_c(r) = (1 + cos(pi r / r_cut)) / 2 for r < r_cut, else 0
+//   eps_i = onsite[Z_i]
+// One thread per row walks the row's slots (coalesced across the 32 rows of
+// a slice), recomputes the bond vector with the FP64 minimum image and
+// writes the value in FP32 or FP64.  Values are evaluated in FP64.
+#include <cmath>
+
+#include "geometry.cuh"
+
+namespace gputb {
+namespace {
+
+struct TeacherConst {
+  double pref[9];
+  double onsite[3];
+  double a_cc, beta, gamma, rcut;
+  int n_species;
+};
+
+template <typename valT>
+__global__ void teacher_kernel(const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n,
+                               Box B, TeacherConst T, const int64_t *__restrict__ slice_ptr,
+                               const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
+                               const int32_t *__restrict__ ncount, valT *__restrict__ val, valT *__restrict__ diag,
+                               int *__restrict__ flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t sb = slice_ptr[i >> 5];
+  const int w = static_cast<int>((slice_ptr[(i >> 5) + 1] - sb) >> 5);
+  const int zi = species[i];
+  if (zi < 0 || zi >= T.n_species) atomicOr(flags, 1);
+  const int zic = min(max(zi, 0), T.n_species - 1);
+  const int ni = ncount[i];
+  const int m = cnt[i];
+  int64_t e = sb + (i & 31);
+  for (int s = 0; s < w; ++s, e += 32) {
+    double t = 0.0;
+    if (s < m) {
+      const int32_t j = col[e];
+      const int zj = min(max(species[j], 0), T.n_species - 1);
+      const double3 d = bond_vector(B, pos, i, j);
+      const double r = sqrt(sq_norm(d));
+      const double fc = r < T.rcut ? 0.5 * (1.0 + cos(M_PI * r / T.rcut)) : 0.0;
+      const double env = 1.0 + T.gamma * ((double)(ni + ncount[j]) - 6.0) / 6.0;
+      t = T.pref[zic * 3 + zj] * exp(-T.beta * (r / T.a_cc - 1.0)) * env * fc;
+    }
+    val[e] = static_cast<valT>(t);
+  }
+  if (diag) diag[i] = static_cast<valT>(T.onsite[zic]);
+}
+
+}  // namespace
+}  // namespace gputb
+
+using namespace gputb;
+
+extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const int32_t *species, int64_t n,
+                                                  const double *box, const int32_t *pbc, const int64_t *slice_ptr,
+                                                  const int32_t *col, const int32_t *cnt, const int32_t *ncount,
+                                                  const double *hop_prefactor, const double *onsite, double a_cc,
+                                                  double beta, double gamma, double rcut, int32_t precision,
+                                                  void *val, void *diag, void *stream) {
+  TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "tb_build_hamiltonian_teacher: bad n");
+  TB_REQUIRE(positions && species && slice_ptr && cnt && ncount && hop_prefactor && onsite,
+             "tb_build_hamiltonian_teacher: null pointer argument");
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian_teacher: bad precision");
+  TB_REQUIRE(a_cc > 0.0 && rcut > 0.0, "tb_build_hamiltonian_teacher: need a_cc > 0 and rcut > 0");
+  Box B;
+  tb_status s = make_box(box, pbc, rcut, &B);
+  if (s != TB_OK) return s;
+  TeacherConst T;
+  for (int k = 0; k < 9; ++k) T.pref[k] = hop_prefactor[k];
+  for (int k = 0; k < 3; ++k) T.onsite[k] = onsite[k];
+  T.a_cc = a_cc;
+  T.beta = beta;
+  T.gamma = gamma;
+  T.rcut = rcut;
+  T.n_species = 3;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int *flags = nullptr;
+  TB_CUDA(cudaMallocAsync(&flags, sizeof(int), st));
+  TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  if (precision == TB_F32)
+    teacher_kernel<float><<<nb, 256, 0, st>>>(positions, species, n, B, T, slice_ptr, col, cnt, ncount,
+                                              static_cast<float *>(val), static_cast<float *>(diag), flags);
+  else
+    teacher_kernel<double><<<nb, 256, 0, st>>>(positions, species, n, B, T, slice_ptr, col, cnt, ncount,
+                                               static_cast<double *>(val), static_cast<double *>(diag), flags);
+  TB_CHECK_LAUNCH();
+  int h = 0;
+  TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaFreeAsync(flags, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  if (h & 1) return fail(TB_ERR_INVALID_ARG, "tb_build_hamiltonian_teacher: species outside [0, 3)");
+  return TB_OK;
+}

@@ -37,9 +37,19 @@ SIGNATURES = {
     "tb_abi_version": (_c_i32, []),
     "tb_last_error": (ctypes.c_char_p, []),
     "kpm_moments_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
+    "tb_launch_count": (_c_i64, []),
     "kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32,
-                             _c_u64, _c_vp, _c_vp, _c_sz, _c_vp]),
+                             _c_u64, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
+    "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl]),
+    "tb_build_neighbors": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_vp, _c_vp, _c_i64,
+                                    _c_vp, _c_vp, ctypes.POINTER(_c_i64), _c_vp, _c_sz, _c_vp]),
+    "tb_build_hamiltonian_teacher": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                                              _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i32, _c_vp,
+                                              _c_vp, _c_vp]),
+    "tb_spectral_bounds_workspace_size": (_c_sz, [_c_i64, _c_i32]),
+    "tb_spectral_bounds": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_i32, _c_u64, _c_vp, _c_vp,
+                                    _c_sz, _c_vp]),
 }
 
 
@@ -115,8 +125,12 @@ class SellMatrix:
 
 
 def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
-                stream=None, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Per-vector KPM moments mu_r [R, M] (float64, device)."""
+                stream=None, workspace: Optional[torch.Tensor] = None, timing: Optional[list] = None
+                ) -> torch.Tensor:
+    """Per-vector KPM moments mu_r [R, M] (float64, device).
+
+    If `timing` is a list, the CUDA-event time (ms) of the Chebyshev-step
+    launches is appended to it."""
     L = lib()
     prec = H.precision
     need = L.kpm_moments_workspace_size(H.n, M, R, prec)
@@ -124,10 +138,14 @@ def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
         raise GputbError("kpm_moments_workspace_size", TB_ERR_INVALID_ARG, f"unsupported n={H.n} M={M} R={R}")
     ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, H.col.device)
     mu = torch.empty((R, M), dtype=torch.float64, device=H.col.device)
+    step_ms = ctypes.c_double(0.0)
     st = L.kpm_moments(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), prec,
                        float(a), float(b), int(M), int(R), int(seed) & ((1 << 64) - 1),
-                       _ptr(mu), _ptr(ws), ws.numel(), _stream(stream))
+                       _ptr(mu), _ptr(ws), ws.numel(), _stream(stream),
+                       ctypes.byref(step_ms) if timing is not None else None)
     _check("kpm_moments", st)
+    if timing is not None:
+        timing.append(step_ms.value)
     return mu
 
 
@@ -141,3 +159,91 @@ def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel
                    energy.numel(), _ptr(out), _stream(stream))
     _check("kpm_dos", st)
     return out
+
+
+def _host_box(box, pbc):
+    import numpy as np
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(9))
+    p = np.ascontiguousarray(np.asarray(pbc, dtype=np.int32).reshape(3))
+    return b, p, b.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Neighbors:
+    """SELL-32 neighbour structure on the device (the Hamiltonian's pattern)."""
+    n: int
+    slice_ptr: torch.Tensor      # int64 [ceil(n/32)+1]
+    col: torch.Tensor            # int32 [total]
+    cnt: torch.Tensor            # int32 [n]
+    ncount: Optional[torch.Tensor]
+    total: int
+
+
+def build_neighbors(positions: torch.Tensor, box, pbc, rcut: float, r_count: float = 1.8,
+                    max_width: int = 16, stream=None) -> Neighbors:
+    """tb_build_neighbors for device positions [N, 3] float64."""
+    L = lib()
+    n = positions.shape[0]
+    dev = positions.device
+    b, p, bptr, pptr = _host_box(box, pbc)
+    need = L.tb_neighbors_workspace_size(n, bptr, pptr, float(rcut))
+    if need == 0:
+        raise GputbError("tb_neighbors_workspace_size", TB_ERR_BOX, lib().tb_last_error().decode())
+    ws = _workspace(need, dev)
+    n_slices = (n + 31) // 32
+    slice_ptr = torch.empty(n_slices + 1, dtype=torch.int64, device=dev)
+    cap = n_slices * 32 * max_width
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    ncount = torch.empty(n, dtype=torch.int32, device=dev) if r_count > 0 else None
+    total = ctypes.c_int64(0)
+    st = L.tb_build_neighbors(_ptr(positions), n, bptr, pptr, float(rcut), float(r_count), int(max_width),
+                              _ptr(slice_ptr), _ptr(col), cap, _ptr(cnt), _ptr(ncount), ctypes.byref(total),
+                              _ptr(ws), ws.numel(), _stream(stream))
+    _check("tb_build_neighbors", st)
+    return Neighbors(n, slice_ptr, col[:total.value], cnt, ncount, total.value)
+
+
+def build_hamiltonian_teacher(positions: torch.Tensor, species: torch.Tensor, box, pbc, nb: Neighbors,
+                              teacher, dtype=torch.float64, with_diag: bool = True, stream=None) -> SellMatrix:
+    """tb_build_hamiltonian_teacher: teacher values in the SELL-32 pattern of nb."""
+    import numpy as np
+    L = lib()
+    dev = positions.device
+    b, p, bptr, pptr = _host_box(box, pbc)
+    pref = np.ascontiguousarray(np.asarray(teacher.hop_prefactor, np.float64).reshape(9))
+    onsite = np.ascontiguousarray(np.asarray(teacher.onsite, np.float64).reshape(3))
+    val = torch.empty(max(nb.total, 1), dtype=dtype, device=dev)
+    diag = torch.empty(nb.n, dtype=dtype, device=dev) if with_diag else None
+    st = L.tb_build_hamiltonian_teacher(
+        _ptr(positions), _ptr(species), nb.n, bptr, pptr, _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(nb.cnt),
+        _ptr(nb.ncount), pref.ctypes.data_as(ctypes.c_void_p), onsite.ctypes.data_as(ctypes.c_void_p),
+        float(teacher.a_cc), float(teacher.beta), float(teacher.gamma), float(teacher.rcut), precision_of(dtype),
+        _ptr(val), _ptr(diag), _stream(stream))
+    _check("tb_build_hamiltonian_teacher", st)
+    return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
+
+
+@dataclass
+class Bounds:
+    emin: float
+    emax: float
+    a: float
+    b: float
+    theta_min: float
+    theta_max: float
+    g_min: float
+    g_max: float
+
+
+def spectral_bounds(H: SellMatrix, lanczos_steps: int = 64, seed: int = 7, stream=None) -> Bounds:
+    import numpy as np
+    L = lib()
+    need = L.tb_spectral_bounds_workspace_size(H.n, lanczos_steps)
+    ws = _workspace(need, H.col.device)
+    out = np.zeros(8, np.float64)
+    st = L.tb_spectral_bounds(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), H.precision,
+                              int(lanczos_steps), int(seed), out.ctypes.data_as(ctypes.c_void_p), _ptr(ws),
+                              ws.numel(), _stream(stream))
+    _check("tb_spectral_bounds", st)
+    return Bounds(*[float(v) for v in out])
