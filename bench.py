@@ -54,13 +54,19 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 teacher comparison run")
+    p.add_argument("--M", type=int, default=None, help="override the workload's moment count (profiling)")
+    p.add_argument("--R", type=int, default=None, help="override the workload's vector count (profiling)")
     return p.parse_args()
 
 
 # ---------------------------------------------------------------- structure
 
-def make_structure(name):
-    w = synth.WORKLOADS[name]
+def make_structure(name, M=None, R=None):
+    w = dict(synth.WORKLOADS[name])
+    if M:
+        w["M"] = M
+    if R:
+        w["R"] = R
     if w["kind"] == "rect":
         return synth.graphene_rect(w["nx"], w["ny"], w["sigma"], w["seed"]), w
     if w["kind"] == "prim":
@@ -241,7 +247,7 @@ def run_ours(args):
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     build.build()
-    s, w = make_structure(args.workload)
+    s, w = make_structure(args.workload, args.M, args.R)
     pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g)
     lib = g.lib()
 
@@ -273,7 +279,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "atoms": n_atoms, "moments": M, "random_vectors": R,
+        "config": {"workload": args.workload + ("" if (args.M is None and args.R is None) else "-override"),
+                   "atoms": n_atoms, "moments": M, "random_vectors": R,
                    "hamiltonian": args.hamiltonian, "kpm_precision": "complex FP32, FP64 moment sums",
                    "l2": "inputs larger than L2 (ELL and vector blocks >> 126 MB)",
                    "step": "neighbours + H build + FP64 bounds + KPM + Jackson DOS"},

@@ -363,3 +363,4 @@ extern "C" tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int3
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments: unsupported R=%d for precision %d", R, precision);
   return status;
 }
+
