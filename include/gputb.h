@@ -123,6 +123,33 @@ TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t 
                       void *stream, double *step_ms);
 
 /* ---------------------------------------------------------------------
+ * kpm_moments without any device allocation (no counterpart in the paper;
+ * an interface convenience of this library).
+ *
+ * For callers that cannot allocate device memory where they need the
+ * moments: code inside a framework that owns the device memory pool,
+ * latency-critical loops where cudaMalloc would synchronise the device, or
+ * plug-ins that are handed only their input and output buffers.  Same
+ * arguments, results and checks as kpm_moments, minus the workspace and the
+ * timing output: the scratch lives in a static 32 MiB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Sizes whose kpm_moments_workspace_size exceeds 32 MiB are rejected
+ * with TB_ERR_WORKSPACE (use kpm_moments with a caller workspace instead).
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and every call
+ * overwrites it: calls whose GPU work may overlap (other streams, other host
+ * threads on the same device) race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ * Synchronises `stream`.
+ * ------------------------------------------------------------------- */
+TB_API tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                                     const void *val, const void *diag, int32_t precision,
+                                     double a, double b, int32_t M, int32_t R, uint64_t seed,
+                                     double *mu_r, void *stream);
+
+/* ---------------------------------------------------------------------
  * KPM density of states, Eq. 4, per orbital per eV (integrates to 1):
  *   rho(E_k) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(x_k)] / (pi a sqrt(1-x_k^2))
  * with x_k = (E_k - b)/a, rho = 0 where |x_k| >= 1, mu_n the mean over the

@@ -364,3 +364,80 @@ extern "C" tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int3
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of kpm_moments.
+//
+// Some callers cannot allocate device memory at the point where they want
+// the moments: code running inside a framework that owns the device memory
+// pool and forbids outside allocations, real-time or latency-critical loops
+// where cudaMalloc would synchronise the device, and plug-ins that only
+// receive input and output buffers.  For them the scratch space (the three
+// vector blocks, the per-CTA moment partials and the status flags) lives in
+// one statically sized device array that the CUDA module carries; every GPU
+// that loads this library holds it until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gputb {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB limit
+static __device__ __align__(256) unsigned char g_kpm_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+struct NoAllocSlot {
+  std::once_flag once;
+  void *ptr = nullptr;
+  cudaError_t err = cudaSuccess;
+};
+NoAllocSlot g_noalloc_slots[kMaxDevices];
+
+// Device address of the static scratch array on the current device.  In host
+// code the array's name is only a host-side stand-in, so the address is
+// looked up once per device with that device current.
+tb_status noalloc_scratch(void **out) {
+  int dev = 0;
+  TB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(TB_ERR_INVALID_ARG, "kpm_moments_noalloc: device %d", dev);
+  NoAllocSlot &slot = g_noalloc_slots[dev];
+  std::call_once(slot.once, [&slot] {
+    slot.err = cudaGetSymbolAddress(&slot.ptr, g_kpm_noalloc_scratch);
+  });
+  if (slot.err != cudaSuccess) return cuda_fail(slot.err, "cudaGetSymbolAddress", __FILE__, __LINE__);
+  if (!slot.ptr) return fail(TB_ERR_CUDA, "kpm_moments_noalloc: null scratch address");
+  *out = slot.ptr;
+  return TB_OK;
+}
+
+}  // namespace
+}  // namespace gputb
+
+extern "C" tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, const int32_t *col, const void *val,
+                                         const void *diag, int32_t precision, double a, double b, int32_t M,
+                                         int32_t R, uint64_t seed, double *mu_r, void *stream) {
+  TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "kpm_moments_noalloc: n=%lld out of range", (long long)n);
+  TB_REQUIRE(M >= 2, "kpm_moments_noalloc: M=%d must be >= 2", M);
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "kpm_moments_noalloc: bad precision %d", precision);
+  TB_REQUIRE(a > 0.0 && std::isfinite(a) && std::isfinite(b), "kpm_moments_noalloc: need finite a > 0, b");
+  TB_REQUIRE(slice_ptr && mu_r, "kpm_moments_noalloc: null pointer argument");
+  const size_t need = kpm_moments_workspace_size(n, M, R, precision);
+  if (need == 0) return fail(TB_ERR_INVALID_ARG, "kpm_moments_noalloc: unsupported R=%d", R);
+  if (need > kNoAllocScratchBytes)
+    return fail(TB_ERR_WORKSPACE,
+                "kpm_moments_noalloc: this size needs %zu bytes of scratch but the built-in scratch holds %zu "
+                "bytes (32 MiB); call kpm_moments with a caller workspace instead",
+                need, kNoAllocScratchBytes);
+  void *scratch = nullptr;
+  tb_status status = noalloc_scratch(&scratch);
+  if (status != TB_OK) return status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the shared KPM runner clears the status flags it accumulates; every other
+  // scratch word is written before it is read
+  bool ok = precision == TB_F32
+                ? KpmDispatch<float, float>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
+                                                         seed, mu_r, scratch, kNoAllocScratchBytes, st, nullptr)
+                : KpmDispatch<double, double>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
+                                                           seed, mu_r, scratch, kNoAllocScratchBytes, st, nullptr);
+  if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_noalloc: unsupported R=%d", R);
+  return status;
+}

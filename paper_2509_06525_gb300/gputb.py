@@ -40,6 +40,8 @@ SIGNATURES = {
     "tb_launch_count": (_c_i64, []),
     "kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32,
                              _c_u64, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
+    "kpm_moments_noalloc": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32,
+                                     _c_i32, _c_u64, _c_vp, _c_vp]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
     "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl]),
     "tb_build_neighbors": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_vp, _c_vp, _c_i64,
