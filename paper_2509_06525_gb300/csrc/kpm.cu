@@ -45,31 +45,41 @@ __device__ __forceinline__ double phase_uniform(uint64_t seed, uint64_t r, uint6
   return static_cast<double>(z >> 11) * 0x1.0p-53;
 }
 
-template <typename real, int CPT> struct Vec;
-template <> struct Vec<float, 1> { using T = float2; };
-template <> struct Vec<float, 2> { using T = float4; };
-template <> struct Vec<double, 1> { using T = double2; };
+// Each thread moves CPT complex numbers of one row: one 8-byte access
+// (FP32, CPT = 1) or CPT*8/16 (FP32) / CPT (FP64) 16-byte accesses.
+template <typename real, int CPT> struct Vec { using T = float4; static constexpr int kChunks = CPT / 2; };
+template <> struct Vec<float, 1> { using T = float2; static constexpr int kChunks = 1; };
+template <int CPT> struct Vec<double, CPT> { using T = double2; static constexpr int kChunks = CPT; };
 
 // read-only cached load (neighbour gathers)
 template <typename real, int CPT>
 __device__ __forceinline__ void ld_gather(const real *p, real (&o)[2 * CPT]) {
   using V = typename Vec<real, CPT>::T;
-  V t = __ldg(reinterpret_cast<const V *>(p));
-  memcpy(o, &t, sizeof(V));
+#pragma unroll
+  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
+    V t = __ldg(reinterpret_cast<const V *>(p) + k);
+    memcpy(o + k * (sizeof(V) / sizeof(real)), &t, sizeof(V));
+  }
 }
 // streaming load / store (each element touched once per step)
 template <typename real, int CPT>
 __device__ __forceinline__ void ld_stream(const real *p, real (&o)[2 * CPT]) {
   using V = typename Vec<real, CPT>::T;
-  V t = __ldcs(reinterpret_cast<const V *>(p));
-  memcpy(o, &t, sizeof(V));
+#pragma unroll
+  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
+    V t = __ldcs(reinterpret_cast<const V *>(p) + k);
+    memcpy(o + k * (sizeof(V) / sizeof(real)), &t, sizeof(V));
+  }
 }
 template <typename real, int CPT>
 __device__ __forceinline__ void st_stream(real *p, const real (&v)[2 * CPT]) {
   using V = typename Vec<real, CPT>::T;
-  V t;
-  memcpy(&t, v, sizeof(V));
-  __stcs(reinterpret_cast<V *>(p), t);
+#pragma unroll
+  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
+    V t;
+    memcpy(&t, v + k * (sizeof(V) / sizeof(real)), sizeof(V));
+    __stcs(reinterpret_cast<V *>(p) + k, t);
+  }
 }
 
 // Sum acc over all rows of the CTA for each of the R vectors and write the
@@ -129,8 +139,17 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
 // One Chebyshev step over all rows:
 //   out = alpha * (sum_s val x[col] + (diag_i - shift) x_i) - (FIRST ? 0 : prev)
 // and the CTA partials of Re(conj(v0) out).  `prev` may alias `out`.
+//
+// The kernel is bound by HBM latency as much as by bandwidth: each row's
+// gathers depend on its column loads, which depend on the slice offset.  So
+// a row with at most kFastW slots issues all of its column and value loads
+// first (predicated, fully unrolled), then all of its neighbour gathers,
+// with the row's own v_{n-1} and v0 loads hoisted above them; wider rows take
+// a plain loop.
+constexpr int kFastW = 16;
+
 template <typename real, typename valT, int R, int CPT, bool FIRST>
-__global__ void __launch_bounds__(kBlock) cheb_step_kernel(
+__global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 3) cheb_step_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x,
     const real *prev, const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha,
@@ -144,23 +163,47 @@ __global__ void __launch_bounds__(kBlock) cheb_step_kernel(
   for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < n; row0 += (int64_t)gridDim.x * RPB) {
     const int64_t i = row0 + threadIdx.x / TPR;
     if (i < n) {
+      const int64_t off = (i * R + part * CPT) * 2;
+      real p[2 * CPT], z[2 * CPT];
+      if (!FIRST) ld_stream<real, CPT>(prev + off, p);
+      ld_stream<real, CPT>(v0 + off, z);
       const int64_t sb = __ldg(slice_ptr + (i >> 5));
       const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
-      int64_t e = sb + (i & 31);
+      const int64_t e0 = sb + (i & 31);
       real y[2 * CPT];
 #pragma unroll
       for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
-#pragma unroll 4
-      for (int s = 0; s < w; ++s, e += 32) {
-        const int32_t j = __ldcs(col + e);
-        const real h = static_cast<real>(__ldcs(val + e));
-        real xv[2 * CPT];
-        ld_gather<real, CPT>(x + ((int64_t)j * R + part * CPT) * 2, xv);
+      if (w <= kFastW) {
+        int32_t j[kFastW];
+        real h[kFastW];
 #pragma unroll
-        for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+        for (int s = 0; s < kFastW; ++s) {
+          if (s < w) {
+            j[s] = __ldcs(col + e0 + 32 * s);
+            h[s] = static_cast<real>(__ldcs(val + e0 + 32 * s));
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < kFastW; ++s) {
+          if (s < w) {
+            real xv[2 * CPT];
+            ld_gather<real, CPT>(x + ((int64_t)j[s] * R + part * CPT) * 2, xv);
+#pragma unroll
+            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h[s], xv[c], y[c]);
+          }
+        }
+      } else {
+        int64_t e = e0;
+        for (int s = 0; s < w; ++s, e += 32) {
+          const int32_t jj = __ldcs(col + e);
+          const real hh = static_cast<real>(__ldcs(val + e));
+          real xv[2 * CPT];
+          ld_gather<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
+#pragma unroll
+          for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
+        }
       }
       const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
-      const int64_t off = (i * R + part * CPT) * 2;
       {
         real xi[2 * CPT];
         ld_gather<real, CPT>(x + off, xi);
@@ -168,18 +211,9 @@ __global__ void __launch_bounds__(kBlock) cheb_step_kernel(
         for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
       }
       real o[2 * CPT];
-      if (FIRST) {
 #pragma unroll
-        for (int c = 0; c < 2 * CPT; ++c) o[c] = alpha * y[c];
-      } else {
-        real p[2 * CPT];
-        ld_stream<real, CPT>(prev + off, p);
-#pragma unroll
-        for (int c = 0; c < 2 * CPT; ++c) o[c] = fma(alpha, y[c], -p[c]);
-      }
+      for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
       st_stream<real, CPT>(out + off, o);
-      real z[2 * CPT];
-      ld_stream<real, CPT>(v0 + off, z);
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         // Re(conj(v0) * o) = z.re o.re + z.im o.im, summed in FP64
@@ -211,7 +245,10 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 
 template <typename real, typename valT, int R>
 struct KpmRunner {
-  static constexpr int CPT = (sizeof(real) == 4 && R >= 2) ? 2 : 1;
+  // complex numbers per thread, chosen by measurement on GB300 (10M-atom
+  // graphene): FP32 R = 4 -> 4 (two 16-byte accesses), other R >= 2 -> 2
+  // (one 16-byte access), R = 1 -> 1; FP64 2 when R >= 2, else 1
+  static constexpr int CPT = sizeof(real) == 4 ? (R == 4 ? 4 : (R >= 2 ? 2 : 1)) : (R >= 2 ? 2 : 1);
   static constexpr int TPR = R / CPT;
   static constexpr int RPB = kBlock / TPR;
 
