@@ -240,6 +240,105 @@ TB_API tb_status tb_spectral_bounds(int64_t n, const int64_t *slice_ptr, const i
                                     int32_t lanczos_steps, uint64_t seed, double *bounds_out,
                                     void *workspace, size_t workspace_bytes, void *stream);
 
+/* =====================================================================
+ * Learned Hamiltonian (Sec. 3, Eq. 2; training per Sec. 2.1 and Eq. 3)
+ *
+ * Descriptors:  f_k(r) = (T_k(2(r/rcut - 1)^2 - 1) + 1)/2 f_c(r), k = 0..7,
+ *               f_c(r) = (1 + cos(pi r/rcut))/2 (r < rcut);
+ *               C_n(r_ij) = sum_k c[Z_i][Z_j][n][k] f_k(r_ij);
+ *               v_i = sum_{j in N(i)} C(r_ij).
+ * Edge input:   x_ij = [C(r_ij), v_i, v_j, C(r_ij)*(v_i + v_j)] (32 floats);
+ *               xn = (x - mean) * inv_std.
+ * Network:      y = W3 silu(W2 silu(W1 xn + b1) + b2) + b3, 32-64-64-2,
+ *               BF16 weights and activations on tensor cores, FP32
+ *               accumulation, FP32 master parameters.
+ * Hamiltonian:  H_ij = (y0(i->j) + y0(j->i))/2, eps_i = eps0[Z_i] + sum_j y1(i->j).
+ *
+ * Parameter vector (FP32, 6402 floats, caller-owned, device):
+ *   W1 [64][32] @0, b1 [64] @2048, W2 [64][64] @2112, b2 [64] @6208,
+ *   W3 [2][64] @6272, b3 [2] @6400   (row-major [out][in]).
+ * BF16 weight copy (6272 bf16): W1 @0, W2 @2048, W3 @6144.
+ * cmix: device float [3][3][8][8];  v: device float [N][8].
+ * Edge arrays (x, y, dy, t_hop) follow the SELL-32 element order of the
+ * neighbour structure; padding elements hold zeros and are ignored.
+ * ===================================================================== */
+
+/* v_i for every atom (device float [N][8]). */
+TB_API tb_status tb_compute_descriptors(const double *positions, const int32_t *species, int64_t n,
+                                        const double *box, const int32_t *pbc, double rcut,
+                                        const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                        const float *cmix, float *v, void *stream);
+
+/* Edge inputs of every SELL element: x_raw (device float [total][32], may be
+ * NULL) and/or x_bf16 (device bf16 [total][32], normalised with mean/inv_std
+ * (device float [32]) when both are given, else raw; may be NULL). */
+TB_API tb_status tb_edge_features(const double *positions, const int32_t *species, int64_t n,
+                                  const double *box, const int32_t *pbc, double rcut,
+                                  const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                  const float *cmix, const float *v, const float *mean,
+                                  const float *inv_std, float *x_raw, void *x_bf16, void *stream);
+
+/* Per-feature mean and standard deviation (population) of x_raw over the
+ * real (non-padding) elements of rows 0..n-1, accumulated in FP64.
+ * workspace >= 96 * 8 * 4 * (SM count) bytes. */
+TB_API tb_status tb_feature_stats(const float *x_raw, int64_t n, const int64_t *slice_ptr,
+                                  const int32_t *cnt, float *mean, float *stdv, void *workspace,
+                                  size_t workspace_bytes, void *stream);
+
+/* Workspace bytes of tb_mlp_backward for n_edges edges. */
+TB_API size_t tb_mlp_workspace_size(int64_t n_edges);
+
+/* y (device float [n_edges][2]) = MLP(x_bf16 [n_edges][32]). */
+TB_API tb_status tb_mlp_forward(int64_t n_edges, const void *x_bf16, const void *w_bf16,
+                                const float *params, float *y, void *stream);
+
+/* grad (device float [6402]) = sum over edges of dL/dparams given dL/dy
+ * (device float [n_edges][2]); the forward pass is recomputed.  Per-CTA
+ * partial gradients are summed in a fixed order (reproducible). */
+TB_API tb_status tb_mlp_backward(int64_t n_edges, const void *x_bf16, const void *w_bf16,
+                                 const float *params, const float *dy, float *grad, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
+/* Loss of the form of Eq. 3 on the Hamiltonian of rows [row_begin, row_end)
+ * (row_begin a multiple of 32):
+ *   D = {y0(e) - t_hop(e) for the real elements e of those rows}
+ *       U {eps0[Z_i] + sum_e y1(e) - eps_target(i)},  n = |D|,
+ *   L = (sum|D|/n)^2 + sum D^2/n.
+ * Writes dL/dy into dy for every element of those rows (0 for padding) and
+ * stats (device double[4]) = {sum|D|/n, sum D^2/n, n, L}.
+ * workspace >= 3 * 8 * 2 * (SM count) bytes. */
+TB_API tb_status tb_mlp_loss(int64_t row_begin, int64_t row_end, const int64_t *slice_ptr,
+                             const int32_t *cnt, const float *y, const float *t_hop,
+                             const float *eps_target, const int32_t *species, const float *eps0,
+                             float *dy, double *stats, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+/* One AdamW step (decoupled weight decay, bias-corrected moments; step >= 1)
+ * on the FP32 parameters; refreshes the BF16 weight copy. */
+TB_API tb_status tb_adamw_step(float *params, const float *grad, float *m, float *v, int64_t step,
+                               double lr, double beta1, double beta2, double eps,
+                               double weight_decay, void *w_bf16, void *stream);
+
+/* BF16 weight copy from the FP32 parameters. */
+TB_API tb_status tb_mlp_pack_weights(const float *params, void *w_bf16, void *stream);
+
+/* Workspace bytes of tb_build_hamiltonian. */
+TB_API size_t tb_build_hamiltonian_workspace_size(int64_t total_elements);
+
+/* Learned Hamiltonian in SELL-32: val (device, `precision`, [total]) and
+ * diag (device [N] or NULL).  v from tb_compute_descriptors on the same
+ * structure; mean/inv_std may be NULL (no normalisation); eps0 device
+ * float [3].  Synchronises `stream`; TB_ERR_INVALID_ARG if the neighbour
+ * relation is not symmetric. */
+TB_API tb_status tb_build_hamiltonian(const double *positions, const int32_t *species, int64_t n,
+                                      const double *box, const int32_t *pbc, double rcut,
+                                      const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                      int64_t total_elements, const float *cmix, const float *v,
+                                      const float *mean, const float *inv_std, const void *w_bf16,
+                                      const float *params, const float *eps0, int32_t precision,
+                                      void *val, void *diag, void *workspace, size_t workspace_bytes,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

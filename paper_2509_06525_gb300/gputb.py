@@ -49,6 +49,23 @@ SIGNATURES = {
     "tb_build_hamiltonian_teacher": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
                                               _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i32, _c_vp,
                                               _c_vp, _c_vp]),
+    "tb_compute_descriptors": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp,
+                                        _c_vp, _c_vp]),
+    "tb_edge_features": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                                  _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]),
+    "tb_feature_stats": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_mlp_workspace_size": (_c_sz, [_c_i64]),
+    "tb_mlp_forward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]),
+    "tb_mlp_backward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_mlp_loss": (_c_i32, [_c_i64, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                             _c_sz, _c_vp]),
+    "tb_adamw_step": (_c_i32, [_c_vp, _c_vp, _c_vp, _c_vp, _c_i64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_vp,
+                               _c_vp]),
+    "tb_mlp_pack_weights": (_c_i32, [_c_vp, _c_vp, _c_vp]),
+    "tb_build_hamiltonian_workspace_size": (_c_sz, [_c_i64]),
+    "tb_build_hamiltonian": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i64,
+                                      _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp,
+                                      _c_sz, _c_vp]),
     "tb_spectral_bounds_workspace_size": (_c_sz, [_c_i64, _c_i32]),
     "tb_spectral_bounds": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_i32, _c_u64, _c_vp, _c_vp,
                                     _c_sz, _c_vp]),
@@ -249,3 +266,147 @@ def spectral_bounds(H: SellMatrix, lanczos_steps: int = 64, seed: int = 7, strea
                               ws.numel(), _stream(stream))
     _check("tb_spectral_bounds", st)
     return Bounds(*[float(v) for v in out])
+
+
+# ------------------------------------------------------------------ learned path
+
+N_PARAM = 6402
+N_WBF16 = 6272
+PARAM_OFFSETS = {"W1": (0, (64, 32)), "b1": (2048, (64,)), "W2": (2112, (64, 64)), "b2": (6208, (64,)),
+                 "W3": (6272, (2, 64)), "b3": (6400, (2,))}
+
+
+def pack_params(params: dict) -> "np.ndarray":
+    """Flatten {W1, b1, W2, b2, W3, b3} into the library's FP32 parameter vector."""
+    import numpy as np
+    flat = np.zeros(N_PARAM, np.float32)
+    for k, (off, shape) in PARAM_OFFSETS.items():
+        flat[off:off + int(np.prod(shape))] = np.asarray(params[k], np.float32).reshape(-1)
+    return flat
+
+
+def unpack_params(flat) -> dict:
+    import numpy as np
+    flat = np.asarray(flat)
+    return {k: flat[off:off + int(np.prod(shape))].reshape(shape).copy() for k, (off, shape) in PARAM_OFFSETS.items()}
+
+
+class MLPModel:
+    """Device state of the learned model: FP32 parameters, their BF16 weight
+    copy, AdamW moments, frozen input normalisation and the descriptor
+    mixing matrices."""
+
+    def __init__(self, params: dict, cmix, eps0, mean=None, std=None, device="cuda", stream=None):
+        import numpy as np
+        self.p = torch.tensor(pack_params(params), device=device)
+        self.wb = torch.empty(N_WBF16, dtype=torch.bfloat16, device=device)
+        self.m = torch.zeros(N_PARAM, dtype=torch.float32, device=device)
+        self.v = torch.zeros(N_PARAM, dtype=torch.float32, device=device)
+        self.cmix = torch.tensor(np.asarray(cmix, np.float32).reshape(-1), device=device)
+        self.eps0 = torch.tensor(np.asarray(eps0, np.float32), device=device)
+        self.mean = None if mean is None else torch.as_tensor(mean, dtype=torch.float32, device=device)
+        self.inv_std = None
+        if std is not None:
+            s = torch.as_tensor(std, dtype=torch.float32, device=device)
+            self.inv_std = 1.0 / torch.clamp(s, min=1e-6)
+        self.step = 0
+        _check("tb_mlp_pack_weights", lib().tb_mlp_pack_weights(_ptr(self.p), _ptr(self.wb), _stream(stream)))
+
+    def set_normalisation(self, mean: torch.Tensor, std: torch.Tensor):
+        self.mean = mean.to(torch.float32).contiguous()
+        self.inv_std = (1.0 / torch.clamp(std.to(torch.float32), min=1e-6)).contiguous()
+
+    def params_numpy(self) -> dict:
+        return unpack_params(self.p.cpu().numpy())
+
+
+def compute_descriptors(positions, species, box, pbc, rcut, nb: Neighbors, cmix: torch.Tensor,
+                        stream=None) -> torch.Tensor:
+    b, p, bptr, pptr = _host_box(box, pbc)
+    v = torch.empty((nb.n, 8), dtype=torch.float32, device=positions.device)
+    st = lib().tb_compute_descriptors(_ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut),
+                                      _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(nb.cnt), _ptr(cmix), _ptr(v),
+                                      _stream(stream))
+    _check("tb_compute_descriptors", st)
+    return v
+
+
+def edge_features(positions, species, box, pbc, rcut, nb: Neighbors, cmix, v, mean=None, inv_std=None,
+                  raw=True, bf16=True, stream=None):
+    b, p, bptr, pptr = _host_box(box, pbc)
+    dev = positions.device
+    xr = torch.empty((max(nb.total, 1), 32), dtype=torch.float32, device=dev) if raw else None
+    xb = torch.empty((max(nb.total, 1), 32), dtype=torch.bfloat16, device=dev) if bf16 else None
+    st = lib().tb_edge_features(_ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr),
+                                _ptr(nb.col), _ptr(nb.cnt), _ptr(cmix), _ptr(v), _ptr(mean), _ptr(inv_std),
+                                _ptr(xr), _ptr(xb), _stream(stream))
+    _check("tb_edge_features", st)
+    return (xr[:nb.total] if raw else None), (xb[:nb.total] if bf16 else None)
+
+
+def feature_stats(x_raw, n, slice_ptr, cnt, stream=None):
+    dev = x_raw.device
+    mean = torch.empty(32, dtype=torch.float32, device=dev)
+    std = torch.empty(32, dtype=torch.float32, device=dev)
+    ws = _workspace(96 * 8 * 8 * 1024, dev)
+    st = lib().tb_feature_stats(_ptr(x_raw), n, _ptr(slice_ptr), _ptr(cnt), _ptr(mean), _ptr(std), _ptr(ws),
+                                ws.numel(), _stream(stream))
+    _check("tb_feature_stats", st)
+    return mean, std
+
+
+def mlp_forward(x_bf16, model: MLPModel, stream=None):
+    E = x_bf16.shape[0]
+    y = torch.empty((E, 2), dtype=torch.float32, device=x_bf16.device)
+    st = lib().tb_mlp_forward(E, _ptr(x_bf16), _ptr(model.wb), _ptr(model.p), _ptr(y), _stream(stream))
+    _check("tb_mlp_forward", st)
+    return y
+
+
+def mlp_backward(x_bf16, model: MLPModel, dy, stream=None, workspace=None):
+    E = x_bf16.shape[0]
+    need = lib().tb_mlp_workspace_size(E)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, x_bf16.device)
+    grad = torch.empty(N_PARAM, dtype=torch.float32, device=x_bf16.device)
+    st = lib().tb_mlp_backward(E, _ptr(x_bf16), _ptr(model.wb), _ptr(model.p), _ptr(dy), _ptr(grad), _ptr(ws),
+                               ws.numel(), _stream(stream))
+    _check("tb_mlp_backward", st)
+    return grad
+
+
+def mlp_loss(row_begin, row_end, slice_ptr, cnt, y, t_hop, eps_target, species, eps0, dy, stream=None):
+    """Fills dy for the rows' elements; returns stats (device double[4])."""
+    stats = torch.empty(4, dtype=torch.float64, device=y.device)
+    ws = _workspace(3 * 8 * 2 * 1024, y.device)
+    st = lib().tb_mlp_loss(int(row_begin), int(row_end), _ptr(slice_ptr), _ptr(cnt), _ptr(y), _ptr(t_hop),
+                           _ptr(eps_target), _ptr(species), _ptr(eps0), _ptr(dy), _ptr(stats), _ptr(ws),
+                           ws.numel(), _stream(stream))
+    _check("tb_mlp_loss", st)
+    return stats
+
+
+def adamw_step(model: MLPModel, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    model.step += 1
+    st = lib().tb_adamw_step(_ptr(model.p), _ptr(grad), _ptr(model.m), _ptr(model.v), model.step, float(lr),
+                             float(beta1), float(beta2), float(eps), float(weight_decay), _ptr(model.wb),
+                             _stream(stream))
+    _check("tb_adamw_step", st)
+
+
+def build_hamiltonian(positions, species, box, pbc, rcut, nb: Neighbors, model: MLPModel, v=None,
+                      dtype=torch.float32, with_diag=True, stream=None) -> SellMatrix:
+    """Learned H (tb_build_hamiltonian) in the SELL-32 pattern of nb."""
+    L = lib()
+    dev = positions.device
+    if v is None:
+        v = compute_descriptors(positions, species, box, pbc, rcut, nb, model.cmix, stream)
+    b, p, bptr, pptr = _host_box(box, pbc)
+    val = torch.empty(max(nb.total, 1), dtype=dtype, device=dev)
+    diag = torch.empty(nb.n, dtype=dtype, device=dev) if with_diag else None
+    ws = _workspace(L.tb_build_hamiltonian_workspace_size(nb.total), dev)
+    st = L.tb_build_hamiltonian(_ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr),
+                                _ptr(nb.col), _ptr(nb.cnt), nb.total, _ptr(model.cmix), _ptr(v), _ptr(model.mean),
+                                _ptr(model.inv_std), _ptr(model.wb), _ptr(model.p), _ptr(model.eps0),
+                                precision_of(dtype), _ptr(val), _ptr(diag), _ptr(ws), ws.numel(), _stream(stream))
+    _check("tb_build_hamiltonian", st)
+    return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
