@@ -50,7 +50,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="graphene-10M-learned", choices=list(synth.WORKLOADS))
-    p.add_argument("--hamiltonian", choices=["mlp", "teacher"], default="teacher")
+    p.add_argument("--hamiltonian", choices=["mlp", "teacher"], default="mlp")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 teacher comparison run")
@@ -141,14 +141,15 @@ def hbm_peak():
 class Pipeline:
     """Holds the device-resident inputs and runs one step through the binding."""
 
-    def __init__(self, s, w, hamiltonian, rank, torch, g):
+    def __init__(self, s, w, hamiltonian, rank, torch, g, model=None):
         self.torch, self.g = torch, g
         self.s, self.w = s, w
         self.M, self.R = w["M"], w["R"]
         self.seed = synth.KPM_SEED + 1000003 * rank
         self.teacher = teacher_for(s)
         self.hamiltonian = hamiltonian
-        self.with_diag = bool(np.any(self.teacher.onsite[np.unique(s.species)] != 0.0))
+        self.model = model
+        self.teacher_diag = bool(np.any(self.teacher.onsite[np.unique(s.species)] != 0.0))
         self.pos = torch.tensor(s.positions, device="cuda")
         self.spc = torch.tensor(s.species, device="cuda")
         self.pos_host = torch.tensor(s.positions).pin_memory()
@@ -156,24 +157,30 @@ class Pipeline:
         self.kpm_ms = []
         self.last = {}
 
-    def step(self, pos, spc, dtype, record=True):
-        g, torch = self.g, self.torch
-        nb = g.build_neighbors(pos, self.s.box, self.s.pbc, self.teacher.rcut, r_count=self.teacher.r_count,
-                               max_width=16)
-        H = g.build_hamiltonian_teacher(pos, spc, self.s.box, self.s.pbc, nb, self.teacher, dtype=dtype,
-                                        with_diag=self.with_diag)
+    def step(self, pos, spc, kind, dtype, record=True, energies=None):
+        """One pass: neighbours -> H (learned or teacher) -> bounds -> KPM -> DOS."""
+        g, torch, s = self.g, self.torch, self.s
+        nb = g.build_neighbors(pos, s.box, s.pbc, self.teacher.rcut, r_count=self.teacher.r_count, max_width=16)
+        if kind == "mlp":
+            v = g.compute_descriptors(pos, spc, s.box, s.pbc, self.teacher.rcut, nb, self.model.cmix)
+            H = g.build_hamiltonian(pos, spc, s.box, s.pbc, self.teacher.rcut, nb, self.model, v=v, dtype=dtype,
+                                    with_diag=True)
+        else:
+            H = g.build_hamiltonian_teacher(pos, spc, s.box, s.pbc, nb, self.teacher, dtype=dtype,
+                                            with_diag=self.teacher_diag)
         bd = g.spectral_bounds(H, 64, synth.LANCZOS_SEED)
         timing = self.kpm_ms if record else None
         mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing)
-        E = torch.linspace(bd.emin, bd.emax, self.w["K"], dtype=torch.float64, device="cuda")
+        E = energies if energies is not None else torch.linspace(bd.emin, bd.emax, self.w["K"],
+                                                                 dtype=torch.float64, device="cuda")
         rho = g.kpm_dos(mu, bd.a, bd.b, E)
-        self.last = dict(nb=nb, H=H, bd=bd, mu=mu, rho=rho)
+        self.last = dict(nb=nb, H=H, bd=bd, mu=mu, rho=rho, E=E)
         return mu, rho
 
-    def step_e2e(self, dtype):
+    def step_e2e(self, kind, dtype):
         pos = self.pos_host.to("cuda", non_blocking=True)
         spc = self.spc_host.to("cuda", non_blocking=True)
-        mu, rho = self.step(pos, spc, dtype, record=False)
+        mu, rho = self.step(pos, spc, kind, dtype, record=False)
         return mu.cpu(), rho.cpu()
 
 
@@ -248,18 +255,28 @@ def run_ours(args):
         dist = dist_mod
     build.build()
     s, w = make_structure(args.workload, args.M, args.R)
-    pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g)
+    model, training = None, None
+    if args.hamiltonian == "mlp":
+        from paper_2509_06525_gb300 import train as tr
+        t0 = time.perf_counter()
+        model, hist = tr.train_graphene_model()
+        torch.cuda.synchronize()
+        training = {"snapshots": synth.TRAIN_SNAPSHOTS, "atoms_per_snapshot": 800,
+                    "epochs": tr.TrainConfig().epochs, "seconds": time.perf_counter() - t0,
+                    "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
+    pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g, model)
+    kind = args.hamiltonian
     lib = g.lib()
 
     # device-resident timed region
     sampler = ClockSampler(local)
     pipe.kpm_ms.clear()
     for _ in range(args.warmup):
-        pipe.step(pipe.pos, pipe.spc, torch.float32, record=False)
+        pipe.step(pipe.pos, pipe.spc, kind, torch.float32, record=False)
     torch.cuda.synchronize()
     l0 = lib.tb_launch_count()
     sampler.start()
-    ms = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, torch.float32), args.steps, 0)
+    ms = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, kind, torch.float32), args.steps, 0)
     clocks = sampler.stop()
     launches = lib.tb_launch_count() - l0
     n_atoms, M, R = s.n, w["M"], w["R"]
@@ -292,17 +309,23 @@ def run_ours(args):
         "clocks": clocks,
     }
 
-    # plain FP64 teacher form on the same structure and GPU
+    if training is not None:
+        out["training"] = training
+
+    # plain FP64 teacher form on the same structure and GPU, and the DOS
+    # error of the timed (learned FP32 by default) path against it
     if not args.no_fp64:
-        pipe.kpm_ms.clear()
-        ms64 = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, torch.float64, record=False),
-                     max(1, args.steps // 2), 1)
-        out["fp64_teacher"] = {"value": world * n_atoms * M / (ms64 * 1e-3), "ms_per_step": ms64,
-                               "speedup_of_value": (world * n_atoms * M / (ms * 1e-3)) /
-                                                   (world * n_atoms * M / (ms64 * 1e-3))}
+        rho32, E32 = pipe.last["rho"], pipe.last["E"]
+        ms64 = timed(torch, dist, lambda: pipe.step(pipe.pos, pipe.spc, "teacher", torch.float64, record=False,
+                                                    energies=E32), max(1, args.steps // 2), 1)
+        rho64 = pipe.last["rho"]
+        l1 = float((rho32 - rho64).abs().sum() / rho64.abs().sum())
+        value64 = world * n_atoms * M / (ms64 * 1e-3)
+        out["fp64_teacher"] = {"value": value64, "ms_per_step": ms64, "speedup_of_value": value / value64,
+                               "dos_l1_vs_fp64_teacher": l1}
 
     if not args.no_e2e:
-        ms_e2e = timed(torch, dist, lambda: pipe.step_e2e(torch.float32), args.steps, 1)
+        ms_e2e = timed(torch, dist, lambda: pipe.step_e2e(kind, torch.float32), args.steps, 1)
         h2d = s.positions.nbytes + s.species.nbytes
         d2h = R * M * 8 + w["K"] * 8
         out["e2e"] = {"value": world * n_atoms * M / (ms_e2e * 1e-3), "unit": UNIT,
