@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="graphene-10M-learned", choices=list(synth.WORKLOADS))
     p.add_argument("--hamiltonian", choices=["mlp", "teacher"], default="mlp")
+    p.add_argument("--kpm", choices=["doubling", "direct"], default="doubling",
+                   help="moment formation: doubling identities (about M/2 steps) or one step per moment")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 teacher comparison run")
@@ -141,7 +143,7 @@ def hbm_peak():
 class Pipeline:
     """Holds the device-resident inputs and runs one step through the binding."""
 
-    def __init__(self, s, w, hamiltonian, rank, torch, g, model=None):
+    def __init__(self, s, w, hamiltonian, rank, torch, g, model=None, doubling=True):
         self.torch, self.g = torch, g
         self.s, self.w = s, w
         self.M, self.R = w["M"], w["R"]
@@ -156,6 +158,7 @@ class Pipeline:
         self.spc_host = torch.tensor(s.species).pin_memory()
         self.kpm_ms = []
         self.last = {}
+        self.doubling = doubling
 
     def step(self, pos, spc, kind, dtype, record=True, energies=None):
         """One pass: neighbours -> H (learned or teacher) -> bounds -> KPM -> DOS."""
@@ -170,7 +173,7 @@ class Pipeline:
                                             with_diag=self.teacher_diag)
         bd = g.spectral_bounds(H, 64, synth.LANCZOS_SEED)
         timing = self.kpm_ms if record else None
-        mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing)
+        mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing, doubling=self.doubling)
         E = energies if energies is not None else torch.linspace(bd.emin, bd.emax, self.w["K"],
                                                                  dtype=torch.float64, device="cuda")
         rho = g.kpm_dos(mu, bd.a, bd.b, E)
@@ -264,7 +267,7 @@ def run_ours(args):
         training = {"snapshots": synth.TRAIN_SNAPSHOTS, "atoms_per_snapshot": 800,
                     "epochs": tr.TrainConfig().epochs, "seconds": time.perf_counter() - t0,
                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
-    pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g, model)
+    pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g, model, doubling=args.kpm == "doubling")
     kind = args.hamiltonian
     lib = g.lib()
 
@@ -286,8 +289,10 @@ def run_ours(args):
     nb, H = pipe.last["nb"], pipe.last["H"]
     nnz = int(nb.cnt.sum().item())
     sv, sc = 4, 8
-    step_bytes = nnz * (sv + 4) + (n_atoms * sv if H.diag is not None else 0) + n_atoms * R * 4 * sc
-    launch_ms = sum(pipe.kpm_ms) / (len(pipe.kpm_ms) * (M - 1))
+    streams = 3 if pipe.doubling else 4      # x gathered once, v_{n-1}, v_{n+1} (+ v0 when direct)
+    step_bytes = nnz * (sv + 4) + (n_atoms * sv if H.diag is not None else 0) + n_atoms * R * streams * sc
+    launches_per_kpm = (M - 1) // 2 + 1 if pipe.doubling else M - 1
+    launch_ms = sum(pipe.kpm_ms) / (len(pipe.kpm_ms) * launches_per_kpm)
     achieved = step_bytes / (launch_ms * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
     kpm_frac_of_step = sum(pipe.kpm_ms) / (ms * args.steps)
@@ -299,10 +304,12 @@ def run_ours(args):
         "config": {"workload": args.workload + ("" if (args.M is None and args.R is None) else "-override"),
                    "atoms": n_atoms, "moments": M, "random_vectors": R,
                    "hamiltonian": args.hamiltonian, "kpm_precision": "complex FP32, FP64 moment sums",
+                   "kpm_moments": ("doubling identities, %d Chebyshev steps" % launches_per_kpm
+                                   if pipe.doubling else "direct, %d Chebyshev steps" % launches_per_kpm),
                    "l2": "inputs larger than L2 (ELL and vector blocks >> 126 MB)",
                    "step": "neighbours + H build + FP64 bounds + KPM + Jackson DOS"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "cheb_step_kernel",
+                     "frac": achieved / peak, "traffic": None, "kernel": "cheb_step (fused Chebyshev step + moment dots)",
                      "bytes_per_launch": step_bytes, "launch_ms": launch_ms, "peak_source": peak_src,
                      "kpm_share_of_step": kpm_frac_of_step},
         "gpu_launches": launches,

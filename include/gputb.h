@@ -65,10 +65,16 @@ typedef int32_t tb_status;
 #define TB_ERR_ELL_OVERFLOW   5   /* a row has more neighbours than allowed  */
 #define TB_ERR_BOUNDS         6   /* |mu_n| > 1 + 1e-6: spectrum outside [-1,1] after rescaling */
 #define TB_ERR_NOT_FINITE     7   /* NaN/Inf met in an input or result       */
+#define TB_ERR_TIMEOUT        8   /* a bounded device-side wait gave up      */
 
 /* precision of Hamiltonian values and KPM vectors */
 #define TB_F32 0
 #define TB_F64 1
+
+/* how kpm_moments forms the moments */
+#define TB_KPM_DIRECT   0   /* mu_n = Re<v0|v_n>/N, one step per moment           */
+#define TB_KPM_DOUBLING 1   /* mu_2k = 2<v_k|v_k>/N - mu_0, mu_2k+1 = 2 Re<v_k|v_k+1>/N - mu_1:
+                               about M/2 steps and no v0 stream (Weisse et al. 2006) */
 
 /* KPM damping kernels (Weisse et al., Rev. Mod. Phys. 78, 275 (2006)) */
 #define TB_KERNEL_JACKSON 0
@@ -94,7 +100,10 @@ TB_API int64_t tb_launch_count(void);
  *     u(seed, r, i) = (splitmix64(seed ^ splitmix64(r * 2^32 + i)) >> 11) * 2^-53
  * and splitmix64 is one output of SplitMix64 from state x (Steele, Lea &
  * Flood 2014).  T_n(H~) v0 uses the recursion v1 = H~ v0,
- * v_{n+1} = 2 H~ v_n - v_{n-1}.  Vector arithmetic is in `precision`
+ * v_{n+1} = 2 H~ v_n - v_{n-1}.  With mode TB_KPM_DOUBLING the same moments
+ * come from the product identities T_2k = 2 T_k^2 - T_0 and
+ * T_2k+1 = 2 T_k T_k+1 - T_1 applied to the vectors (equal in exact
+ * arithmetic), which needs only about M/2 steps.  Vector arithmetic is in `precision`
  * (TB_F32: complex FP32, TB_F64: complex FP64); every moment partial sum is
  * accumulated in FP64 and reduced in a fixed order (bitwise reproducible).
  *
@@ -107,19 +116,29 @@ TB_API int64_t tb_launch_count(void);
  *   a, b         rescaling H~ = (H - b)/a; a > 0
  *   M            moments (>= 2);  R  vectors: 1, 2, 4, 8, 16 or 32
  *   seed         random-phase seed
+ *   mode         TB_KPM_DIRECT or TB_KPM_DOUBLING
  *   mu_r         device double [R*M] output (vector r, moment n at r*M+n)
  *   workspace    >= kpm_moments_workspace_size(n, M, R, precision) bytes
  *   step_ms      host double or NULL: if given, receives the CUDA-event time
  *                (ms) of the M-1 Chebyshev-step launches on `stream`
  * Synchronises `stream`, then checks |mu_r| <= 1 + 1e-6 (TB_ERR_BOUNDS)
- * and finiteness (TB_ERR_NOT_FINITE).
+ * and finiteness (TB_ERR_NOT_FINITE).  The pipelined step kernel bounds
+ * every wait on its copy barriers and reports TB_ERR_TIMEOUT if one gives
+ * up.  col and val must be 16-byte aligned.
  * ------------------------------------------------------------------- */
 TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_t precision);
+
+/* Tuning hook for the Chebyshev-step kernel used by kpm_moments and
+ * kpm_moments_noalloc: 0 = automatic (the bulk-copy pipeline wherever its
+ * tile geometry fits, else direct loads), 1 = direct loads, 2 = pipeline
+ * where it fits.  Process-wide; both variants compute the same result.
+ * Query workspace sizes after setting it. */
+TB_API tb_status tb_kpm_set_variant(int32_t variant);
 
 TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col,
                       const void *val, const void *diag, int32_t precision,
                       double a, double b, int32_t M, int32_t R, uint64_t seed,
-                      double *mu_r, void *workspace, size_t workspace_bytes,
+                      int32_t mode, double *mu_r, void *workspace, size_t workspace_bytes,
                       void *stream, double *step_ms);
 
 /* ---------------------------------------------------------------------
@@ -130,8 +149,8 @@ TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t 
  * moments: code inside a framework that owns the device memory pool,
  * latency-critical loops where cudaMalloc would synchronise the device, or
  * plug-ins that are handed only their input and output buffers.  Same
- * arguments, results and checks as kpm_moments, minus the workspace and the
- * timing output: the scratch lives in a static 32 MiB device array inside the
+ * arguments, results and checks as kpm_moments in TB_KPM_DIRECT mode, minus
+ * the mode, the workspace and the timing output: the scratch lives in a static 32 MiB device array inside the
  * library, which every GPU that loads the library keeps until the process
  * exits.  Sizes whose kpm_moments_workspace_size exceeds 32 MiB are rejected
  * with TB_ERR_WORKSPACE (use kpm_moments with a caller workspace instead).

@@ -25,6 +25,7 @@ TB_ERR_BOX = 4
 TB_ERR_ELL_OVERFLOW = 5
 TB_ERR_BOUNDS = 6
 TB_ERR_NOT_FINITE = 7
+TB_ERR_TIMEOUT = 8
 
 F32, F64 = 0, 1
 KERNELS = {"jackson": 0, "lorentz": 1, "none": 2}
@@ -38,8 +39,9 @@ SIGNATURES = {
     "tb_last_error": (ctypes.c_char_p, []),
     "kpm_moments_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
     "tb_launch_count": (_c_i64, []),
+    "tb_kpm_set_variant": (_c_i32, [_c_i32]),
     "kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32,
-                             _c_u64, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
+                             _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_moments_noalloc": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32,
                                      _c_i32, _c_u64, _c_vp, _c_vp]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
@@ -143,9 +145,12 @@ class SellMatrix:
         return precision_of(self.val.dtype)
 
 
+KPM_DIRECT, KPM_DOUBLING = 0, 1
+
+
 def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
-                stream=None, workspace: Optional[torch.Tensor] = None, timing: Optional[list] = None
-                ) -> torch.Tensor:
+                stream=None, workspace: Optional[torch.Tensor] = None, timing: Optional[list] = None,
+                doubling: bool = False) -> torch.Tensor:
     """Per-vector KPM moments mu_r [R, M] (float64, device).
 
     If `timing` is a list, the CUDA-event time (ms) of the Chebyshev-step
@@ -160,12 +165,17 @@ def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
     step_ms = ctypes.c_double(0.0)
     st = L.kpm_moments(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), prec,
                        float(a), float(b), int(M), int(R), int(seed) & ((1 << 64) - 1),
-                       _ptr(mu), _ptr(ws), ws.numel(), _stream(stream),
+                       KPM_DOUBLING if doubling else KPM_DIRECT, _ptr(mu), _ptr(ws), ws.numel(), _stream(stream),
                        ctypes.byref(step_ms) if timing is not None else None)
     _check("kpm_moments", st)
     if timing is not None:
         timing.append(step_ms.value)
     return mu
+
+
+def kpm_set_variant(variant: int):
+    """0 = automatic, 1 = direct-load Chebyshev step, 2 = bulk-copy pipeline."""
+    _check("tb_kpm_set_variant", lib().tb_kpm_set_variant(int(variant)))
 
 
 def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel: str = "jackson",

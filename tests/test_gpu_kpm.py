@@ -38,6 +38,20 @@ def gputb():
     return g
 
 
+@pytest.fixture(params=[1, 2], ids=["direct", "pipelined"])
+def variant(request, gputb):
+    gputb.kpm_set_variant(request.param)
+    yield request.param
+    gputb.kpm_set_variant(0)
+
+
+@pytest.fixture(params=[False, True], ids=["plain", "doubling"])
+def doubling(request):
+    """Moment doubling (mu_2k, mu_2k+1 from <v_k|v_k>, <v_k|v_k+1>) must give
+    the oracle's directly defined moments within the same tolerances."""
+    return request.param
+
+
 @pytest.fixture(scope="module")
 def cfg800():
     w = synth.WORKLOADS["graphene-800-fp64"]
@@ -48,23 +62,33 @@ def cfg800():
     return s, indptr, idx, t, eps, H, a, b, w
 
 
-def test_fp64_moments_match_oracle(gputb, cfg800):
+def test_fp64_moments_match_oracle(gputb, cfg800, variant, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
     Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
-    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED, doubling=doubling).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
     # bitwise reproducible
-    mu2 = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    mu2 = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED, doubling=doubling).cpu().numpy()
     assert np.array_equal(mu, mu2)
 
 
-def test_fp32_moments_match_oracle(gputb, cfg800):
+@pytest.mark.parametrize("M", [2, 3, 4, 511])
+def test_doubling_odd_and_tiny_moment_counts(gputb, cfg800, M):
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, M, 2, 11, doubling=True).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, M, 2, 11)
+    assert mu.shape == (2, M)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+
+
+def test_fp32_moments_match_oracle(gputb, cfg800, variant, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
     Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float32)
-    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED).cpu().numpy()
+    mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED, doubling=doubling).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F32
 
@@ -89,11 +113,13 @@ def test_dos_matches_oracle(gputb, cfg800):
                                    rtol=1e-9, atol=1e-11)
 
 
+
+
 @pytest.mark.parametrize("R", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_all_block_widths_ragged_rows(gputb, R, dtype):
+def test_all_block_widths_ragged_rows(gputb, R, dtype, variant, doubling):
     """Ragged N (not a multiple of 32), an h-BN junction with onsite terms
-    (diag present), every supported R."""
+    (diag present), every supported R, both Chebyshev-step kernels."""
     s = synth.hbn_graphene_junction(6, 7, sigma=0.1, seed=9)   # 168 atoms
     s.positions = s.positions[:-5].copy()                          # ragged, still periodic-valid
     s.species = s.species[:-5].copy()
@@ -103,14 +129,14 @@ def test_all_block_widths_ragged_rows(gputb, R, dtype):
     _, _, a, b = obo.spectral_bounds(H, 64, 7)
     M = 96
     Hd = sell_matrix(indptr, idx, t, eps, s.n, dtype)
-    mu = gputb.kpm_moments(Hd, a, b, M, R, 1234).cpu().numpy()
+    mu = gputb.kpm_moments(Hd, a, b, M, R, 1234, doubling=doubling).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, M, R, 1234)
     tol = TOL_F64 if dtype == torch.float64 else TOL_F32
     assert np.max(np.abs(mu - mu_ref)) <= tol
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 33])
-def test_tiny_systems(gputb, n):
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 300])
+def test_tiny_systems(gputb, n, variant):
     rng = np.random.default_rng(n)
     dense = np.zeros((n, n))
     if n > 1:
@@ -135,3 +161,24 @@ def test_bounds_violation_reported(gputb, cfg800):
     with pytest.raises(gputb.GputbError) as ei:
         gputb.kpm_moments(Hd, 0.3 * a, b, 256, 1, 1)
     assert ei.value.status in (gputb.TB_ERR_BOUNDS, gputb.TB_ERR_NOT_FINITE)
+
+
+def test_wide_rows_fall_back_inside_the_pipeline(gputb, variant):
+    """Rows wider than the pipeline's 16-slot tile budget (dense random
+    pattern, 40 neighbours per row) take the direct-load path per tile."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(3)
+    n = 700
+    A = sp.random(n, n, density=40 / n, random_state=rng, format="csr")
+    A = A + A.T
+    A.setdiag(0)
+    A.eliminate_zeros()
+    A = A.tocsr()
+    A.sort_indices()
+    onsite = rng.uniform(-0.3, 0.3, n)
+    H = oha.csr_hamiltonian(n, A.indptr, A.indices, A.data, onsite)
+    _, _, a, b = obo.spectral_bounds(H, 64, 7)
+    Hd = sell_matrix(A.indptr, A.indices, A.data, onsite, n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, 64, 8, 77).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, 64, 8, 77)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
