@@ -56,6 +56,8 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 teacher comparison run")
+    p.add_argument("--train-epochs", type=int, default=None,
+                   help="epochs of the untimed model training (default: the training default); fewer for profiling")
     p.add_argument("--M", type=int, default=None, help="override the workload's moment count (profiling)")
     p.add_argument("--R", type=int, default=None, help="override the workload's vector count (profiling)")
     return p.parse_args()
@@ -262,10 +264,11 @@ def run_ours(args):
     if args.hamiltonian == "mlp":
         from paper_2509_06525_gb300 import train as tr
         t0 = time.perf_counter()
-        model, hist = tr.train_graphene_model()
+        cfg = tr.TrainConfig() if args.train_epochs is None else tr.TrainConfig(epochs=args.train_epochs)
+        model, hist = tr.train_graphene_model(cfg=cfg)
         torch.cuda.synchronize()
         training = {"snapshots": synth.TRAIN_SNAPSHOTS, "atoms_per_snapshot": 800,
-                    "epochs": tr.TrainConfig().epochs, "seconds": time.perf_counter() - t0,
+                    "epochs": cfg.epochs, "seconds": time.perf_counter() - t0,
                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
     pipe = Pipeline(s, w, args.hamiltonian, rank, torch, g, model, doubling=args.kpm == "doubling")
     kind = args.hamiltonian

@@ -31,7 +31,8 @@
  *     slice_ptr[i / 32] + s * 32 + (i % 32),       0 <= s < w_(i/32).
  * col (int32) and the values share this layout.  Within a row the occupied
  * slots hold the neighbours j in ascending order; padding slots hold
- * col = i and value 0 (rows i >= N of the last slice hold col = 0).
+ * col = i and value 0 (rows i >= N of the last slice hold col = 0 and
+ * value 0).
  *
  * Boxes: box is 9 host doubles, row k = lattice vector a_k, in the lower-
  * triangular form a1 = (ax,0,0), a2 = (bx,by,0), a3 = (cx,cy,cz) with
@@ -167,6 +168,38 @@ TB_API tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, const 
                                      const void *val, const void *diag, int32_t precision,
                                      double a, double b, int32_t M, int32_t R, uint64_t seed,
                                      double *mu_r, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Batched KPM over many uneven snapshots (multi-frame averaging of the
+ * LSQT calculation, Sec. 2.4), one CUDA-graph launch for all of them.
+ *
+ * Snapshot s (0 <= s < n_snap) is a SELL-32 Hamiltonian with n_rows[s]
+ * rows given by the device pointers slice_ptr[s], col[s], val[s], diag[s]
+ * (diag[s] may be NULL; the pointer arrays themselves are host arrays), with
+ * its own rescaling (a[s], b[s]) (host arrays).  Its moments are those of
+ * kpm_moments(H_s, a[s], b[s], M, R, seed + s, mode): random phases of
+ * snapshot s use seed + s and the snapshot's own row numbers.  The call
+ * folds every (a[s], b[s]) into a block-diagonal copy of the matrices in the
+ * workspace (snapshots padded to 256-row tiles), runs the shared Chebyshev
+ * step kernels with one moment partial per row block, and captures the
+ * whole recursion as a CUDA graph launched on `stream`.  The workspace-size
+ * query reads each snapshot's element count from its slice_ptr and
+ * synchronises `stream`.
+ *   mu         device double [n_snap][R][M] output
+ *   graph_ms   host double or NULL: CUDA-event time of the graph launch
+ * Synchronises `stream`; TB_ERR_BOUNDS / TB_ERR_NOT_FINITE as kpm_moments.
+ * ------------------------------------------------------------------- */
+TB_API size_t kpm_moments_batched_workspace_size(int32_t n_snap, const int64_t *const *slice_ptr,
+                                                 const int64_t *n_rows, int32_t M, int32_t R,
+                                                 int32_t precision, void *stream);
+
+TB_API tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows,
+                                     const int64_t *const *slice_ptr, const int32_t *const *col,
+                                     const void *const *val, const void *const *diag,
+                                     int32_t precision, const double *a, const double *b,
+                                     int32_t M, int32_t R, uint64_t seed, int32_t mode, double *mu,
+                                     void *workspace, size_t workspace_bytes, void *stream,
+                                     double *graph_ms);
 
 /* ---------------------------------------------------------------------
  * KPM density of states, Eq. 4, per orbital per eV (integrates to 1):

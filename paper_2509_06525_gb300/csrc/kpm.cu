@@ -24,100 +24,32 @@
 //   in a fixed order by a final kernel: results are bitwise reproducible.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
-#include "common.cuh"
+#include "kpm_common.cuh"
 
 namespace gputb {
 namespace {
+using namespace kpmdev;
 
-constexpr int kBlock = 256;
-constexpr int kWarps = kBlock / 32;
+// Batch description (device tables) for kpm_moments_batched: rows of
+// snapshot s occupy [row0[s], row0[s] + padded) of the concatenated blocks,
+// the first rows[s] of them real; tile_snap maps each 256-row tile to its
+// snapshot.
+struct BatchTables {
+  const int32_t *tile_snap = nullptr;
+  const int64_t *row0 = nullptr;
+  const int64_t *rows = nullptr;
+  int n_snap = 0;
+};
+constexpr int kBatchTile = 256;
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-  uint64_t z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ double phase_uniform(uint64_t seed, uint64_t r, uint64_t i) {
-  const uint64_t z = splitmix64(seed ^ splitmix64((r << 32) + i));
-  return static_cast<double>(z >> 11) * 0x1.0p-53;
-}
-
-// Each thread moves CPT complex numbers of one row: one 8-byte access
-// (FP32, CPT = 1) or CPT*8/16 (FP32) / CPT (FP64) 16-byte accesses.
-template <typename real, int CPT> struct Vec { using T = float4; static constexpr int kChunks = CPT / 2; };
-template <> struct Vec<float, 1> { using T = float2; static constexpr int kChunks = 1; };
-template <int CPT> struct Vec<double, CPT> { using T = double2; static constexpr int kChunks = CPT; };
-
-// read-only cached load (neighbour gathers)
-template <typename real, int CPT>
-__device__ __forceinline__ void ld_gather(const real *p, real (&o)[2 * CPT]) {
-  using V = typename Vec<real, CPT>::T;
-#pragma unroll
-  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
-    V t = __ldg(reinterpret_cast<const V *>(p) + k);
-    memcpy(o + k * (sizeof(V) / sizeof(real)), &t, sizeof(V));
-  }
-}
-// streaming load / store (each element touched once per step)
-template <typename real, int CPT>
-__device__ __forceinline__ void ld_stream(const real *p, real (&o)[2 * CPT]) {
-  using V = typename Vec<real, CPT>::T;
-#pragma unroll
-  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
-    V t = __ldcs(reinterpret_cast<const V *>(p) + k);
-    memcpy(o + k * (sizeof(V) / sizeof(real)), &t, sizeof(V));
-  }
-}
-template <typename real, int CPT>
-__device__ __forceinline__ void st_stream(real *p, const real (&v)[2 * CPT]) {
-  using V = typename Vec<real, CPT>::T;
-#pragma unroll
-  for (int k = 0; k < Vec<real, CPT>::kChunks; ++k) {
-    V t;
-    memcpy(&t, v + k * (sizeof(V) / sizeof(real)), sizeof(V));
-    __stcs(reinterpret_cast<V *>(p) + k, t);
-  }
-}
-
-// acc + Re(conj(a) b) for complex a = (ar, ai), b = (br, bi): FP32 products
-// summed into the FP64 accumulator (FP64 arithmetic for FP64 vectors)
-template <typename real>
-__device__ __forceinline__ double dot_acc(real ar, real ai, real br, real bi, double acc) {
-  if (sizeof(real) == 4) return acc + (double)fmaf((float)ar, (float)br, (float)ai * (float)bi);
-  return fma((double)ar, (double)br, fma((double)ai, (double)bi, acc));
-}
-
-// Sum acc over all rows of the CTA for each of the R vectors and write the
-// CTA's R partials.  Lanes that share `part` (lane mod TPR) hold the same
-// vector components.
-template <int R, int CPT>
-__device__ __forceinline__ void cta_partial(double (&acc)[CPT], double *out) {
-  constexpr int TPR = R / CPT;
-  __shared__ double red[kWarps][R];
-#pragma unroll
-  for (int off = 16; off >= TPR; off >>= 1)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane < TPR)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) red[warp][lane * CPT + c] = acc[c];
-  __syncthreads();
-  if (threadIdx.x < R) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-}
-
-// v0[i, r] = exp(2 pi i u(seed, r, i)); partial of mu_0 = Re <v0|v0>.
-template <typename real, int R, int CPT>
-__global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_t seed, real *__restrict__ v0,
-                                                              double *__restrict__ partial) {
+// v0[i, r] = exp(2 pi i u(seed, r, i)) (batched: u(seed + s, r, i - row0[s])
+// on the real rows of snapshot s, 0 on padding rows); partials of
+// Re <v0|v0> per CTA, or per RPB-row block when SEG.
+template <typename real, int R, int CPT, bool SEG>
+__global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_t seed, BatchTables bt,
+                                                              real *__restrict__ v0, double *__restrict__ partial) {
   constexpr int TPR = R / CPT;
   constexpr int RPB = kBlock / TPR;
   const int part = threadIdx.x % TPR;
@@ -127,21 +59,38 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
   for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < n; row0 += (int64_t)gridDim.x * RPB) {
     const int64_t i = row0 + threadIdx.x / TPR;
     if (i < n) {
+      uint64_t sd = seed;
+      int64_t li = i;
+      bool real_row = true;
+      if (bt.tile_snap) {
+        const int s = bt.tile_snap[i / kBatchTile];
+        sd = seed + (uint64_t)s;
+        li = i - bt.row0[s];
+        real_row = li < bt.rows[s];
+      }
       real v[2 * CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         const int r = part * CPT + c;
-        const double phi = 2.0 * M_PI * phase_uniform(seed, (uint64_t)r, (uint64_t)i);
-        double s, co;
-        sincos(phi, &s, &co);
+        double sn = 0.0, co = 0.0;
+        if (real_row) {
+          const double phi = 2.0 * M_PI * phase_uniform(sd, (uint64_t)r, (uint64_t)li);
+          sincos(phi, &sn, &co);
+        }
         v[2 * c] = static_cast<real>(co);
-        v[2 * c + 1] = static_cast<real>(s);
+        v[2 * c + 1] = static_cast<real>(sn);
         acc[c] += (double)v[2 * c] * (double)v[2 * c] + (double)v[2 * c + 1] * (double)v[2 * c + 1];
       }
       st_stream<real, CPT>(v0 + (i * R + part * CPT) * 2, v);
     }
+    if (SEG) {
+      cta_partial<R, CPT>(acc, partial + (row0 / RPB) * R);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) acc[c] = 0.0;
+    }
   }
-  cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
+  if (!SEG) cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
 }
 
 // One Chebyshev step over all rows:
@@ -156,19 +105,67 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
 // a plain loop.
 constexpr int kFastW = 16;
 
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL>
+// Write the CTA's partial sums as entry `idx` of the moment slot (and of the
+// next slot for the doubling pair), then restart the accumulators.  Every
+// thread of the CTA must call it.
+template <typename real, int R, int CPT, bool DBL>
+__device__ __forceinline__ void flush_partials(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
+                                               double *partial, int64_t idx, int64_t slot_stride) {
+  double sum[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) sum[c] = acc[c].value();
+  cta_partial<R, CPT>(sum, partial + idx * R);
+  __syncthreads();
+  if (DBL) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) sum[c] = acc2[c].value();
+    cta_partial<R, CPT>(sum, partial + slot_stride + idx * R);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
+}
+
+// Segmented mode: block `blk` of the current run of RPB-row blocks has just
+// been processed.  Every block of the run except its first gets zeros; when
+// the next block of this CTA starts another snapshot (or there is none) the
+// run's sums go into the entry of the run's first block.  Uniform across the
+// CTA.
+template <typename real, int R, int CPT, bool DBL>
+__device__ __forceinline__ void segment_boundary(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
+                                                 double *partial, int64_t slot_stride, const BatchTables &bt,
+                                                 int64_t blk, int rpb, int64_t blk_end, int64_t &run_head) {
+  const int64_t nxt = blk + 1;
+  const bool ends = nxt >= blk_end || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
+  if (blk != run_head && threadIdx.x < R) {  // every block but the run's first holds zero
+    partial[blk * R + threadIdx.x] = 0.0;
+    if (DBL) partial[slot_stride + blk * R + threadIdx.x] = 0.0;
+  }
+  if (ends) {
+    flush_partials<real, R, CPT, DBL>(acc, acc2, partial, run_head, slot_stride);
+    run_head = nxt;
+  }
+}
+
+template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 3) cheb_step_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x,
     const real *prev, const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha,
-    real shift) {
+    real shift, int64_t slot_stride, BatchTables bt) {
   constexpr int TPR = R / CPT;
   constexpr int RPB = kBlock / TPR;
   const int part = threadIdx.x % TPR;
-  double acc[CPT], acc2[CPT];
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = 0.0;
-  for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < n; row0 += (int64_t)gridDim.x * RPB) {
+  DotAcc<real> acc[CPT], acc2[CPT];
+  // SEG (batched): each CTA takes a contiguous run of blocks and reduces
+  // only where the snapshot changes; other blocks' entries are zero
+  const int64_t nblk = (n + RPB - 1) / RPB;
+  const int64_t b_first = SEG ? nblk * blockIdx.x / gridDim.x : blockIdx.x;
+  const int64_t b_last = SEG ? nblk * (blockIdx.x + 1) / gridDim.x : nblk;
+  const int64_t b_step = SEG ? 1 : gridDim.x;
+  int64_t run_head = b_first;
+  for (int64_t blk = b_first; blk < b_last; blk += b_step) {
+    const int64_t row0 = blk * RPB;
     const int64_t i = row0 + threadIdx.x / TPR;
     if (i < n) {
       const int64_t off = (i * R + part * CPT) * 2;
@@ -224,21 +221,18 @@ __global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 3
         // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-          acc[c] = dot_acc<real>(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1], acc[c]);
-          acc2[c] = dot_acc<real>(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1], acc2[c]);
+          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
+          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
         }
       } else {
         // Re(conj(v0) * o) = z.re o.re + z.im o.im
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = dot_acc<real>(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1], acc[c]);
+        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
       }
     }
+    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head);
   }
-  cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
-  if (DBL) {
-    __syncthreads();
-    cta_partial<R, CPT>(acc2, partial + (int64_t)gridDim.x * R + (int64_t)blockIdx.x * R);
-  }
+  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,12 +294,12 @@ struct BulkGeom {
   static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024;
 };
 
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL>
+template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
-    int *__restrict__ flags) {
+    int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
   using G = BulkGeom<real, valT, R, CPT>;
   constexpr int TPR = G::TPR, TR = G::TR;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -322,6 +316,10 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
+  // tiles of this CTA: grid-stride, or one contiguous run in SEG mode
+  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
+  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
+  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(full + st, 1);
@@ -331,7 +329,7 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
 
   // producer: stream the operands of local tile number kk into its stage
   auto issue = [&](int64_t kk) {
-    const int64_t tile = blockIdx.x + kk * gridDim.x;
+    const int64_t tile = tile_of(kk);
     const int st = static_cast<int>(kk % kStages);
     const int64_t r0 = tile * TR;
     const int64_t k0 = r0 >> 5;
@@ -352,14 +350,14 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
     if (!DBL) bulk_g2s(s_v0(st), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
   };
 
-  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t my_tiles =
+      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  int64_t run_head = t_begin;
   int64_t issued = 0;
   if (threadIdx.x == 0)
     for (; issued < my_tiles && issued < kStages; ++issued) issue(issued);
 
-  double acc[CPT], acc2[CPT];
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = 0.0;
+  DotAcc<real> acc[CPT], acc2[CPT];
   bool ok = true;
   int64_t kk = 0;
   for (; kk < my_tiles; ++kk) {
@@ -367,7 +365,7 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
     const uint32_t parity = static_cast<uint32_t>((kk / kStages) & 1);
     ok = __syncthreads_and(mbar_wait_bounded(full + st, parity)) != 0;
     if (!ok) break;
-    const int64_t tile = blockIdx.x + kk * gridDim.x;
+    const int64_t tile = tile_of(kk);
     const int64_t r0 = tile * TR;
     const int64_t i = r0 + lr;
     if (i < n) {
@@ -422,15 +420,16 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
         // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-          acc[c] = dot_acc<real>(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1], acc[c]);
-          acc2[c] = dot_acc<real>(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1], acc2[c]);
+          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
+          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
         }
       } else {
         // Re(conj(v0) * o) = z.re o.re + z.im o.im
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = dot_acc<real>(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1], acc[c]);
+        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
       }
     }
+    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x == 0 && issued < my_tiles) issue(issued++);
   }
@@ -443,13 +442,9 @@ __global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = 0.0;
+    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
   }
-  cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
-  if (DBL) {
-    __syncthreads();
-    cta_partial<R, CPT>(acc2, partial + (int64_t)gridDim.x * R + (int64_t)blockIdx.x * R);
-  }
+  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
 
 // mu_r[r, m] = (sum over CTAs in index order of partial[m, cta, r]) / n;
@@ -480,6 +475,32 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 // 1 = direct loads, 2 = bulk-copy pipeline (set with tb_kpm_set_variant)
 int g_kpm_variant = 0;
 
+// batched: mu[s][r][m] from the RPB-row block partials of snapshot s (block order)
+__global__ void batched_reduce_kernel(BatchTables bt, int M, int R, int rpb, int64_t nblk,
+                                      const double *__restrict__ partial, int doubling, double *__restrict__ mu,
+                                      int *__restrict__ flags) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)bt.n_snap * R * M) return;
+  const int m = static_cast<int>(t % M);
+  const int r = static_cast<int>((t / M) % R);
+  const int s = static_cast<int>(t / ((int64_t)M * R));
+  const int64_t rows = bt.rows[s];
+  const int64_t b0 = bt.row0[s] / rpb;
+  const int64_t b1 = (bt.row0[s] + (rows + kBatchTile - 1) / kBatchTile * kBatchTile) / rpb;
+  const double inv_n = 1.0 / (double)rows;
+  auto slot = [&](int k) {
+    const double *p = partial + (int64_t)k * nblk * R + r;
+    double acc = 0.0;
+    for (int64_t q = b0; q < b1; ++q) acc += p[q * R];
+    return acc * inv_n;
+  };
+  double v = slot(m);
+  if (doubling && m >= 2) v = 2.0 * v - slot(m & 1);
+  mu[t] = v;
+  if (!isfinite(v)) atomicOr(flags, 2);
+  else if (fabs(v) > 1.0 + 1e-6) atomicOr(flags, 1);
+}
+
 template <typename real, typename valT, int R>
 struct KpmRunner {
   // complex numbers per thread, chosen by measurement on GB300 (10M-atom
@@ -503,9 +524,9 @@ struct KpmRunner {
     if (use_bulk()) {
       if (per_sm_bulk == 0) {
         int b = 0;
-        cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false>,
+        cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
                                                           kBlock, G::kSmem) != cudaSuccess ||
             b <= 0)
           b = 1;
@@ -517,7 +538,7 @@ struct KpmRunner {
     }
     if (per_sm_direct == 0) {
       int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_kernel<real, valT, R, CPT, false, false>, kBlock, 0) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_kernel<real, valT, R, CPT, false, false, false>, kBlock, 0) !=
               cudaSuccess ||
           b <= 0)
         b = 4;
@@ -529,29 +550,110 @@ struct KpmRunner {
   }
 
   static int64_t padded_rows(int64_t n) { return (n + kRowPad - 1) / kRowPad * kRowPad; }
+  static int64_t blocks(int64_t n) { return (n + RPB - 1) / RPB; }   // RPB == G::TR
 
-  static size_t workspace(int64_t n, int M) {
+  static size_t workspace(int64_t n, int M, bool segmented) {
     Carver cv(nullptr, 0);
     for (int k = 0; k < 3; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
-    cv.take<double>((size_t)(M + 1) * grid_for(n) * R);
+    cv.take<double>((size_t)(M + 1) * (segmented ? blocks(n) : grid_for(n)) * R);
     cv.take<int>(4);
     return cv.used + 256;
   }
 
-  template <bool FIRST, bool DBL>
+  // opt every pipelined instantiation into its shared-memory size (before any
+  // stream capture)
+  static void prepare() {
+    if (!use_bulk()) return;
+    const int sm = (int)G::kSmem;
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  }
+
+  template <bool FIRST, bool DBL, bool SEG>
   static tb_status step(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                         const valT *diag, const real *x, const real *prev, const real *v0, real *out,
-                        double *partial, real alpha, real shift, int *flags, cudaStream_t st) {
-    if (use_bulk()) {
-      cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
-      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL><<<grid, kBlock, G::kSmem, st>>>(
-          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags);
+                        double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
+                        const BatchTables &bt, cudaStream_t st) {
+    if (use_bulk())
+      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, G::kSmem, st>>>(
+          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt);
+    else
+      cheb_step_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
+          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
+    TB_CHECK_LAUNCH();
+    return TB_OK;
+  }
+
+  // The whole recursion: random phases, the Chebyshev steps, the reduction.
+  template <bool SEG>
+  static tb_status enqueue(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
+                           const valT *diag, double a, double b, int M, uint64_t seed, bool dbl, double *mu_r,
+                           real *v0, real *A, real *B, double *partial, int *flags, const BatchTables &bt,
+                           cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+    const int64_t units = SEG ? blocks(n) : grid;   // partials per moment slot
+    const int64_t ps = units * R;
+    TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+    random_phase_kernel<real, R, CPT, SEG><<<grid, kBlock, 0, st>>>(n, seed, bt, v0, partial);
+    TB_CHECK_LAUNCH();
+    if (ev_begin) TB_CUDA(cudaEventRecord(ev_begin, st));
+    // v1 = H~ v0 -> A.  Direct mode: the step making v_m adds the partials of
+    // mu_m; doubling mode: the step reading v_k adds those of S_2k and S_2k+1.
+    const real shift = static_cast<real>(b);
+    const real inv_a = static_cast<real>(1.0 / a);
+    tb_status s = dbl ? step<true, true, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial, inv_a,
+                                              shift, flags, ps, bt, st)
+                      : step<true, false, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial + ps,
+                                               inv_a, shift, flags, ps, bt, st);
+    if (s != TB_OK) return s;
+    const real two_over_a = static_cast<real>(2.0 / a);
+    const int last = dbl ? (M - 1) / 2 + 1 : M - 1;   // index of the last vector computed
+    for (int m = 2; m <= last; ++m) {
+      // v_m is written over v_{m-2}: m even -> B, m odd -> A; v_2 reads prev = v0
+      real *out = (m & 1) ? A : B;
+      const real *x = (m & 1) ? B : A;
+      const real *prev = (m == 2) ? v0 : out;
+      s = dbl ? step<false, true, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                       partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift, flags, ps, bt, st)
+              : step<false, false, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                        partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
+      if (s != TB_OK) return s;
+    }
+    if (ev_end) TB_CUDA(cudaEventRecord(ev_end, st));
+    if (SEG) {
+      const int64_t total = (int64_t)bt.n_snap * M * R;
+      batched_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(bt, M, R, RPB, units, partial,
+                                                                             dbl ? 1 : 0, mu_r, flags);
     } else {
-      cheb_step_kernel<real, valT, R, CPT, FIRST, DBL><<<grid, kBlock, 0, st>>>(n, slice_ptr, col, val, diag, x,
-                                                                               prev, v0, out, partial, alpha, shift);
+      const int total = M * R;
+      moment_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, dbl ? 1 : 0,
+                                                                mu_r, flags);
     }
     TB_CHECK_LAUNCH();
+    return TB_OK;
+  }
+
+  static tb_status check_flags(const int *flags, cudaStream_t st, const char *who) {
+    int hflags[4] = {0, 0, 0, 0};
+    TB_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(cudaStreamSynchronize(st));
+    if (hflags[0] & 4) return fail(TB_ERR_TIMEOUT, "%s: a pipeline wait timed out", who);
+    if (hflags[0] & 2) return fail(TB_ERR_NOT_FINITE, "%s: non-finite moment", who);
+    if (hflags[0] & 1)
+      return fail(TB_ERR_BOUNDS, "%s: |mu_n| > 1 + 1e-6; the spectrum is not inside [b - a, b + a]", who);
     return TB_OK;
   }
 
@@ -570,58 +672,74 @@ struct KpmRunner {
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments: workspace too small (%zu < %zu)", ws_bytes, cv.used);
     if (use_bulk() && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
       return fail(TB_ERR_INVALID_ARG, "kpm_moments: col and val must be 16-byte aligned");
-    TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
-    random_phase_kernel<real, R, CPT><<<grid, kBlock, 0, st>>>(n, seed, v0, partial);
-    TB_CHECK_LAUNCH();
-    const real shift = static_cast<real>(b);
-    const size_t pstride = (size_t)grid * R;
+    prepare();
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (step_ms) {
       TB_CUDA(cudaEventCreate(&ev[0]));
       TB_CUDA(cudaEventCreate(&ev[1]));
-      TB_CUDA(cudaEventRecord(ev[0], st));
     }
-    // v1 = H~ v0 -> A.  Direct mode: the step making v_m adds the partials of
-    // mu_m; doubling mode: the step reading v_k adds those of S_2k and S_2k+1.
-    const real inv_a = static_cast<real>(1.0 / a);
-    tb_status s = dbl ? step<true, true>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial, inv_a,
-                                         shift, flags, st)
-                      : step<true, false>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A,
-                                          partial + pstride, inv_a, shift, flags, st);
-    if (s != TB_OK) return s;
-    const real two_over_a = static_cast<real>(2.0 / a);
-    const int last = dbl ? (M - 1) / 2 + 1 : M - 1;   // index of the last vector computed
-    for (int m = 2; m <= last; ++m) {
-      // v_m is written over v_{m-2}: m even -> B, m odd -> A; v_2 reads prev = v0
-      real *out = (m & 1) ? A : B;
-      const real *x = (m & 1) ? B : A;
-      const real *prev = (m == 2) ? v0 : out;
-      s = dbl ? step<false, true>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                  partial + (size_t)(2 * (m - 1)) * pstride, two_over_a, shift, flags, st)
-              : step<false, false>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                   partial + (size_t)m * pstride, two_over_a, shift, flags, st);
-      if (s != TB_OK) return s;
-    }
-    if (step_ms) TB_CUDA(cudaEventRecord(ev[1], st));
-    const int total = M * R;
-    moment_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, dbl ? 1 : 0,
-                                                              mu_r, flags);
-    TB_CHECK_LAUNCH();
-    int hflags[4] = {0, 0, 0, 0};
-    TB_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
-    TB_CUDA(cudaStreamSynchronize(st));
+    tb_status s = enqueue<false>(grid, n, slice_ptr, col, val, diag, a, b, M, seed, dbl, mu_r, v0, A, B, partial,
+                                 flags, BatchTables(), st, ev[0], ev[1]);
+    if (s == TB_OK) s = check_flags(flags, st, "kpm_moments");
     if (step_ms) {
       float ms = 0.f;
-      TB_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      if (s == TB_OK) cudaEventElapsedTime(&ms, ev[0], ev[1]);
       *step_ms = ms;
       cudaEventDestroy(ev[0]);
       cudaEventDestroy(ev[1]);
     }
-    if (hflags[0] & 4) return fail(TB_ERR_TIMEOUT, "kpm_moments: a pipeline wait timed out");
-    if (hflags[0] & 2) return fail(TB_ERR_NOT_FINITE, "kpm_moments: non-finite moment");
-    if (hflags[0] & 1)
-      return fail(TB_ERR_BOUNDS, "kpm_moments: |mu_n| > 1 + 1e-6; the spectrum is not inside [b - a, b + a]");
-    return TB_OK;
+    return s;
+  }
+
+  // Batched: the caller's block-diagonal, already rescaled matrix of
+  // n_pad rows (see kpm_moments_batched); the recursion is captured once as
+  // a CUDA graph and launched on `st`.
+  static tb_status run_batched(int64_t n_pad, const int64_t *slice_ptr, const int32_t *col, const valT *val,
+                               const valT *diag, int M, uint64_t seed, int mode, const BatchTables &bt,
+                               double *mu, void *ws, size_t ws_bytes, cudaStream_t st, double *graph_ms) {
+    const int grid = grid_for(n_pad);
+    const bool dbl = mode == TB_KPM_DOUBLING;
+    Carver cv(ws, ws_bytes);
+    real *v0 = cv.take<real>((size_t)n_pad * R * 2);
+    real *A = cv.take<real>((size_t)n_pad * R * 2);
+    real *B = cv.take<real>((size_t)n_pad * R * 2);
+    double *partial = cv.take<double>((size_t)(M + 1) * blocks(n_pad) * R);
+    int *flags = cv.take<int>(4);
+    if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments_batched: workspace too small");
+    prepare();
+    cudaStream_t cs = nullptr;
+    TB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    tb_status s = TB_OK;
+    if (e == cudaSuccess) {
+      s = enqueue<true>(grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, dbl, mu, v0, A, B, partial, flags,
+                        bt, cs, nullptr, nullptr);
+      e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess && s == TB_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess && s == TB_OK && graph_ms) {
+      cudaEventCreate(&ev[0]);
+      cudaEventCreate(&ev[1]);
+      cudaEventRecord(ev[0], st);
+    }
+    if (e == cudaSuccess && s == TB_OK) e = cudaGraphLaunch(exec, st);
+    if (ev[1]) cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess && s == TB_OK) s = check_flags(flags, st, "kpm_moments_batched");
+    if (graph_ms && ev[1]) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      *graph_ms = ms;
+    }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "kpm_moments_batched graph", __FILE__, __LINE__);
+    return s;
   }
 };
 
@@ -641,10 +759,59 @@ struct KpmDispatch {
   }
 };
 
+// Copy snapshot s into the block-diagonal batch matrix with its rescaling
+// folded in: val' = val / a_s, diag' = (diag - b_s) / a_s on the real rows
+// (0 on padding rows); columns shifted by the snapshot's first row; padding
+// slices get width 0.
+template <typename valT>
+__global__ void batch_fold_kernel(const int64_t *__restrict__ sp, const int32_t *__restrict__ col,
+                                  const valT *__restrict__ val, const valT *__restrict__ diag, int64_t rows,
+                                  int64_t n_slices, int64_t pad_slices, int64_t total, int64_t row0, int64_t e0,
+                                  double inv_a, double shift, int64_t *__restrict__ dsp, int32_t *__restrict__ dcol,
+                                  valT *__restrict__ dval, valT *__restrict__ ddiag) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= pad_slices) dsp[row0 / 32 + t] = e0 + (t <= n_slices ? sp[t] : total);
+  if (t < total) {
+    // rows >= `rows` of the last slice are phantom rows: value 0 whatever
+    // the source holds there
+    const int64_t last0 = n_slices > 0 ? sp[n_slices - 1] : 0;
+    const bool phantom = t >= last0 && (n_slices - 1) * 32 + (t - last0) % 32 >= rows;
+    dcol[e0 + t] = col[t] + static_cast<int32_t>(row0);
+    dval[e0 + t] = phantom ? valT(0) : static_cast<valT>((double)val[t] * inv_a);
+  }
+  if (t < pad_slices * 32)
+    ddiag[row0 + t] = t < rows ? static_cast<valT>(((diag ? (double)diag[t] : 0.0) - shift) * inv_a) : valT(0);
+}
+
+template <typename real, typename valT, int R>
+struct BatchWsOp {
+  static tb_status apply(int64_t n_pad, int M, size_t *out) {
+    *out = KpmRunner<real, valT, R>::workspace(n_pad, M, true);
+    return TB_OK;
+  }
+};
+
+template <typename real, typename valT, int R>
+struct BatchRunOp {
+  static tb_status apply(int64_t n_pad, const int64_t *sp, const int32_t *col, const void *val, const void *diag,
+                         int M, uint64_t seed, int mode, const BatchTables *bt, double *mu, void *ws, size_t wsb,
+                         cudaStream_t st, double *ms) {
+    return KpmRunner<real, valT, R>::run_batched(n_pad, sp, col, static_cast<const valT *>(val),
+                                                 static_cast<const valT *>(diag), M, seed, mode, *bt, mu, ws, wsb, st,
+                                                 ms);
+  }
+};
+
+struct BatchLayout {
+  int64_t n_pad = 0, elements = 0;
+  std::vector<int64_t> row0, rows, e0, total, slices, pad_slices;
+  std::vector<int32_t> tile_snap;
+};
+
 template <typename real, typename valT, int R>
 struct WsOp {
   static tb_status apply(int64_t n, int M, size_t *out) {
-    *out = KpmRunner<real, valT, R>::workspace(n, M);
+    *out = KpmRunner<real, valT, R>::workspace(n, M, false);
     return TB_OK;
   }
 };
@@ -781,5 +948,146 @@ extern "C" tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, co
                                                            seed, (int)TB_KPM_DIRECT, mu_r, scratch,
                                                            kNoAllocScratchBytes, st, nullptr);
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_noalloc: unsupported R=%d", R);
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Batched KPM over uneven snapshots (multi-frame averaging, Sec. 2.4).
+// ---------------------------------------------------------------------------
+namespace gputb {
+namespace {
+
+tb_status batch_layout(int n_snap, const int64_t *n_rows, const int64_t *const *slice_ptr, bool read_totals,
+                       cudaStream_t st, BatchLayout *L) {
+  L->row0.resize(n_snap);
+  L->rows.resize(n_snap);
+  L->e0.resize(n_snap);
+  L->total.assign(n_snap, 0);
+  L->slices.resize(n_snap);
+  L->pad_slices.resize(n_snap);
+  L->tile_snap.clear();
+  int64_t row = 0, el = 0;
+  for (int s = 0; s < n_snap; ++s) {
+    TB_REQUIRE(n_rows[s] >= 1 && n_rows[s] < (int64_t(1) << 31), "kpm_moments_batched: snapshot %d size", s);
+    const int64_t padded = (n_rows[s] + kBatchTile - 1) / kBatchTile * kBatchTile;
+    L->row0[s] = row;
+    L->rows[s] = n_rows[s];
+    L->slices[s] = (n_rows[s] + 31) / 32;
+    L->pad_slices[s] = padded / 32;
+    if (read_totals) {
+      TB_REQUIRE(slice_ptr && slice_ptr[s], "kpm_moments_batched: snapshot %d has no slice_ptr", s);
+      TB_CUDA(cudaMemcpyAsync(&L->total[s], slice_ptr[s] + L->slices[s], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                              st));
+    }
+    for (int64_t q = 0; q < padded / kBatchTile; ++q) L->tile_snap.push_back(s);
+    row += padded;
+  }
+  if (read_totals) TB_CUDA(cudaStreamSynchronize(st));
+  for (int s = 0; s < n_snap; ++s) {
+    L->e0[s] = el;
+    el += L->total[s];
+  }
+  L->n_pad = row;
+  L->elements = el;
+  return TB_OK;
+}
+
+size_t batch_prefix_bytes(const BatchLayout &L, int n_snap, size_t val_size) {
+  Carver cv(nullptr, 0);
+  cv.take<int64_t>(L.n_pad / 32 + 1);
+  cv.take<int32_t>(L.elements > 0 ? L.elements : 1);
+  cv.take<char>((L.elements > 0 ? L.elements : 1) * val_size);
+  cv.take<char>(L.n_pad * val_size);
+  cv.take<int32_t>(L.tile_snap.size());
+  cv.take<int64_t>(n_snap);
+  cv.take<int64_t>(n_snap);
+  return align_up(cv.used, 256);
+}
+
+}  // namespace
+}  // namespace gputb
+
+extern "C" size_t kpm_moments_batched_workspace_size(int32_t n_snap, const int64_t *const *slice_ptr,
+                                                     const int64_t *n_rows, int32_t M, int32_t R,
+                                                     int32_t precision, void *stream) {
+  if (n_snap < 1 || !n_rows || !slice_ptr || M < 2) return 0;
+  BatchLayout L;
+  if (batch_layout(n_snap, n_rows, slice_ptr, true, static_cast<cudaStream_t>(stream), &L) != TB_OK) return 0;
+  size_t run = 0;
+  tb_status st = TB_OK;
+  const bool ok = precision == TB_F32 ? KpmDispatch<float, float>::call<BatchWsOp>(R, st, L.n_pad, (int)M, &run)
+                                      : KpmDispatch<double, double>::call<BatchWsOp>(R, st, L.n_pad, (int)M, &run);
+  if (!ok) return 0;
+  return batch_prefix_bytes(L, n_snap, precision == TB_F32 ? 4 : 8) + run + 256;
+}
+
+extern "C" tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows, const int64_t *const *slice_ptr,
+                                         const int32_t *const *col, const void *const *val, const void *const *diag,
+                                         int32_t precision, const double *a, const double *b, int32_t M, int32_t R,
+                                         uint64_t seed, int32_t mode, double *mu, void *workspace,
+                                         size_t workspace_bytes, void *stream, double *graph_ms) {
+  TB_REQUIRE(n_snap >= 1 && n_rows && slice_ptr && col && val && a && b && mu && workspace,
+             "kpm_moments_batched: bad argument");
+  TB_REQUIRE(M >= 2, "kpm_moments_batched: M must be >= 2");
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "kpm_moments_batched: bad precision");
+  TB_REQUIRE(mode == TB_KPM_DIRECT || mode == TB_KPM_DOUBLING, "kpm_moments_batched: bad mode");
+  TB_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "kpm_moments_batched: workspace alignment");
+  for (int s = 0; s < n_snap; ++s)
+    TB_REQUIRE(a[s] > 0.0 && std::isfinite(a[s]) && std::isfinite(b[s]), "kpm_moments_batched: bad a/b of %d", s);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchLayout L;
+  tb_status status = batch_layout(n_snap, n_rows, slice_ptr, true, st, &L);
+  if (status != TB_OK) return status;
+  const size_t vs = precision == TB_F32 ? 4 : 8;
+  Carver cv(workspace, workspace_bytes);
+  int64_t *dsp = cv.take<int64_t>(L.n_pad / 32 + 1);
+  int32_t *dcol = cv.take<int32_t>(L.elements > 0 ? L.elements : 1);
+  char *dval = cv.take<char>((L.elements > 0 ? L.elements : 1) * vs);
+  char *ddiag = cv.take<char>(L.n_pad * vs);
+  int32_t *dtile = cv.take<int32_t>(L.tile_snap.size());
+  int64_t *drow0 = cv.take<int64_t>(n_snap);
+  int64_t *drows = cv.take<int64_t>(n_snap);
+  cv.used = align_up(cv.used, 256);
+  if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments_batched: workspace too small");
+  void *run_ws = static_cast<char *>(workspace) + cv.used;
+  const size_t run_bytes = workspace_bytes - cv.used;
+  TB_CUDA(cudaMemcpyAsync(dtile, L.tile_snap.data(), L.tile_snap.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                          st));
+  TB_CUDA(cudaMemcpyAsync(drow0, L.row0.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  TB_CUDA(cudaMemcpyAsync(drows, L.rows.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  for (int s = 0; s < n_snap; ++s) {
+    const int64_t work = std::max(L.total[s], L.pad_slices[s] * 32 + 1);
+    const unsigned nb = (unsigned)((work + 255) / 256);
+    if (precision == TB_F32)
+      batch_fold_kernel<float><<<nb, 256, 0, st>>>(slice_ptr[s], col[s], static_cast<const float *>(val[s]),
+                                                   diag ? static_cast<const float *>(diag[s]) : nullptr, L.rows[s],
+                                                   L.slices[s], L.pad_slices[s], L.total[s], L.row0[s], L.e0[s],
+                                                   1.0 / a[s], b[s], dsp, dcol, reinterpret_cast<float *>(dval),
+                                                   reinterpret_cast<float *>(ddiag));
+    else
+      batch_fold_kernel<double><<<nb, 256, 0, st>>>(slice_ptr[s], col[s], static_cast<const double *>(val[s]),
+                                                    diag ? static_cast<const double *>(diag[s]) : nullptr,
+                                                    L.rows[s], L.slices[s], L.pad_slices[s], L.total[s], L.row0[s],
+                                                    L.e0[s], 1.0 / a[s], b[s], dsp, dcol,
+                                                    reinterpret_cast<double *>(dval),
+                                                    reinterpret_cast<double *>(ddiag));
+    TB_CHECK_LAUNCH();
+  }
+  TB_CUDA(cudaStreamSynchronize(st));  // the host tables above may go out of scope
+  BatchTables bt;
+  bt.tile_snap = dtile;
+  bt.row0 = drow0;
+  bt.rows = drows;
+  bt.n_snap = n_snap;
+  const bool ok = precision == TB_F32
+                      ? KpmDispatch<float, float>::call<BatchRunOp>(R, status, L.n_pad, (const int64_t *)dsp,
+                                                                    (const int32_t *)dcol, (const void *)dval,
+                                                                    (const void *)ddiag, (int)M, seed, (int)mode, &bt,
+                                                                    mu, run_ws, run_bytes, st, graph_ms)
+                      : KpmDispatch<double, double>::call<BatchRunOp>(R, status, L.n_pad, (const int64_t *)dsp,
+                                                                      (const int32_t *)dcol, (const void *)dval,
+                                                                      (const void *)ddiag, (int)M, seed, (int)mode,
+                                                                      &bt, mu, run_ws, run_bytes, st, graph_ms);
+  if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: unsupported R=%d", R);
   return status;
 }

@@ -28,9 +28,13 @@ __global__ void teacher_kernel(const double *__restrict__ pos, const int32_t *__
                                const int32_t *__restrict__ ncount, valT *__restrict__ val, valT *__restrict__ diag,
                                int *__restrict__ flags) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= ((n + 31) >> 5) << 5) return;
   const int64_t sb = slice_ptr[i >> 5];
   const int w = static_cast<int>((slice_ptr[(i >> 5) + 1] - sb) >> 5);
+  if (i >= n) {  // phantom rows of the last slice hold value 0
+    for (int s = 0; s < w; ++s) val[sb + (i & 31) + 32 * s] = valT(0);
+    return;
+  }
   const int zi = species[i];
   if (zi < 0 || zi >= T.n_species) atomicOr(flags, 1);
   const int zic = min(max(zi, 0), T.n_species - 1);
@@ -84,7 +88,7 @@ extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const
   int *flags = nullptr;
   TB_CUDA(cudaMallocAsync(&flags, sizeof(int), st));
   TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
-  const unsigned nb = (unsigned)((n + 255) / 256);
+  const unsigned nb = (unsigned)((((n + 31) / 32) * 32 + 255) / 256);
   if (precision == TB_F32)
     teacher_kernel<float><<<nb, 256, 0, st>>>(positions, species, n, B, T, slice_ptr, col, cnt, ncount,
                                               static_cast<float *>(val), static_cast<float *>(diag), flags);

@@ -44,6 +44,9 @@ SIGNATURES = {
                              _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_moments_noalloc": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32,
                                      _c_i32, _c_u64, _c_vp, _c_vp]),
+    "kpm_moments_batched_workspace_size": (_c_sz, [_c_i32, _c_vp, _c_vp, _c_i32, _c_i32, _c_i32, _c_vp]),
+    "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
+                                     _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
     "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl]),
     "tb_build_neighbors": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_vp, _c_vp, _c_i64,
@@ -170,6 +173,43 @@ def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
     _check("kpm_moments", st)
     if timing is not None:
         timing.append(step_ms.value)
+    return mu
+
+
+def kpm_moments_batched(mats, a, b, M: int, R: int, seed: int, doubling: bool = False, stream=None,
+                        timing: Optional[list] = None) -> torch.Tensor:
+    """Moments of every snapshot in one graph launch: mu [S, R, M] (float64,
+    device).  Snapshot s uses seed + s."""
+    import numpy as np
+    L = lib()
+    S = len(mats)
+    prec = mats[0].precision
+    if any(m.precision != prec for m in mats):
+        raise ValueError("all snapshots must share one precision")
+    rows = np.array([m.n for m in mats], np.int64)
+    aa = np.ascontiguousarray(np.asarray(a, np.float64))
+    bb = np.ascontiguousarray(np.asarray(b, np.float64))
+    arr = lambda ts: (ctypes.c_void_p * S)(*[(t.data_ptr() if t is not None else None) for t in ts])
+    sp, col = arr([m.slice_ptr for m in mats]), arr([m.col for m in mats])
+    val, dg = arr([m.val for m in mats]), arr([m.diag for m in mats])
+    need = L.kpm_moments_batched_workspace_size(S, ctypes.cast(sp, ctypes.c_void_p), rows.ctypes.data_as(ctypes.c_void_p),
+                                                M, R, prec, _stream(stream))
+    if need == 0:
+        raise GputbError("kpm_moments_batched_workspace_size", TB_ERR_INVALID_ARG, f"unsupported R={R} M={M}")
+    dev = mats[0].col.device
+    ws = _workspace(need, dev)
+    ws.fill_(0xFF)  # contents on entry are ignored by the library; keep stale data visible to tests
+    mu = torch.empty((S, R, M), dtype=torch.float64, device=dev)
+    ms = ctypes.c_double(0.0)
+    st = L.kpm_moments_batched(S, rows.ctypes.data_as(ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
+                               ctypes.cast(col, ctypes.c_void_p), ctypes.cast(val, ctypes.c_void_p),
+                               ctypes.cast(dg, ctypes.c_void_p), prec, aa.ctypes.data_as(ctypes.c_void_p),
+                               bb.ctypes.data_as(ctypes.c_void_p), int(M), int(R), int(seed) & ((1 << 64) - 1),
+                               KPM_DOUBLING if doubling else KPM_DIRECT, _ptr(mu), _ptr(ws), ws.numel(),
+                               _stream(stream), ctypes.byref(ms) if timing is not None else None)
+    _check("kpm_moments_batched", st)
+    if timing is not None:
+        timing.append(ms.value)
     return mu
 
 
