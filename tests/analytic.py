@@ -41,9 +41,61 @@ def nn_graphene_dos_closed_form(E, t):
     return out
 
 
-def chebyshev_moments_of_levels(levels, a, b, M):
-    """mu_n = mean over levels of T_n((E - b)/a) = cos(n arccos x)."""
-    x = np.clip((np.asarray(levels) - b) / a, -1.0, 1.0)
-    th = np.arccos(x)
-    n = np.arange(M)[:, None]
-    return np.cos(n * th[None, :]).mean(axis=1)
+def chebyshev_moments_of_levels(levels, a, b, M, chunk=1 << 15):
+    """mu_n = mean over levels of T_n((E - b)/a).
+
+    Small level sets use T_n(x) = cos(n arccos x); large ones the three-term
+    recurrence T_{n+1} = 2 x T_n - T_{n-1} on cache-sized chunks."""
+    x = np.clip((np.asarray(levels, np.float64) - b) / a, -1.0, 1.0)
+    if x.size <= 100000:
+        n = np.arange(M)[:, None]
+        return np.cos(n * np.arccos(x)[None, :]).mean(axis=1)
+    acc = np.zeros(M)
+    for s in range(0, x.size, chunk):
+        xc = x[s:s + chunk]
+        t0 = np.ones_like(xc)
+        t1 = xc.copy()
+        acc[0] += t0.sum()
+        if M > 1:
+            acc[1] += t1.sum()
+        two_x = 2.0 * xc
+        for k in range(2, M):
+            t2 = two_x * t1
+            t2 -= t0
+            acc[k] += t2.sum()
+            t0, t1 = t1, t2
+    return acc / x.size
+
+
+def rect_cell_bloch_levels(nx, ny, shell_hoppings, a_cc=1.42, onsite=0.0, chunk=200000):
+    """All 4 nx ny eigenvalues of pristine graphene on an nx x ny torus of
+    4-atom rectangular cells (3 a_cc by sqrt(3) a_cc, basis (0,0), (a,0),
+    (1.5a, h), (2.5a, h)), with hoppings given per neighbour shell as
+    {distance: t}.  Bloch's theorem: H(k)_{bb'} = sum_T t(|d|) e^{i k.d},
+    d = r_b' + T - r_b, for k on the torus grid."""
+    h = 0.5 * np.sqrt(3.0) * a_cc
+    lx, ly = 3.0 * a_cc, np.sqrt(3.0) * a_cc
+    basis = np.array([[0.0, 0.0], [a_cc, 0.0], [1.5 * a_cc, h], [2.5 * a_cc, h]])
+    terms = []                                   # (b, b', d, t)
+    for b in range(4):
+        for bp in range(4):
+            for tx in (-1, 0, 1):
+                for ty in (-1, 0, 1):
+                    d = basis[bp] + np.array([tx * lx, ty * ly]) - basis[b]
+                    r = float(np.hypot(*d))
+                    for dist, t in shell_hoppings.items():
+                        if abs(r - dist) < 1e-6:
+                            terms.append((b, bp, d, t))
+    m1, m2 = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    kx = (2 * np.pi * m1 / (nx * lx)).reshape(-1)
+    ky = (2 * np.pi * m2 / (ny * ly)).reshape(-1)
+    out = []
+    for s in range(0, kx.size, chunk):
+        k = np.stack([kx[s:s + chunk], ky[s:s + chunk]], axis=1)
+        Hk = np.zeros((k.shape[0], 4, 4), np.complex128)
+        for b in range(4):
+            Hk[:, b, b] += onsite
+        for b, bp, d, t in terms:
+            Hk[:, b, bp] += t * np.exp(1j * (k @ d))
+        out.append(np.linalg.eigvalsh(Hk).reshape(-1))
+    return np.concatenate(out)
