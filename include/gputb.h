@@ -256,7 +256,8 @@ TB_API tb_status tb_build_neighbors(const double *positions, int64_t n, const do
  * Eq. 1; it replaces the DFT labels of Sec. 2.3):
  *   t_ij  = P[Z_i][Z_j] exp(-beta (r_ij/a_cc - 1)) (1 + gamma (n_i+n_j-6)/6) f_c(r_ij)
  *   f_c(r) = (1 + cos(pi r/rcut))/2 for r < rcut, else 0;  eps_i = onsite[Z_i]
- * evaluated in FP64 and stored in `precision` into the SELL-32 layout of
+ * evaluated from FP64 distances (exp and cos in `precision`) and stored in
+ * `precision` into the SELL-32 layout of
  * (slice_ptr, col) from tb_build_neighbors (same positions and box).
  *
  *   species        device int32 [N], values 0..2 (else TB_ERR_INVALID_ARG)

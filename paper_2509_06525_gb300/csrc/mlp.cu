@@ -165,7 +165,9 @@ struct DescConst {
 __device__ __forceinline__ void bond_descriptor(float r, float rcut, const float *__restrict__ c /*[8][8]*/,
                                                 float (&C)[8]) {
   float f[8];
-  const float fc = r < rcut ? 0.5f * (1.0f + cospif(r / rcut)) : 0.0f;
+  // (1 + cos(pi r/rc))/2 written as cos^2(pi r/(2 rc)): no cancellation near rc
+  const float ch = cospif(0.5f * r / rcut);
+  const float fc = r < rcut ? ch * ch : 0.0f;
   const float u = r / rcut - 1.0f;
   const float x = 2.0f * u * u - 1.0f;
   float t0 = 1.0f, t1 = x;

@@ -9,8 +9,10 @@
 //  4. count         per-row neighbour count cnt_i and n_i (r < r_count)
 //  5. slice widths  max cnt over each 32-row slice, overflow check, scan
 //  6. fill          sorted neighbour indices of each row into col
-// Distances use the explicitly rounded FP64 minimum image of geometry.cuh,
-// so membership is decided exactly as the FP64 definition states.
+// Pairs are screened in FP32 with a safety margin; only candidates whose
+// |d|^2 lies within a relative 4e-6 of r_cut^2 (or r_count^2) take the
+// explicitly rounded FP64 test, so membership is decided as the FP64
+// definition states at a fraction of the FP64 work (GB300's FP64 rate is low).
 #include <cmath>
 
 #include "geometry.cuh"
@@ -47,18 +49,27 @@ struct Grid {
   int64_t ncell;
 };
 
-__device__ __forceinline__ int cell_coord(double s, int nc, int periodic) {
-  if (!periodic || nc == 1) return 0;
-  s = s - floor(s);
-  int c = static_cast<int>(s * nc);
-  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
-}
-
-__device__ __forceinline__ int3 cell_of(const Box &B, const Grid &G, double x, double y, double z) {
-  const double s3 = z / B.cz;
-  const double s2 = (y - s3 * B.cy) / B.by;
-  const double s1 = (x - s3 * B.cx - s2 * B.bx) / B.ax;
-  return make_int3(cell_coord(s1, G.nc[0], B.p1), cell_coord(s2, G.nc[1], B.p2), cell_coord(s3, G.nc[2], B.p3));
+// Fractional coordinates s (B^T s = p for the lower-triangular box rows),
+// the periodic image of p inside the cell (pw = p - sum_k floor(s_k) a_k
+// over periodic k) and its cell.  The same function serves the binning and
+// the search, so every atom's wrapped position is computed identically.
+__device__ __forceinline__ void wrap_and_bin(const Box &B, const Grid &G, double x, double y, double z, double3 &pw,
+                                             int3 &cell) {
+  // explicitly rounded operations: every kernel gets bit-identical results
+  const double s3 = __ddiv_rn(z, B.cz);
+  const double s2 = __ddiv_rn(__dsub_rn(y, __dmul_rn(s3, B.cy)), B.by);
+  const double s1 = __ddiv_rn(__dsub_rn(__dsub_rn(x, __dmul_rn(s3, B.cx)), __dmul_rn(s2, B.bx)), B.ax);
+  const double n1 = B.p1 ? floor(s1) : 0.0, n2 = B.p2 ? floor(s2) : 0.0, n3 = B.p3 ? floor(s3) : 0.0;
+  pw.x = __dsub_rn(__dsub_rn(__dsub_rn(x, __dmul_rn(n1, B.ax)), __dmul_rn(n2, B.bx)), __dmul_rn(n3, B.cx));
+  pw.y = __dsub_rn(__dsub_rn(y, __dmul_rn(n2, B.by)), __dmul_rn(n3, B.cy));
+  pw.z = __dsub_rn(z, __dmul_rn(n3, B.cz));
+  auto coord = [](double f, int nc, int periodic) {
+    if (!periodic || nc == 1) return 0;
+    int c = static_cast<int>(__dmul_rn(f, (double)nc));
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+  };
+  cell = make_int3(coord(__dsub_rn(s1, n1), G.nc[0], B.p1), coord(__dsub_rn(s2, n2), G.nc[1], B.p2),
+                   coord(__dsub_rn(s3, n3), G.nc[2], B.p3));
 }
 
 __device__ __forceinline__ int64_t cell_index(const Grid &G, int c1, int c2, int c3) {
@@ -76,84 +87,129 @@ __global__ void cell_bin_kernel(const double *__restrict__ pos, int64_t n, Box B
     atomicAdd(count, 1ull);
     return;
   }
-  const int3 c = cell_of(B, G, x, y, z);
+  double3 pw;
+  int3 c;
+  wrap_and_bin(B, G, x, y, z, pw, c);
   const int64_t id = cell_index(G, c.x, c.y, c.z);
   cell[i] = static_cast<int32_t>(id);
   atomicAdd(count + id, 1ull);
 }
 
-__global__ void cell_scatter_kernel(const double *__restrict__ pos, int64_t n, const int32_t *__restrict__ cell,
-                                    unsigned long long *__restrict__ cursor, int32_t *__restrict__ atom,
-                                    double *__restrict__ px, double *__restrict__ py, double *__restrict__ pz) {
+// atoms of each cell in cell order, with their wrapped positions (SoA)
+__global__ void cell_scatter_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G,
+                                    const int32_t *__restrict__ cell, unsigned long long *__restrict__ cursor,
+                                    int32_t *__restrict__ atom, double *__restrict__ px, double *__restrict__ py,
+                                    double *__restrict__ pz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  double3 pw;
+  int3 c;
+  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pw, c);
   const int64_t slot = (int64_t)atomicAdd(cursor + cell[i], 1ull);
   atom[slot] = static_cast<int32_t>(i);
-  px[slot] = pos[3 * i];
-  py[slot] = pos[3 * i + 1];
-  pz[slot] = pos[3 * i + 2];
+  px[slot] = pw.x;
+  py[slot] = pw.y;
+  pz[slot] = pw.z;
 }
 
-// Visit every candidate j of atom i (each candidate cell once), calling
-// f(j, d, r2) for j != i with r2 < rcut2.
+// Search parameters: thresholds on r^2 with FP32 safety margins.  A
+// candidate's FP64 displacement d is rounded to FP32 and its FP32 |d|^2 is
+// within a relative 1e-6 of the exact value, so |d|^2 < lo means inside,
+// >= hi outside; only candidates between lo and hi take the explicitly
+// rounded FP64 test ((dx*dx + dy*dy) + dz*dz < r^2).
+struct Radii {
+  double rc2, rn2;            // exact thresholds (r_count^2 < 0 disables)
+  float rc_lo, rc_hi, rn_lo, rn_hi;
+};
+
+// Visit every neighbour j of atom i: f(j, within_r_count).  Neighbour cells
+// are visited with the lattice shift of their periodic image, so a pair
+// costs one FP64 difference per component; directions with fewer than 3
+// cells visit every cell with shifts -1, 0, +1 (only one image of j can be
+// within r_cut because the periodic widths are at least 2 r_cut).
 template <typename F>
 __device__ __forceinline__ void for_each_neighbor(const Box &B, const Grid &G, const int64_t *__restrict__ start,
                                                   const int32_t *__restrict__ atom, const double *__restrict__ px,
                                                   const double *__restrict__ py, const double *__restrict__ pz,
-                                                  int64_t i, double xi, double yi, double zi, int32_t my_cell,
-                                                  double rcut2, F &&f) {
-  const int c1 = (int)(my_cell % G.nc[0]);
-  const int c2 = (int)((my_cell / G.nc[0]) % G.nc[1]);
-  const int c3 = (int)(my_cell / ((int64_t)G.nc[0] * G.nc[1]));
-  // search ranges: +-1 cell, or every cell when a direction has < 3 cells
-  int lo[3], hi[3];
-  const int cc[3] = {c1, c2, c3};
+                                                  int64_t i, const double3 &pwi, const int3 &ci, const Radii &rad,
+                                                  F &&f) {
+  int cells[3][6], shifts[3][6], cnt[3];
+  const int cc[3] = {ci.x, ci.y, ci.z};
+  const int per[3] = {B.p1, B.p2, B.p3};
   for (int k = 0; k < 3; ++k) {
-    if (G.nc[k] < 3) {
-      lo[k] = 0;
-      hi[k] = G.nc[k] - 1;
+    const int nc = G.nc[k];
+    cnt[k] = 0;
+    if (!per[k]) {
+      for (int e = 0; e < nc; ++e) {
+        cells[k][cnt[k]] = e;
+        shifts[k][cnt[k]++] = 0;
+      }
+    } else if (nc >= 3) {
+      for (int dlt = -1; dlt <= 1; ++dlt) {
+        const int raw = cc[k] + dlt;
+        cells[k][cnt[k]] = (raw + nc) % nc;
+        shifts[k][cnt[k]++] = raw < 0 ? -1 : (raw >= nc ? 1 : 0);
+      }
     } else {
-      lo[k] = cc[k] - 1;
-      hi[k] = cc[k] + 1;
+      for (int e = 0; e < nc; ++e)
+        for (int sh = -1; sh <= 1; ++sh) {
+          cells[k][cnt[k]] = e;
+          shifts[k][cnt[k]++] = sh;
+        }
     }
   }
-  for (int d3 = lo[2]; d3 <= hi[2]; ++d3) {
-    const int e3 = G.nc[2] < 3 ? d3 : (d3 + G.nc[2]) % G.nc[2];
-    for (int d2 = lo[1]; d2 <= hi[1]; ++d2) {
-      const int e2 = G.nc[1] < 3 ? d2 : (d2 + G.nc[1]) % G.nc[1];
-      for (int d1 = lo[0]; d1 <= hi[0]; ++d1) {
-        const int e1 = G.nc[0] < 3 ? d1 : (d1 + G.nc[0]) % G.nc[0];
-        const int64_t c = cell_index(G, e1, e2, e3);
-        const int64_t s0 = __ldg(start + c), s1 = __ldg(start + c + 1);
-        for (int64_t s = s0; s < s1; ++s) {
+  for (int q3 = 0; q3 < cnt[2]; ++q3)
+    for (int q2 = 0; q2 < cnt[1]; ++q2)
+      for (int q1 = 0; q1 < cnt[0]; ++q1) {
+        const double s1 = shifts[0][q1], s2 = shifts[1][q2], s3 = shifts[2][q3];
+        // q = pw_i - S: the displacement to the image of j is pw_j - q
+        const double qx = pwi.x - (s1 * B.ax + s2 * B.bx + s3 * B.cx);
+        const double qy = pwi.y - (s2 * B.by + s3 * B.cy);
+        const double qz = pwi.z - s3 * B.cz;
+        const int64_t c = cell_index(G, cells[0][q1], cells[1][q2], cells[2][q3]);
+        const int64_t a0 = __ldg(start + c), a1 = __ldg(start + c + 1);
+        for (int64_t s = a0; s < a1; ++s) {
+          const double dx = __dsub_rn(__ldg(px + s), qx);
+          const double dy = __dsub_rn(__ldg(py + s), qy);
+          const double dz = __dsub_rn(__ldg(pz + s), qz);
+          const float fx = static_cast<float>(dx), fy = static_cast<float>(dy), fz = static_cast<float>(dz);
+          const float r2f = fx * fx + fy * fy + fz * fz;
+          if (r2f >= rad.rc_hi) continue;
           const int32_t j = __ldg(atom + s);
           if (j == i) continue;
-          double3 d;
-          d.x = __dsub_rn(__ldg(px + s), xi);
-          d.y = __dsub_rn(__ldg(py + s), yi);
-          d.z = __dsub_rn(__ldg(pz + s), zi);
-          d = min_image(B, d);
-          const double r2 = sq_norm(d);
-          if (r2 < rcut2) f(j, r2);
+          double r2 = -1.0;
+          if (r2f >= rad.rc_lo) {
+            r2 = sq_norm(make_double3(dx, dy, dz));
+            if (!(r2 < rad.rc2)) continue;
+          }
+          bool close = false;
+          if (rad.rn2 > 0.0) {
+            if (r2f < rad.rn_lo) close = true;
+            else if (r2f < rad.rn_hi) {
+              if (r2 < 0.0) r2 = sq_norm(make_double3(dx, dy, dz));
+              close = r2 < rad.rn2;
+            }
+          }
+          f(j, close);
         }
       }
-    }
-  }
 }
 
 __global__ void count_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G,
-                             const int32_t *__restrict__ cell, const int64_t *__restrict__ start,
-                             const int32_t *__restrict__ atom, const double *__restrict__ px,
-                             const double *__restrict__ py, const double *__restrict__ pz, double rcut2,
-                             double rcount2, int32_t *__restrict__ cnt, int32_t *__restrict__ ncount) {
+                             const int64_t *__restrict__ start, const int32_t *__restrict__ atom,
+                             const double *__restrict__ px, const double *__restrict__ py,
+                             const double *__restrict__ pz, Radii rad, int32_t *__restrict__ cnt,
+                             int32_t *__restrict__ ncount) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  double3 pwi;
+  int3 ci;
+  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pwi, ci);
   int c = 0, nc = 0;
-  for_each_neighbor(B, G, start, atom, px, py, pz, i, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], cell[i], rcut2,
-                    [&](int32_t, double r2) {
-                      ++c;
-                      if (r2 < rcount2) ++nc;
-                    });
+  for_each_neighbor(B, G, start, atom, px, py, pz, i, pwi, ci, rad, [&](int32_t, bool close) {
+    ++c;
+    if (close) ++nc;
+  });
   cnt[i] = c;
   if (ncount) ncount[i] = nc;
 }
@@ -176,10 +232,10 @@ __global__ void slice_width_kernel(const int32_t *__restrict__ cnt, int64_t n, i
 }
 
 __global__ void fill_kernel(const double *__restrict__ pos, int64_t n, int64_t n_slices, Box B, Grid G,
-                            const int32_t *__restrict__ cell, const int64_t *__restrict__ start,
-                            const int32_t *__restrict__ atom, const double *__restrict__ px,
-                            const double *__restrict__ py, const double *__restrict__ pz, double rcut2,
-                            const int64_t *__restrict__ slice_ptr, int32_t *__restrict__ col) {
+                            const int64_t *__restrict__ start, const int32_t *__restrict__ atom,
+                            const double *__restrict__ px, const double *__restrict__ py,
+                            const double *__restrict__ pz, Radii rad, const int64_t *__restrict__ slice_ptr,
+                            int32_t *__restrict__ col) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_slices * 32) return;
   const int64_t k = i >> 5;
@@ -189,19 +245,21 @@ __global__ void fill_kernel(const double *__restrict__ pos, int64_t n, int64_t n
     for (int s = 0; s < w; ++s) col[base + 32 * s] = 0;
     return;
   }
+  double3 pwi;
+  int3 ci;
+  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pwi, ci);
   int32_t list[kMaxWidth];
   int m = 0;
-  for_each_neighbor(B, G, start, atom, px, py, pz, i, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], cell[i], rcut2,
-                    [&](int32_t j, double) {
-                      if (m < w) {  // insertion sort, ascending j
-                        int p = m++;
-                        while (p > 0 && list[p - 1] > j) {
-                          list[p] = list[p - 1];
-                          --p;
-                        }
-                        list[p] = j;
-                      }
-                    });
+  for_each_neighbor(B, G, start, atom, px, py, pz, i, pwi, ci, rad, [&](int32_t j, bool) {
+    if (m < w) {  // insertion sort, ascending j
+      int p = m++;
+      while (p > 0 && list[p - 1] > j) {
+        list[p] = list[p - 1];
+        --p;
+      }
+      list[p] = j;
+    }
+  });
   for (int s = 0; s < w; ++s) col[base + 32 * s] = s < m ? list[s] : static_cast<int32_t>(i);
 }
 
@@ -295,8 +353,13 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
   if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_build_neighbors: workspace too small");
   const int64_t n_slices = (n + 31) / 32;
   const unsigned nb = (unsigned)((n + 255) / 256);
-  const double rc2 = rcut * rcut;
-  const double rn2 = r_count > 0.0 ? r_count * r_count : -1.0;
+  Radii rad;
+  rad.rc2 = rcut * rcut;
+  rad.rn2 = r_count > 0.0 ? r_count * r_count : -1.0;
+  rad.rc_lo = static_cast<float>(rad.rc2 * (1.0 - 4e-6));
+  rad.rc_hi = static_cast<float>(rad.rc2 * (1.0 + 4e-6));
+  rad.rn_lo = rad.rn2 > 0.0 ? static_cast<float>(rad.rn2 * (1.0 - 4e-6)) : -1.0f;
+  rad.rn_hi = rad.rn2 > 0.0 ? static_cast<float>(rad.rn2 * (1.0 + 4e-6)) : -1.0f;
 
   TB_CUDA(cudaMemsetAsync(w.count, 0, (G.ncell + 1) * sizeof(unsigned long long), st));
   TB_CUDA(cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
@@ -306,10 +369,9 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
   s = exclusive_scan_i64(start, start, G.ncell + 1, w.total, w.scan_ws, st);
   if (s != TB_OK) return s;
   TB_CUDA(cudaMemcpyAsync(w.cursor, w.count, (G.ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-  cell_scatter_kernel<<<nb, 256, 0, st>>>(positions, n, w.cell, w.cursor, w.atom, w.px, w.py, w.pz);
+  cell_scatter_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, w.cell, w.cursor, w.atom, w.px, w.py, w.pz);
   TB_CHECK_LAUNCH();
-  count_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, w.cell, start, w.atom, w.px, w.py, w.pz, rc2, rn2, cnt,
-                                   ncount);
+  count_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, start, w.atom, w.px, w.py, w.pz, rad, cnt, ncount);
   TB_CHECK_LAUNCH();
   TB_CUDA(cudaMemsetAsync(w.sizes, 0, (n_slices + 1) * sizeof(int64_t), st));
   slice_width_kernel<<<(unsigned)((n_slices + 255) / 256), 256, 0, st>>>(cnt, n, n_slices, max_width, w.sizes,
@@ -331,7 +393,7 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
                 (long long)col_capacity);
   if (total > 0) {
     fill_kernel<<<(unsigned)((n_slices * 32 + 255) / 256), 256, 0, st>>>(
-        positions, n, n_slices, B, G, w.cell, start, w.atom, w.px, w.py, w.pz, rc2, slice_ptr, col);
+        positions, n, n_slices, B, G, start, w.atom, w.px, w.py, w.pz, rad, slice_ptr, col);
     TB_CHECK_LAUNCH();
   }
   return TB_OK;

@@ -6,7 +6,8 @@
 //   eps_i = onsite[Z_i]
 // One thread per row walks the row's slots (coalesced across the 32 rows of
 // a slice), recomputes the bond vector with the FP64 minimum image and
-// writes the value in FP32 or FP64.  Values are evaluated in FP64.
+// writes the value in FP32 or FP64.  Distances are FP64; the exponential and
+// cosine are evaluated in the output precision.
 #include <cmath>
 
 #include "geometry.cuh"
@@ -48,9 +49,19 @@ __global__ void teacher_kernel(const double *__restrict__ pos, const int32_t *__
       const int zj = min(max(species[j], 0), T.n_species - 1);
       const double3 d = bond_vector(B, pos, i, j);
       const double r = sqrt(sq_norm(d));
-      const double fc = r < T.rcut ? 0.5 * (1.0 + cos(M_PI * r / T.rcut)) : 0.0;
       const double env = 1.0 + T.gamma * ((double)(ni + ncount[j]) - 6.0) / 6.0;
-      t = T.pref[zic * 3 + zj] * exp(-T.beta * (r / T.a_cc - 1.0)) * env * fc;
+      if (sizeof(valT) == 8) {
+        const double fc = r < T.rcut ? 0.5 * (1.0 + cos(M_PI * r / T.rcut)) : 0.0;
+        t = T.pref[zic * 3 + zj] * exp(-T.beta * (r / T.a_cc - 1.0)) * env * fc;
+      } else {
+        // FP32 output: FP32 transcendentals, their small arguments formed in
+        // FP64 so that values near the cutoff keep FP32 relative accuracy:
+        // (1 + cos(pi r/rc))/2 = sin^2(pi u/2) with u = 1 - r/rc
+        const float sh = sinpif(0.5f * static_cast<float>(1.0 - r / T.rcut));
+        const float fc = r < T.rcut ? sh * sh : 0.0f;
+        const float ex = expf(static_cast<float>(-T.beta * (r / T.a_cc - 1.0)));
+        t = (double)((float)T.pref[zic * 3 + zj] * ex * (float)env * fc);
+      }
     }
     val[e] = static_cast<valT>(t);
   }

@@ -140,7 +140,8 @@ def test_teacher_values(g, name, params, dtype):
         np.testing.assert_allclose(v, t, rtol=1e-13, atol=1e-15)
         np.testing.assert_allclose(H.diag.cpu().numpy(), eps, rtol=0, atol=0)
     else:
-        np.testing.assert_allclose(v, t.astype(np.float32), rtol=2.0 ** -23, atol=1e-12)
+        # FP32 exp/cos: within a few FP32 ulp of the FP64 teacher
+        np.testing.assert_allclose(v, t.astype(np.float32), rtol=2.0 ** -20, atol=1e-12)
 
 
 def test_spectral_bounds_match_oracle(g):
