@@ -107,26 +107,48 @@ __global__ void scale_kernel(int64_t n, double *__restrict__ q, const double *__
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) q[i] *= inv;
 }
 
-// w = H q - beta_prev q_prev; part = sum q.w
+// w = H q - beta_prev q_prev; part = sum q.w.  A row with at most 16 slots
+// issues all its column and value loads before its gathers (memory-level
+// parallelism: the kernel is bound by latency, not by its FP64 arithmetic).
 template <typename valT>
-__global__ void lanczos_spmv_kernel(int64_t n, const int64_t *__restrict__ sp, const int32_t *__restrict__ col,
-                                    const valT *__restrict__ val, const valT *__restrict__ diag,
-                                    const double *__restrict__ q, const double *__restrict__ qprev,
-                                    const double *__restrict__ beta_prev, double *__restrict__ w,
-                                    double *__restrict__ part) {
+__global__ void __launch_bounds__(kB) lanczos_spmv_kernel(int64_t n, const int64_t *__restrict__ sp,
+                                                          const int32_t *__restrict__ col,
+                                                          const valT *__restrict__ val, const valT *__restrict__ diag,
+                                                          const double *__restrict__ q,
+                                                          const double *__restrict__ qprev,
+                                                          const double *__restrict__ beta_prev,
+                                                          double *__restrict__ w, double *__restrict__ part) {
+  constexpr int kW = 16;
   const double bp = beta_prev ? *beta_prev : 0.0;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
-    const int64_t sb = sp[i >> 5];
-    const int ww = static_cast<int>((sp[(i >> 5) + 1] - sb) >> 5);
-    double y = diag ? (double)diag[i] * q[i] : 0.0;
-    for (int s = 0; s < ww; ++s) {
-      const int64_t e = sb + (i & 31) + 32 * s;
-      y = fma((double)val[e], q[col[e]], y);
+    const int64_t sb = __ldg(sp + (i >> 5));
+    const int ww = static_cast<int>((__ldg(sp + (i >> 5) + 1) - sb) >> 5);
+    const int64_t e0 = sb + (i & 31);
+    const double qi = __ldg(q + i);
+    const double qp = qprev ? __ldcs(qprev + i) : 0.0;
+    double y = diag ? (double)__ldg(diag + i) * qi : 0.0;
+    if (ww <= kW) {
+      int32_t j[kW];
+      double h[kW];
+#pragma unroll
+      for (int s = 0; s < kW; ++s)
+        if (s < ww) {
+          j[s] = __ldcs(col + e0 + 32 * s);
+          h[s] = (double)__ldcs(val + e0 + 32 * s);
+        }
+#pragma unroll
+      for (int s = 0; s < kW; ++s)
+        if (s < ww) y = fma(h[s], __ldg(q + j[s]), y);
+    } else {
+      for (int s = 0; s < ww; ++s) {
+        const int64_t e = e0 + 32 * s;
+        y = fma((double)val[e], __ldg(q + col[e]), y);
+      }
     }
-    if (qprev) y = fma(-bp, qprev[i], y);
+    if (qprev) y = fma(-bp, qp, y);
     w[i] = y;
-    acc = fma(q[i], y, acc);
+    acc = fma(qi, y, acc);
   }
   const double s = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = s;

@@ -5,9 +5,9 @@
 // minimum-image displacement is reduced one lattice direction at a time
 // (a3, then a2, then a1).  When every periodic perpendicular width is at
 // least 2 r_cut, an image of j closer than r_cut to i, if one exists, is the
-// image this reduction returns.  Every operation is an explicitly rounded
-// FP64 intrinsic so the compiler cannot contract it into an FMA: the
-// membership test |d|^2 < r_cut^2 is reproducible bit for bit.
+// image this reduction returns.  It serves the kernels that recompute bond
+// vectors for values (teacher, descriptors, MLP features); neighbour
+// membership itself is decided by the search in neighbors.cu.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -18,25 +18,28 @@ namespace gputb {
 struct Box {
   double ax, bx, by, cx, cy, cz;
   int p1, p2, p3;  // periodic flags along a1, a2, a3
+  double iax, iby, icz;  // reciprocals of ax, by, cz
 };
 
 // Validate the box form and the 2 r_cut width rule on the host.
 tb_status make_box(const double *box9, const int32_t *pbc, double rcut, Box *out);
 
 __device__ __forceinline__ double3 min_image(const Box &B, double3 d) {
+  // the image index only needs to be right, not correctly rounded: multiply
+  // by the reciprocal box lengths (the FP64 divide is slow on GB300)
   if (B.p3) {
-    const double n3 = rint(__ddiv_rn(d.z, B.cz));
+    const double n3 = rint(d.z * B.icz);
     d.x = __dsub_rn(d.x, __dmul_rn(n3, B.cx));
     d.y = __dsub_rn(d.y, __dmul_rn(n3, B.cy));
     d.z = __dsub_rn(d.z, __dmul_rn(n3, B.cz));
   }
   if (B.p2) {
-    const double n2 = rint(__ddiv_rn(d.y, B.by));
+    const double n2 = rint(d.y * B.iby);
     d.x = __dsub_rn(d.x, __dmul_rn(n2, B.bx));
     d.y = __dsub_rn(d.y, __dmul_rn(n2, B.by));
   }
   if (B.p1) {
-    const double n1 = rint(__ddiv_rn(d.x, B.ax));
+    const double n1 = rint(d.x * B.iax);
     d.x = __dsub_rn(d.x, __dmul_rn(n1, B.ax));
   }
   return d;

@@ -25,7 +25,8 @@ tb_status make_box(const double *b, const int32_t *pbc, double rcut, Box *out) {
   if (b[1] != 0.0 || b[2] != 0.0 || b[5] != 0.0)
     return fail(TB_ERR_BOX, "box rows must have the form a1=(ax,0,0), a2=(bx,by,0), a3=(cx,cy,cz)");
   if (!(b[0] > 0.0 && b[4] > 0.0 && b[8] > 0.0)) return fail(TB_ERR_BOX, "box needs ax, by, cz > 0");
-  Box B{b[0], b[3], b[4], b[6], b[7], b[8], pbc[0] != 0, pbc[1] != 0, pbc[2] != 0};
+  Box B{b[0], b[3], b[4], b[6], b[7], b[8], pbc[0] != 0, pbc[1] != 0, pbc[2] != 0, 1.0 / b[0], 1.0 / b[4],
+        1.0 / b[8]};
   const double vol = B.ax * B.by * B.cz;
   const double w1 = vol / std::sqrt((B.by * B.cz) * (B.by * B.cz) + (B.bx * B.cz) * (B.bx * B.cz) +
                                     (B.bx * B.cy - B.by * B.cx) * (B.bx * B.cy - B.by * B.cx));

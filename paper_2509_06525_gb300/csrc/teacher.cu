@@ -18,7 +18,7 @@ namespace {
 struct TeacherConst {
   double pref[9];
   double onsite[3];
-  double a_cc, beta, gamma, rcut;
+  double a_cc, beta, gamma, rcut, inv_a;
   int n_species;
 };
 
@@ -48,19 +48,26 @@ __global__ void teacher_kernel(const double *__restrict__ pos, const int32_t *__
       const int32_t j = col[e];
       const int zj = min(max(species[j], 0), T.n_species - 1);
       const double3 d = bond_vector(B, pos, i, j);
-      const double r = sqrt(sq_norm(d));
-      const double env = 1.0 + T.gamma * ((double)(ni + ncount[j]) - 6.0) / 6.0;
+      const double r2 = sq_norm(d);
       if (sizeof(valT) == 8) {
+        const double r = sqrt(r2);
+        const double env = 1.0 + T.gamma * ((double)(ni + ncount[j]) - 6.0) / 6.0;
         const double fc = r < T.rcut ? 0.5 * (1.0 + cos(M_PI * r / T.rcut)) : 0.0;
         t = T.pref[zic * 3 + zj] * exp(-T.beta * (r / T.a_cc - 1.0)) * env * fc;
       } else {
-        // FP32 output: FP32 transcendentals, their small arguments formed in
-        // FP64 so that values near the cutoff keep FP32 relative accuracy:
-        // (1 + cos(pi r/rc))/2 = sin^2(pi u/2) with u = 1 - r/rc
-        const float sh = sinpif(0.5f * static_cast<float>(1.0 - r / T.rcut));
-        const float fc = r < T.rcut ? sh * sh : 0.0f;
-        const float ex = expf(static_cast<float>(-T.beta * (r / T.a_cc - 1.0)));
-        t = (double)((float)T.pref[zic * 3 + zj] * ex * (float)env * fc);
+        // FP32 output: FP32 transcendentals whose small arguments are formed
+        // from the FP64 r^2 without FP64 division or square root (both are
+        // slow on GB300's FP64 pipe), keeping FP32 relative accuracy near
+        // the cutoff:  1 - r/rc = (rc^2 - r^2) / (rc (rc + r)),
+        // r - a = (r^2 - a^2) / (r + a), (1 + cos(pi r/rc))/2 = sin^2(pi u/2).
+        const float rf = sqrtf(static_cast<float>(r2));
+        const float u = static_cast<float>(T.rcut * T.rcut - r2) / ((float)T.rcut * ((float)T.rcut + rf));
+        const float sh = sinpif(0.5f * u);
+        const float fc = u > 0.0f ? sh * sh : 0.0f;
+        const float dr = static_cast<float>(r2 - T.a_cc * T.a_cc) / (rf + (float)T.a_cc);
+        const float ex = expf(-(float)T.beta * dr * (float)T.inv_a);
+        const float env = 1.0f + (float)T.gamma * (float)(ni + ncount[j] - 6) * (1.0f / 6.0f);
+        t = (double)((float)T.pref[zic * 3 + zj] * ex * env * fc);
       }
     }
     val[e] = static_cast<valT>(t);
@@ -91,6 +98,7 @@ extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const
   for (int k = 0; k < 9; ++k) T.pref[k] = hop_prefactor[k];
   for (int k = 0; k < 3; ++k) T.onsite[k] = onsite[k];
   T.a_cc = a_cc;
+  T.inv_a = 1.0 / a_cc;
   T.beta = beta;
   T.gamma = gamma;
   T.rcut = rcut;
