@@ -13,6 +13,7 @@
 //    (2 - 0.01), b = (E_max + E_min) / 2.
 // Every reduction is two-level (CTA partials, then one CTA in fixed order),
 // so the result is bitwise reproducible.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -168,6 +169,153 @@ __global__ void lanczos_orth_kernel(int64_t n, const double *__restrict__ q, con
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// ---- Lanczos for an FP32 Hamiltonian in double-float arithmetic ----------
+// GB300 issues FP64 at a small fraction of its FP32 rate, and an FP64 SpMV of
+// an FP32 matrix spends a conversion and an FMA on that pipe per stored
+// element.  For FP32 values the vectors are kept as unevaluated sums
+// hi + lo of two floats (about 48 significant bits) and every product and
+// sum is made from the error-free transformations TwoSum (Knuth) and
+// TwoProduct (Dekker, in its FMA form): a + b = s + e and a * b = p + e hold
+// exactly in round-to-nearest FP32.  The Lanczos vectors are stored
+// unnormalised, U_j, with q_j = s_j U_j and s_j = 1 / beta_{j-1} applied on
+// read, so no separate scaling pass is needed and w overwrites U_{j-1}.
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = two_sum(a.hi, b.hi);
+  const dfl t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(s.hi, s.lo + t.lo);
+}
+
+// products that feed TwoSum use __fmul_rn, which the compiler never contracts
+// into an FMA (a contracted sum would break the error-free identities)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl to_dfl(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
+__device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// running sum S += h * (u.hi + u.lo): S.hi collects the rounded products
+// exactly (TwoSum), S.lo the rounding errors and the low-order products
+__device__ __forceinline__ void df_axpy_acc(float h, float2 u, float &shi, float &slo) {
+  const float p = __fmul_rn(h, u.x);
+  const float e = fmaf(h, u.x, -p);
+  const dfl t = two_sum(shi, p);
+  shi = t.hi;
+  slo += t.lo + fmaf(h, u.y, e);
+}
+
+__global__ void lanczos_start_df_kernel(int64_t n, uint64_t seed, float2 *__restrict__ u,
+                                        double *__restrict__ part) {
+  dfl acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const uint64_t z = smix(seed ^ smix((0ull << 32) + (uint64_t)i));
+    const dfl v = to_dfl(static_cast<double>(z >> 11) * 0x1.0p-53 - 0.5);
+    u[i] = make_float2(v.hi, v.lo);
+    acc = df_add(acc, df_mul(v, v));
+  }
+  const double s = block_sum(to_double(acc));
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// w = s_j H U_j - beta_{j-1} s_{j-1} U_{j-1}, written over U_{j-1} (each row
+// is read and written by the same thread); part = sum (s_j U_j) . w
+template <bool PREV>
+__global__ void __launch_bounds__(kB, 3) lanczos_spmv_df_kernel(
+    int64_t n, const int64_t *__restrict__ sp, const int32_t *__restrict__ col, const float *__restrict__ val,
+    const float *__restrict__ diag, const float2 *__restrict__ u, const double *__restrict__ s_j, float2 *prev_w,
+    const double *__restrict__ s_prev, const double *__restrict__ beta_prev, double *__restrict__ part) {
+  constexpr int kW = 16;
+  const dfl sj = to_dfl(*s_j);
+  const dfl c = PREV ? to_dfl(-(*beta_prev) * (*s_prev)) : dfl{0.0f, 0.0f};
+  dfl acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const int64_t sb = __ldg(sp + (i >> 5));
+    const int ww = static_cast<int>((__ldg(sp + (i >> 5) + 1) - sb) >> 5);
+    const int64_t e0 = sb + (i & 31);
+    const float2 ui = __ldg(u + i);
+    float2 pv = make_float2(0.0f, 0.0f);
+    if (PREV) pv = __ldcs(prev_w + i);
+    float shi = 0.0f, slo = 0.0f;
+    if (diag) df_axpy_acc(__ldg(diag + i), ui, shi, slo);
+    if (ww <= kW) {
+      int32_t j[kW];
+      float h[kW];
+#pragma unroll
+      for (int s = 0; s < kW; ++s)
+        if (s < ww) {
+          j[s] = __ldcs(col + e0 + 32 * s);
+          h[s] = __ldcs(val + e0 + 32 * s);
+        }
+#pragma unroll
+      for (int s = 0; s < kW; ++s)
+        if (s < ww) df_axpy_acc(h[s], __ldg(u + j[s]), shi, slo);
+    } else {
+      for (int s = 0; s < ww; ++s) {
+        const int64_t e = e0 + 32 * s;
+        df_axpy_acc(val[e], __ldg(u + col[e]), shi, slo);
+      }
+    }
+    dfl y = df_mul(two_sum(shi, slo), sj);
+    if (PREV) y = df_add(y, df_mul(dfl{pv.x, pv.y}, c));
+    prev_w[i] = make_float2(y.hi, y.lo);
+    acc = df_add(acc, df_mul(df_mul(dfl{ui.x, ui.y}, sj), y));
+  }
+  const double s = block_sum(to_double(acc));
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// w -= alpha_j s_j U_j; part = sum w.w
+__global__ void lanczos_orth_df_kernel(int64_t n, const float2 *__restrict__ u, const double *__restrict__ s_j,
+                                       const double *__restrict__ alpha, float2 *__restrict__ w,
+                                       double *__restrict__ part) {
+  const dfl c = to_dfl(-(*alpha) * (*s_j));
+  dfl acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kB) {
+    const float2 a = __ldg(u + i), b = w[i];
+    const dfl v = df_add(dfl{b.x, b.y}, df_mul(dfl{a.x, a.y}, c));
+    w[i] = make_float2(v.hi, v.lo);
+    acc = df_add(acc, df_mul(v, v));
+  }
+  const double s = block_sum(to_double(acc));
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// beta = sqrt(sum of partials) (skipped when beta is null), inv = 1 / beta
+__global__ void reduce_norm_kernel(const double *__restrict__ part, int nparts, double *__restrict__ beta,
+                                   double *__restrict__ inv) {
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < nparts; c += kB) acc += part[c];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    const double r = sqrt(s);
+    if (beta) *beta = r;
+    *inv = 1.0 / r;
+  }
+}
+
 __device__ int sturm_below(const double *alpha, const double *beta, int m, double x) {
   int count = 0;
   double d = 1.0;
@@ -260,35 +408,70 @@ tb_status run_bounds(int64_t n, const int64_t *sp, const int32_t *col, const val
   double *q0 = cv.take<double>(n), *q1 = cv.take<double>(n), *w = cv.take<double>(n);
   double *part = cv.take<double>(grid), *glo = cv.take<double>(grid), *ghi = cv.take<double>(grid);
   double *alpha = cv.take<double>(k), *beta = cv.take<double>(k), *norm = cv.take<double>(1);
-  double *out = cv.take<double>(8);
+  double *out = cv.take<double>(8), *inv = cv.take<double>(k + 1);
   if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_spectral_bounds: workspace too small");
   gershgorin_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, glo, ghi);
   TB_CHECK_LAUNCH();
-  lanczos_start_kernel<<<grid, kB, 0, st>>>(n, seed, q1, part);
-  TB_CHECK_LAUNCH();
-  reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, norm, 0, 1);
-  TB_CHECK_LAUNCH();
-  scale_kernel<<<grid, kB, 0, st>>>(n, q1, norm);
-  TB_CHECK_LAUNCH();
-  double *q = q1, *qprev = q0;
-  for (int j = 0; j < k; ++j) {
-    lanczos_spmv_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, q, j > 0 ? qprev : nullptr,
-                                                   j > 0 ? beta + (j - 1) : nullptr, w, part);
+  if constexpr (sizeof(valT) == 4) {
+    // double-float Lanczos on two buffers of float2 (inside q0 and q1)
+    float2 *ua = reinterpret_cast<float2 *>(q0), *ub = reinterpret_cast<float2 *>(q1);
+    // one wave of resident CTAs for the SpMV (its grid-stride loop has no tail wave)
+    static int per_sm = 0;
+    if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_spmv_df_kernel<true>, kB,
+                                                                      0) != cudaSuccess ||
+                        per_sm <= 0))
+      per_sm = 3;
+    const int gs = std::min<int64_t>(grid, (int64_t)per_sm * sm_count());
+    lanczos_start_df_kernel<<<grid, kB, 0, st>>>(n, seed, ua, part);
     TB_CHECK_LAUNCH();
-    reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, alpha, j, 0);
+    reduce_norm_kernel<<<1, kB, 0, st>>>(part, grid, nullptr, inv);
     TB_CHECK_LAUNCH();
-    if (j == k - 1) break;
-    lanczos_orth_kernel<<<grid, kB, 0, st>>>(n, q, alpha + j, w, part);
+    for (int j = 0; j < k; ++j) {
+      if (j == 0)
+        lanczos_spmv_df_kernel<false><<<gs, kB, 0, st>>>(n, sp, col, val, diag, ua, inv, ub, nullptr, nullptr,
+                                                         part);
+      else
+        lanczos_spmv_df_kernel<true><<<gs, kB, 0, st>>>(n, sp, col, val, diag, ua, inv + j, ub, inv + j - 1,
+                                                        beta + j - 1, part);
+      TB_CHECK_LAUNCH();
+      reduce_scalar_kernel<<<1, kB, 0, st>>>(part, gs, alpha, j, 0);
+      TB_CHECK_LAUNCH();
+      if (j == k - 1) break;
+      lanczos_orth_df_kernel<<<grid, kB, 0, st>>>(n, ua, inv + j, alpha + j, ub, part);
+      TB_CHECK_LAUNCH();
+      reduce_norm_kernel<<<1, kB, 0, st>>>(part, grid, beta + j, inv + j + 1);
+      TB_CHECK_LAUNCH();
+      float2 *t = ua;  // U_{j+1} = w; U_j becomes the previous vector
+      ua = ub;
+      ub = t;
+    }
+  } else {
+    lanczos_start_kernel<<<grid, kB, 0, st>>>(n, seed, q1, part);
     TB_CHECK_LAUNCH();
-    reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, beta, j, 1);
+    reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, norm, 0, 1);
     TB_CHECK_LAUNCH();
-    // q_{j+1} = w / beta_j, written over q_{j-1}
-    scale_kernel<<<grid, kB, 0, st>>>(n, w, beta + j);
-    double *t = qprev;
-    qprev = q;
-    q = w;
-    w = t;
+    scale_kernel<<<grid, kB, 0, st>>>(n, q1, norm);
     TB_CHECK_LAUNCH();
+    double *q = q1, *qprev = q0;
+    for (int j = 0; j < k; ++j) {
+      lanczos_spmv_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, q, j > 0 ? qprev : nullptr,
+                                                     j > 0 ? beta + (j - 1) : nullptr, w, part);
+      TB_CHECK_LAUNCH();
+      reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, alpha, j, 0);
+      TB_CHECK_LAUNCH();
+      if (j == k - 1) break;
+      lanczos_orth_kernel<<<grid, kB, 0, st>>>(n, q, alpha + j, w, part);
+      TB_CHECK_LAUNCH();
+      reduce_scalar_kernel<<<1, kB, 0, st>>>(part, grid, beta, j, 1);
+      TB_CHECK_LAUNCH();
+      // q_{j+1} = w / beta_j, written over q_{j-1}
+      scale_kernel<<<grid, kB, 0, st>>>(n, w, beta + j);
+      double *t = qprev;
+      qprev = q;
+      q = w;
+      w = t;
+      TB_CHECK_LAUNCH();
+    }
   }
   finish_bounds_kernel<<<1, 32, 0, st>>>(alpha, beta, k, glo, ghi, grid, 0.01, 0.01, out);
   TB_CHECK_LAUNCH();
@@ -319,6 +502,7 @@ extern "C" size_t tb_spectral_bounds_workspace_size(int64_t n, int32_t lanczos_s
   cv.take<double>(lanczos_steps);
   cv.take<double>(1);
   cv.take<double>(8);
+  cv.take<double>(lanczos_steps + 1);
   return cv.used + 256;
 }
 

@@ -161,6 +161,35 @@ def test_spectral_bounds_match_oracle(g):
     np.testing.assert_allclose([bd.g_min, bd.g_max], [gmin, gmax], rtol=1e-13)
 
 
+@pytest.mark.parametrize("name", ["prim800", "junction_ragged", "rect100k_ragged"])
+def test_spectral_bounds_fp32_values_match_oracle(g, name):
+    """FP32 Hamiltonian: the GPU Lanczos runs in double-float arithmetic
+    (about 48 significant bits); against the FP64 oracle on the same
+    FP32-rounded values the bounds agree to rel 1e-9, and both enclose the
+    spectrum.  The 100k-atom case spans many CTAs with a ragged last slice."""
+    from tests.sell_helpers import sell_matrix
+    if name == "prim800":
+        s, params = synth.graphene_primitive(20, 20, 0.05, 1001), synth.teacher_graphene()
+    elif name == "junction_ragged":
+        s, params = synth.hbn_graphene_junction(6, 7, 0.1, 9), synth.teacher_hbn_graphene()
+        s.positions, s.species = s.positions[:-5].copy(), s.species[:-5].copy()
+    else:
+        s, params = synth.graphene_rect(101, 251, 0.1, 31), synth.teacher_graphene()
+    indptr, idx, t, eps = _oracle_teacher(s, params)
+    t32 = t.astype(np.float32).astype(np.float64)
+    e32 = eps.astype(np.float32).astype(np.float64)
+    Hd = sell_matrix(indptr, idx, t32, e32, s.n, torch.float32)
+    bd = g.spectral_bounds(Hd, 64, synth.LANCZOS_SEED)
+    Hc = oha.csr_hamiltonian(s.n, indptr, idx, t32, e32)
+    emin, emax, a, b = obo.spectral_bounds(Hc, 64, synth.LANCZOS_SEED)
+    np.testing.assert_allclose([bd.emin, bd.emax, bd.a, bd.b], [emin, emax, a, b], rtol=1e-9, atol=1e-12)
+    gmin, gmax = obo.gershgorin(Hc)
+    np.testing.assert_allclose([bd.g_min, bd.g_max], [gmin, gmax], rtol=1e-13)
+    if s.n <= 1000:
+        ev = np.linalg.eigvalsh(Hc.toarray())
+        assert bd.emin <= ev[0] and ev[-1] <= bd.emax
+
+
 def test_plain_path_end_to_end(g):
     """positions -> GPU path -> DOS, against the oracle path on the same input."""
     w = synth.WORKLOADS["graphene-800-fp64"]
