@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 1
+#define GPUTB_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -240,9 +240,14 @@ TB_API tb_status kpm_dos(const double *mu_r, int32_t R, int32_t M, int32_t kerne
  *   cnt         device int32 [N] output: neighbours per row
  *   ncount      device int32 [N] output or NULL
  *   total_out   host int64: number of SELL elements (slice_ptr[last])
- * Synchronises `stream`.  Positions must be finite (TB_ERR_NOT_FINITE).
+ * Synchronises `stream`.  Positions must be finite (TB_ERR_NOT_FINITE), and
+ * every wrapped coordinate within 2^20 * rcut of the origin
+ * (TB_ERR_INVALID_ARG): the FP32 pair screen's error bound assumes it.
+ * The workspace size (0 for an invalid box, rcut or max_width) depends on
+ * max_width: the search keeps every row's sorted list once.
  * ------------------------------------------------------------------- */
-TB_API size_t tb_neighbors_workspace_size(int64_t n, const double *box, const int32_t *pbc, double rcut);
+TB_API size_t tb_neighbors_workspace_size(int64_t n, const double *box, const int32_t *pbc, double rcut,
+                                          int32_t max_width);
 
 TB_API tb_status tb_build_neighbors(const double *positions, int64_t n, const double *box,
                                     const int32_t *pbc, double rcut, double r_count,

@@ -3,16 +3,21 @@
 // straight into the SELL-32 column layout of the Hamiltonian.
 //
 // Passes (all on the device, O(N)):
-//  1. cell_bin      fractional coordinates -> cell id, per-cell counts
+//  1. cell_bin      wrapped position and cell of every atom, per-cell counts
 //  2. scan          cell offsets (exclusive prefix sum)
-//  3. cell_scatter  atoms and SoA positions in cell order
-//  4. count         per-row neighbour count cnt_i and n_i (r < r_count)
+//  3. cell_scatter  positions in cell order: FP64, and split into two floats
+//  4. search        one thread per row: neighbour count cnt_i, n_i
+//                   (r < r_count) and the row's sorted list, once
 //  5. slice widths  max cnt over each 32-row slice, overflow check, scan
-//  6. fill          sorted neighbour indices of each row into col
-// Pairs are screened in FP32 with a safety margin; only candidates whose
-// |d|^2 lies within a relative 4e-6 of r_cut^2 (or r_count^2) take the
-// explicitly rounded FP64 test, so membership is decided as the FP64
-// definition states at a fraction of the FP64 work (GB300's FP64 rate is low).
+//  6. compact       the sorted lists into the SELL-32 column array
+// Pairs are screened in FP32: positions are stored as float pairs hi + lo
+// (hi = fl32(x), lo = fl32(x - hi)) so that the difference of two nearby
+// atoms is formed as (hi_j - hi_i) + (lo_j - lo_i) to a few FP32 ulps of
+// |d| whatever the coordinates' magnitude.  Only candidates whose |d|^2
+// lies within a relative 4e-6 of r_cut^2 (or r_count^2) take the explicitly
+// rounded FP64 test, so membership is decided as the FP64 definition states
+// with almost no FP64 work (GB300's FP64 rate is low).
+#include <algorithm>
 #include <cmath>
 
 #include "geometry.cuh"
@@ -44,6 +49,9 @@ tb_status make_box(const double *b, const int32_t *pbc, double rcut, Box *out) {
 namespace {
 
 constexpr int kMaxWidth = 64;   // hard cap on slots per row (local sort buffer)
+// |wrapped coordinate| <= kCoordRange * rcut keeps the float-pair screen
+// within its margin (the pair split leaves 2^-48 |x| of each coordinate)
+constexpr double kCoordRange = 1048576.0;
 
 struct Grid {
   int nc[3];       // cells per direction
@@ -77,63 +85,73 @@ __device__ __forceinline__ int64_t cell_index(const Grid &G, int c1, int c2, int
   return ((int64_t)c3 * G.nc[1] + c2) * G.nc[0] + c1;
 }
 
-__global__ void cell_bin_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G, int32_t *__restrict__ cell,
+// wrapped positions (input order) and cells; flags |= 4 for a non-finite
+// position, |= 8 for a coordinate beyond the float-pair screen's range
+__global__ void cell_bin_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G, double max_abs,
+                                int32_t *__restrict__ cell, double *__restrict__ pw_out,
                                 unsigned long long *__restrict__ count, int *__restrict__ flags) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  double3 pw = make_double3(0.0, 0.0, 0.0);
+  int64_t id = 0;
   if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
     atomicOr(flags, 4);
-    cell[i] = 0;
-    atomicAdd(count, 1ull);
-    return;
+  } else {
+    int3 c;
+    wrap_and_bin(B, G, x, y, z, pw, c);
+    id = cell_index(G, c.x, c.y, c.z);
+    if (fabs(pw.x) > max_abs || fabs(pw.y) > max_abs || fabs(pw.z) > max_abs) atomicOr(flags, 8);
   }
-  double3 pw;
-  int3 c;
-  wrap_and_bin(B, G, x, y, z, pw, c);
-  const int64_t id = cell_index(G, c.x, c.y, c.z);
   cell[i] = static_cast<int32_t>(id);
+  pw_out[3 * i] = pw.x;
+  pw_out[3 * i + 1] = pw.y;
+  pw_out[3 * i + 2] = pw.z;
   atomicAdd(count + id, 1ull);
 }
 
-// atoms of each cell in cell order, with their wrapped positions (SoA)
-__global__ void cell_scatter_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G,
-                                    const int32_t *__restrict__ cell, unsigned long long *__restrict__ cursor,
-                                    int32_t *__restrict__ atom, double *__restrict__ px, double *__restrict__ py,
-                                    double *__restrict__ pz) {
+// positions in cell order: FP64 (for the exact test) and as float pairs
+// (hi.w carries the atom index); slot_of[i] = the slot of atom i
+__global__ void cell_scatter_kernel(int64_t n, const int32_t *__restrict__ cell, const double *__restrict__ pw,
+                                    unsigned long long *__restrict__ cursor, int32_t *__restrict__ slot_of,
+                                    float4 *__restrict__ hi, float4 *__restrict__ lo, double *__restrict__ px,
+                                    double *__restrict__ py, double *__restrict__ pz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double3 pw;
-  int3 c;
-  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pw, c);
   const int64_t slot = (int64_t)atomicAdd(cursor + cell[i], 1ull);
-  atom[slot] = static_cast<int32_t>(i);
-  px[slot] = pw.x;
-  py[slot] = pw.y;
-  pz[slot] = pw.z;
+  slot_of[i] = static_cast<int32_t>(slot);
+  const double x = pw[3 * i], y = pw[3 * i + 1], z = pw[3 * i + 2];
+  px[slot] = x;
+  py[slot] = y;
+  pz[slot] = z;
+  const float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
+  hi[slot] = make_float4(xh, yh, zh, __int_as_float(static_cast<int32_t>(i)));
+  lo[slot] = make_float4(__double2float_rn(__dsub_rn(x, (double)xh)), __double2float_rn(__dsub_rn(y, (double)yh)),
+                         __double2float_rn(__dsub_rn(z, (double)zh)), 0.0f);
 }
 
-// Search parameters: thresholds on r^2 with FP32 safety margins.  A
-// candidate's FP64 displacement d is rounded to FP32 and its FP32 |d|^2 is
-// within a relative 1e-6 of the exact value, so |d|^2 < lo means inside,
-// >= hi outside; only candidates between lo and hi take the explicitly
-// rounded FP64 test ((dx*dx + dy*dy) + dz*dz < r^2).
+// Search parameters: thresholds on r^2 with FP32 safety margins.  The FP32
+// |d|^2 of a candidate is within a relative 1e-6 of the exact value (float
+// pair differences, coordinates below 2^20 r_cut), so |d|^2 < lo means
+// inside, >= hi outside; only candidates between lo and hi take the
+// explicitly rounded FP64 test ((dx*dx + dy*dy) + dz*dz < r^2).
 struct Radii {
   double rc2, rn2;            // exact thresholds (r_count^2 < 0 disables)
   float rc_lo, rc_hi, rn_lo, rn_hi;
 };
 
 // Visit every neighbour j of atom i: f(j, within_r_count).  Neighbour cells
-// are visited with the lattice shift of their periodic image, so a pair
-// costs one FP64 difference per component; directions with fewer than 3
-// cells visit every cell with shifts -1, 0, +1 (only one image of j can be
-// within r_cut because the periodic widths are at least 2 r_cut).
+// are visited with the lattice shift of their periodic image (q = pw_i - S,
+// the displacement to the image of j is pw_j - q); directions with fewer
+// than 3 cells visit every cell with shifts -1, 0, +1 (only one image of j
+// can be within r_cut because the periodic widths are at least 2 r_cut).
 template <typename F>
 __device__ __forceinline__ void for_each_neighbor(const Box &B, const Grid &G, const int64_t *__restrict__ start,
-                                                  const int32_t *__restrict__ atom, const double *__restrict__ px,
-                                                  const double *__restrict__ py, const double *__restrict__ pz,
-                                                  int64_t i, const double3 &pwi, const int3 &ci, const Radii &rad,
-                                                  F &&f) {
+                                                  const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                                                  const double *__restrict__ px, const double *__restrict__ py,
+                                                  const double *__restrict__ pz, int64_t i, const double3 &pwi,
+                                                  const float4 &hi_i, const float4 &lo_i, const int3 &ci,
+                                                  const Radii &rad, F &&f) {
   int cells[3][6], shifts[3][6], cnt[3];
   const int cc[3] = {ci.x, ci.y, ci.z};
   const int per[3] = {B.p1, B.p2, B.p3};
@@ -162,32 +180,47 @@ __device__ __forceinline__ void for_each_neighbor(const Box &B, const Grid &G, c
   for (int q3 = 0; q3 < cnt[2]; ++q3)
     for (int q2 = 0; q2 < cnt[1]; ++q2)
       for (int q1 = 0; q1 < cnt[0]; ++q1) {
-        const double s1 = shifts[0][q1], s2 = shifts[1][q2], s3 = shifts[2][q3];
-        // q = pw_i - S: the displacement to the image of j is pw_j - q
-        const double qx = pwi.x - (s1 * B.ax + s2 * B.bx + s3 * B.cx);
-        const double qy = pwi.y - (s2 * B.by + s3 * B.cy);
-        const double qz = pwi.z - s3 * B.cz;
+        const int s1 = shifts[0][q1], s2 = shifts[1][q2], s3 = shifts[2][q3];
+        double qx = pwi.x, qy = pwi.y, qz = pwi.z;
+        float hx = hi_i.x, hy = hi_i.y, hz = hi_i.z, lx = lo_i.x, ly = lo_i.y, lz = lo_i.z;
+        if (s1 | s2 | s3) {  // image cell: FP64 q, then its float pair
+          qx = pwi.x - ((double)s1 * B.ax + (double)s2 * B.bx + (double)s3 * B.cx);
+          qy = pwi.y - ((double)s2 * B.by + (double)s3 * B.cy);
+          qz = pwi.z - (double)s3 * B.cz;
+          hx = __double2float_rn(qx);
+          hy = __double2float_rn(qy);
+          hz = __double2float_rn(qz);
+          lx = __double2float_rn(__dsub_rn(qx, (double)hx));
+          ly = __double2float_rn(__dsub_rn(qy, (double)hy));
+          lz = __double2float_rn(__dsub_rn(qz, (double)hz));
+        }
         const int64_t c = cell_index(G, cells[0][q1], cells[1][q2], cells[2][q3]);
         const int64_t a0 = __ldg(start + c), a1 = __ldg(start + c + 1);
         for (int64_t s = a0; s < a1; ++s) {
-          const double dx = __dsub_rn(__ldg(px + s), qx);
-          const double dy = __dsub_rn(__ldg(py + s), qy);
-          const double dz = __dsub_rn(__ldg(pz + s), qz);
-          const float fx = static_cast<float>(dx), fy = static_cast<float>(dy), fz = static_cast<float>(dz);
+          const float4 h = __ldg(hi + s), l = __ldg(lo + s);
+          const float fx = __fadd_rn(__fsub_rn(h.x, hx), __fsub_rn(l.x, lx));
+          const float fy = __fadd_rn(__fsub_rn(h.y, hy), __fsub_rn(l.y, ly));
+          const float fz = __fadd_rn(__fsub_rn(h.z, hz), __fsub_rn(l.z, lz));
           const float r2f = fx * fx + fy * fy + fz * fz;
           if (r2f >= rad.rc_hi) continue;
-          const int32_t j = __ldg(atom + s);
+          const int32_t j = __float_as_int(h.w);
           if (j == i) continue;
           double r2 = -1.0;
+          auto exact = [&]() {
+            const double dx = __dsub_rn(__ldg(px + s), qx);
+            const double dy = __dsub_rn(__ldg(py + s), qy);
+            const double dz = __dsub_rn(__ldg(pz + s), qz);
+            return sq_norm(make_double3(dx, dy, dz));
+          };
           if (r2f >= rad.rc_lo) {
-            r2 = sq_norm(make_double3(dx, dy, dz));
+            r2 = exact();
             if (!(r2 < rad.rc2)) continue;
           }
           bool close = false;
           if (rad.rn2 > 0.0) {
             if (r2f < rad.rn_lo) close = true;
             else if (r2f < rad.rn_hi) {
-              if (r2 < 0.0) r2 = sq_norm(make_double3(dx, dy, dz));
+              if (r2 < 0.0) r2 = exact();
               close = r2 < rad.rn2;
             }
           }
@@ -196,23 +229,39 @@ __device__ __forceinline__ void for_each_neighbor(const Box &B, const Grid &G, c
       }
 }
 
-__global__ void count_kernel(const double *__restrict__ pos, int64_t n, Box B, Grid G,
-                             const int64_t *__restrict__ start, const int32_t *__restrict__ atom,
-                             const double *__restrict__ px, const double *__restrict__ py,
-                             const double *__restrict__ pz, Radii rad, int32_t *__restrict__ cnt,
-                             int32_t *__restrict__ ncount) {
+// One thread per row: count, n_i and the sorted list (first cap entries)
+// into the fixed-width buffer list[slice][cap][32].
+__global__ void search_kernel(int64_t n, Box B, Grid G, const int64_t *__restrict__ start,
+                              const int32_t *__restrict__ cell, const int32_t *__restrict__ slot_of,
+                              const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                              const double *__restrict__ px, const double *__restrict__ py,
+                              const double *__restrict__ pz, Radii rad, int cap, int32_t *__restrict__ cnt,
+                              int32_t *__restrict__ ncount, int32_t *__restrict__ list) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double3 pwi;
-  int3 ci;
-  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pwi, ci);
-  int c = 0, nc = 0;
-  for_each_neighbor(B, G, start, atom, px, py, pz, i, pwi, ci, rad, [&](int32_t, bool close) {
+  const int32_t slot = slot_of[i];
+  const int32_t id = cell[i];
+  const int3 ci = make_int3(id % G.nc[0], (id / G.nc[0]) % G.nc[1], id / (G.nc[0] * G.nc[1]));
+  const double3 pwi = make_double3(px[slot], py[slot], pz[slot]);
+  const float4 hi_i = hi[slot], lo_i = lo[slot];
+  int32_t lst[kMaxWidth];
+  int m = 0, c = 0, nclose = 0;
+  for_each_neighbor(B, G, start, hi, lo, px, py, pz, i, pwi, hi_i, lo_i, ci, rad, [&](int32_t j, bool close) {
     ++c;
-    if (close) ++nc;
+    if (close) ++nclose;
+    if (m < cap) {  // insertion sort, ascending j
+      int p = m++;
+      while (p > 0 && lst[p - 1] > j) {
+        lst[p] = lst[p - 1];
+        --p;
+      }
+      lst[p] = j;
+    }
   });
   cnt[i] = c;
-  if (ncount) ncount[i] = nc;
+  if (ncount) ncount[i] = nclose;
+  int32_t *dst = list + (i >> 5) * 32 * (int64_t)cap + (i & 31);
+  for (int s = 0; s < m; ++s) dst[32 * s] = lst[s];
 }
 
 // slice width = 32 * max(cnt) over the slice; flags |= 1 on overflow
@@ -232,36 +281,22 @@ __global__ void slice_width_kernel(const int32_t *__restrict__ cnt, int64_t n, i
   sizes[k] = 32 * (int64_t)w;
 }
 
-__global__ void fill_kernel(const double *__restrict__ pos, int64_t n, int64_t n_slices, Box B, Grid G,
-                            const int64_t *__restrict__ start, const int32_t *__restrict__ atom,
-                            const double *__restrict__ px, const double *__restrict__ py,
-                            const double *__restrict__ pz, Radii rad, const int64_t *__restrict__ slice_ptr,
-                            int32_t *__restrict__ col) {
+// sorted lists -> SELL-32 columns (padding col = i, phantom rows col 0)
+__global__ void compact_kernel(int64_t n, int64_t n_slices, const int64_t *__restrict__ slice_ptr,
+                               const int32_t *__restrict__ cnt, const int32_t *__restrict__ list, int cap,
+                               int32_t *__restrict__ col) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_slices * 32) return;
   const int64_t k = i >> 5;
   const int64_t base = slice_ptr[k] + (i & 31);
   const int w = static_cast<int>((slice_ptr[k + 1] - slice_ptr[k]) >> 5);
-  if (i >= n) {  // phantom rows of the last slice
+  if (i >= n) {
     for (int s = 0; s < w; ++s) col[base + 32 * s] = 0;
     return;
   }
-  double3 pwi;
-  int3 ci;
-  wrap_and_bin(B, G, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pwi, ci);
-  int32_t list[kMaxWidth];
-  int m = 0;
-  for_each_neighbor(B, G, start, atom, px, py, pz, i, pwi, ci, rad, [&](int32_t j, bool) {
-    if (m < w) {  // insertion sort, ascending j
-      int p = m++;
-      while (p > 0 && list[p - 1] > j) {
-        list[p] = list[p - 1];
-        --p;
-      }
-      list[p] = j;
-    }
-  });
-  for (int s = 0; s < w; ++s) col[base + 32 * s] = s < m ? list[s] : static_cast<int32_t>(i);
+  const int m = cnt[i];
+  const int32_t *src = list + k * 32 * (int64_t)cap + (i & 31);
+  for (int s = 0; s < w; ++s) col[base + 32 * s] = s < m ? __ldcs(src + 32 * s) : static_cast<int32_t>(i);
 }
 
 __global__ void read_total_kernel(const int64_t *slice_ptr, int64_t n_slices, int64_t *dst) {
@@ -292,23 +327,32 @@ Grid make_grid(const Box &B, double rcut) {
 }
 
 struct NeighborWs {
-  int32_t *cell, *atom;
+  int32_t *cell, *slot_of;
   unsigned long long *count, *cursor;
-  double *px, *py, *pz;
+  double *pw;             // [N][3] wrapped positions, input order (until the scatter)
+  int32_t *list;          // [ceil(N/32)][cap][32] sorted lists (shares pw's bytes)
+  double *px, *py, *pz;   // wrapped positions, cell order
+  float4 *hi, *lo;        // the same as float pairs
   int64_t *sizes, *total;
   int *flags;
   void *scan_ws;
 };
 
-size_t carve(Carver &cv, int64_t n, int64_t ncell, NeighborWs *w) {
+size_t carve(Carver &cv, int64_t n, int64_t ncell, int cap, NeighborWs *w) {
   const int64_t n_slices = (n + 31) / 32;
   w->cell = cv.take<int32_t>(n);
-  w->atom = cv.take<int32_t>(n);
+  w->slot_of = cv.take<int32_t>(n);
   w->count = cv.take<unsigned long long>(ncell + 1);
   w->cursor = cv.take<unsigned long long>(ncell + 1);
+  const size_t shared = std::max<size_t>(3 * sizeof(double) * (size_t)n, sizeof(int32_t) * (size_t)n_slices * 32 * cap);
+  char *u = cv.take<char>(shared);
+  w->pw = reinterpret_cast<double *>(u);
+  w->list = reinterpret_cast<int32_t *>(u);
   w->px = cv.take<double>(n);
   w->py = cv.take<double>(n);
   w->pz = cv.take<double>(n);
+  w->hi = cv.take<float4>(n);
+  w->lo = cv.take<float4>(n);
   w->sizes = cv.take<int64_t>(n_slices + 1);
   w->total = cv.take<int64_t>(4);
   w->flags = cv.take<int>(4);
@@ -322,13 +366,15 @@ size_t carve(Carver &cv, int64_t n, int64_t ncell, NeighborWs *w) {
 
 using namespace gputb;
 
-extern "C" size_t tb_neighbors_workspace_size(int64_t n, const double *box, const int32_t *pbc, double rcut) {
+extern "C" size_t tb_neighbors_workspace_size(int64_t n, const double *box, const int32_t *pbc, double rcut,
+                                               int32_t max_width) {
   Box B;
-  if (n <= 0 || !(rcut > 0.0) || make_box(box, pbc, rcut, &B) != TB_OK) return 0;
+  if (n <= 0 || !(rcut > 0.0) || max_width < 1 || max_width > kMaxWidth || make_box(box, pbc, rcut, &B) != TB_OK)
+    return 0;
   const Grid G = make_grid(B, rcut);
   Carver cv(nullptr, 0);
   NeighborWs w;
-  return carve(cv, n, G.ncell, &w) + 256;
+  return carve(cv, n, G.ncell, max_width, &w) + 256;
 }
 
 extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, const double *box, const int32_t *pbc,
@@ -350,7 +396,7 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver cv(workspace, workspace_bytes);
   NeighborWs w;
-  carve(cv, n, G.ncell, &w);
+  carve(cv, n, G.ncell, max_width, &w);
   if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_build_neighbors: workspace too small");
   const int64_t n_slices = (n + 31) / 32;
   const unsigned nb = (unsigned)((n + 255) / 256);
@@ -364,15 +410,16 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
 
   TB_CUDA(cudaMemsetAsync(w.count, 0, (G.ncell + 1) * sizeof(unsigned long long), st));
   TB_CUDA(cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
-  cell_bin_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, w.cell, w.count, w.flags);
+  cell_bin_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, kCoordRange * rcut, w.cell, w.pw, w.count, w.flags);
   TB_CHECK_LAUNCH();
   int64_t *start = reinterpret_cast<int64_t *>(w.count);
   s = exclusive_scan_i64(start, start, G.ncell + 1, w.total, w.scan_ws, st);
   if (s != TB_OK) return s;
   TB_CUDA(cudaMemcpyAsync(w.cursor, w.count, (G.ncell + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-  cell_scatter_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, w.cell, w.cursor, w.atom, w.px, w.py, w.pz);
+  cell_scatter_kernel<<<nb, 256, 0, st>>>(n, w.cell, w.pw, w.cursor, w.slot_of, w.hi, w.lo, w.px, w.py, w.pz);
   TB_CHECK_LAUNCH();
-  count_kernel<<<nb, 256, 0, st>>>(positions, n, B, G, start, w.atom, w.px, w.py, w.pz, rad, cnt, ncount);
+  search_kernel<<<nb, 256, 0, st>>>(n, B, G, start, w.cell, w.slot_of, w.hi, w.lo, w.px, w.py, w.pz, rad,
+                                    max_width, cnt, ncount, w.list);
   TB_CHECK_LAUNCH();
   TB_CUDA(cudaMemsetAsync(w.sizes, 0, (n_slices + 1) * sizeof(int64_t), st));
   slice_width_kernel<<<(unsigned)((n_slices + 255) / 256), 256, 0, st>>>(cnt, n, n_slices, max_width, w.sizes,
@@ -388,13 +435,15 @@ extern "C" tb_status tb_build_neighbors(const double *positions, int64_t n, cons
   const int64_t total = host[1];
   *total_out = total;
   if (hflags & 4) return fail(TB_ERR_NOT_FINITE, "tb_build_neighbors: non-finite position");
+  if (hflags & 8)
+    return fail(TB_ERR_INVALID_ARG, "tb_build_neighbors: a wrapped coordinate exceeds %g * rcut", kCoordRange);
   if (hflags & 1) return fail(TB_ERR_ELL_OVERFLOW, "tb_build_neighbors: a row has more than %d neighbours", max_width);
   if (total > col_capacity || (total > 0 && !col))
     return fail(TB_ERR_ELL_OVERFLOW, "tb_build_neighbors: col needs %lld elements, capacity %lld", (long long)total,
                 (long long)col_capacity);
   if (total > 0) {
-    fill_kernel<<<(unsigned)((n_slices * 32 + 255) / 256), 256, 0, st>>>(
-        positions, n, n_slices, B, G, start, w.atom, w.px, w.py, w.pz, rad, slice_ptr, col);
+    compact_kernel<<<(unsigned)((n_slices * 32 + 255) / 256), 256, 0, st>>>(n, n_slices, slice_ptr, cnt, w.list,
+                                                                            max_width, col);
     TB_CHECK_LAUNCH();
   }
   return TB_OK;

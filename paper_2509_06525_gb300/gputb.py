@@ -48,7 +48,7 @@ SIGNATURES = {
     "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
-    "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl]),
+    "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_i32]),
     "tb_build_neighbors": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_vp, _c_vp, _c_i64,
                                     _c_vp, _c_vp, ctypes.POINTER(_c_i64), _c_vp, _c_sz, _c_vp]),
     "tb_build_hamiltonian_teacher": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
@@ -86,6 +86,9 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
+ABI_VERSION = 2   # GPUTB_ABI_VERSION of include/gputb.h
+
+
 def lib() -> ctypes.CDLL:
     """Load libgputb.so (raises if it was not built)."""
     global _lib
@@ -97,6 +100,9 @@ def lib() -> ctypes.CDLL:
             fn = getattr(handle, name)
             fn.restype = res
             fn.argtypes = args
+        if handle.tb_abi_version() != ABI_VERSION:
+            raise ImportError(f"{LIB_PATH} has ABI {handle.tb_abi_version()}, the binding expects {ABI_VERSION}; "
+                              "rebuild it with paper_2509_06525_gb300.build.build(force=True)")
         _lib = handle
     return _lib
 
@@ -255,7 +261,7 @@ def build_neighbors(positions: torch.Tensor, box, pbc, rcut: float, r_count: flo
     n = positions.shape[0]
     dev = positions.device
     b, p, bptr, pptr = _host_box(box, pbc)
-    need = L.tb_neighbors_workspace_size(n, bptr, pptr, float(rcut))
+    need = L.tb_neighbors_workspace_size(n, bptr, pptr, float(rcut), int(max_width))
     if need == 0:
         raise GputbError("tb_neighbors_workspace_size", TB_ERR_BOX, lib().tb_last_error().decode())
     ws = _workspace(need, dev)
