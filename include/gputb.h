@@ -130,10 +130,14 @@ TB_API int64_t tb_launch_count(void);
 TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_t precision);
 
 /* Tuning hook for the Chebyshev-step kernel used by kpm_moments and
- * kpm_moments_noalloc: 0 = automatic (the bulk-copy pipeline wherever its
- * tile geometry fits, else direct loads), 1 = direct loads, 2 = pipeline
- * where it fits.  Process-wide; both variants compute the same result.
- * Query workspace sizes after setting it. */
+ * kpm_moments_noalloc: 0 = automatic (the bulk-copy pipeline where several
+ * threads share a row and its tile geometry fits, else direct loads),
+ * 1 = direct loads, 2 = pipeline where it fits, 3 = two Chebyshev steps per
+ * cooperative launch with the matrix read once (temporal blocking; doubling
+ * mode of kpm_moments only, other calls use single steps).  Process-wide;
+ * every variant computes the same moments up to the order of the partial
+ * sums (each variant is bitwise reproducible).  Query workspace sizes after
+ * setting it. */
 TB_API tb_status tb_kpm_set_variant(int32_t variant);
 
 TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col,

@@ -35,6 +35,12 @@ struct Carver {
   bool ok() const { return used <= cap; }
 };
 
+// Exclusive scan of int64 values (in may equal out); total (device) receives
+// the sum.  Workspace from scan_workspace_bytes(n).  (scan.cu)
+size_t scan_workspace_bytes(int64_t n);
+tb_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *ws,
+                             cudaStream_t st);
+
 }  // namespace gputb
 
 #define TB_CUDA(call)                                                         \

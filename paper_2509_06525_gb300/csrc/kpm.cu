@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "kpm_common.cuh"
+#include "kpm_fused.cuh"
 
 namespace gputb {
 namespace {
@@ -43,6 +44,7 @@ struct BatchTables {
   int n_snap = 0;
 };
 constexpr int kBatchTile = 256;
+constexpr int kMaxPairGrid = 4096;   // CTAs of a cooperative pair launch (at most)
 
 // v0[i, r] = exp(2 pi i u(seed, r, i)) (batched: u(seed + s, r, i - row0[s])
 // on the real rows of snapshot s, 0 on padding rows); partials of
@@ -472,7 +474,8 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 }
 
 // kernel variant for the Chebyshev step: 0 = choose automatically,
-// 1 = direct loads, 2 = bulk-copy pipeline (set with tb_kpm_set_variant)
+// 1 = direct loads, 2 = bulk-copy pipeline, 3 = two steps per launch
+// (doubling mode; set with tb_kpm_set_variant)
 int g_kpm_variant = 0;
 
 // batched: mu[s][r][m] from the RPB-row block partials of snapshot s (block order)
@@ -557,7 +560,101 @@ struct KpmRunner {
     for (int k = 0; k < 3; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
     cv.take<double>((size_t)(M + 1) * (segmented ? blocks(n) : grid_for(n)) * R);
     cv.take<int>(4);
+    if (!segmented) {
+      PairWs pw;
+      carve_pair(cv, n, M, &pw);
+    }
     return cv.used + 256;
+  }
+
+  // ---- two steps per launch (kpm_fused.cuh) ----
+  struct PairWs {
+    PairPlan plan;
+    int32_t *tasks;
+    int2 *wait;
+    int *lo, *hi, *rlo, *rhi, *key, *fill;
+    int64_t *gsize, *gtotal;
+    void *scan_ws;
+    double *bpart;
+  };
+
+  static void carve_pair(Carver &cv, int64_t n, int M, PairWs *w) {
+    (void)M;
+    const int64_t nb = blocks(n);
+    w->tasks = cv.take<int32_t>(2 * nb);
+    w->wait = cv.take<int2>(nb);
+    w->plan.done = cv.take<int>(nb);
+    w->plan.cta_s1 = cv.take<int>(kMaxPairGrid);
+    w->lo = cv.take<int>(nb);
+    w->hi = cv.take<int>(nb);
+    w->rlo = cv.take<int>(nb);
+    w->rhi = cv.take<int>(nb);
+    w->key = cv.take<int>(nb);
+    w->fill = cv.take<int>(nb);
+    w->gsize = cv.take<int64_t>(nb + 1);
+    w->gtotal = cv.take<int64_t>(1);
+    w->scan_ws = cv.take<char>(scan_workspace_bytes(nb + 1));
+    w->bpart = cv.take<double>((size_t)4 * nb * R);
+    w->plan.tasks = w->tasks;
+    w->plan.wait = w->wait;
+    w->plan.nb = nb;
+  }
+
+  // opt-in only: on GB300 the per-task latency chain (task, slice offsets,
+  // columns, gathers) with one row per thread costs more than the L2 reuse
+  // saves (measured 2.1x slower than single steps at 1e8 atoms, R = 1)
+  static bool use_pair(bool dbl) { return dbl && g_kpm_variant == 3; }
+
+  // resident CTAs of the cooperative pair launch
+  static int pair_grid() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_pair_kernel<real, valT, R, CPT>, kBlock, 0) !=
+              cudaSuccess ||
+          b <= 0)
+        b = 1;
+      per_sm = b;
+    }
+    const int g = per_sm * sm_count();
+    return g < kMaxPairGrid ? g : kMaxPairGrid;
+  }
+
+  // the task list of the matrix (see kpm_fused.cuh); lag = the grid size
+  static tb_status build_pair_plan(int64_t n, const int64_t *slice_ptr, const int32_t *col, PairWs &w,
+                                   cudaStream_t st) {
+    const int64_t nb = w.plan.nb;
+    TB_CUDA(cudaMemsetAsync(w.plan.done, 0, nb * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.plan.cta_s1, 0, kMaxPairGrid * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.lo, 0x7f, nb * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.hi, 0xff, nb * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.rlo, 0x7f, nb * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.rhi, 0xff, nb * sizeof(int), st));
+    TB_CUDA(cudaMemsetAsync(w.fill, 0, nb * sizeof(int), st));
+    pair_hull_kernel<RPB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, slice_ptr, col, w.lo, w.hi, w.rlo, w.rhi);
+    TB_CHECK_LAUNCH();
+    fill_ones_kernel<<<(unsigned)((nb + 1 + 255) / 256), 256, 0, st>>>(nb + 1, w.gsize);
+    TB_CHECK_LAUNCH();
+    pair_wait_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+        nb, pair_grid(), w.lo, w.hi, w.rlo, w.rhi, w.wait, w.key, reinterpret_cast<unsigned long long *>(w.gsize));
+    TB_CHECK_LAUNCH();
+    tb_status s = exclusive_scan_i64(w.gsize, w.gsize, nb + 1, w.gtotal, w.scan_ws, st);
+    if (s != TB_OK) return s;
+    pair_tasks_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(nb, w.gsize, w.key, w.fill, w.tasks);
+    TB_CHECK_LAUNCH();
+    return TB_OK;
+  }
+
+  static tb_status launch_pair(int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
+                               const valT *diag, real *P, real *Q, PairWs &w, int pair, real alpha, real shift,
+                               int *flags, cudaStream_t st) {
+    PairPlan plan = w.plan;
+    double *bpart = w.bpart;
+    void *args[] = {&n, &slice_ptr, &col, &val, &diag, &P, &Q, &plan, &pair, &bpart, &alpha, &shift, &flags};
+    TB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(cheb_pair_kernel<real, valT, R, CPT>),
+                                        dim3(pair_grid()), dim3(kBlock), args, 0, st));
+    note_launch();
+    return TB_OK;
   }
 
   // opt every pipelined instantiation into its shared-memory size (before any
@@ -603,7 +700,7 @@ struct KpmRunner {
   static tb_status enqueue(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                            const valT *diag, double a, double b, int M, uint64_t seed, bool dbl, double *mu_r,
                            real *v0, real *A, real *B, double *partial, int *flags, const BatchTables &bt,
-                           cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                           cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end, PairWs *pw = nullptr) {
     const int64_t units = SEG ? blocks(n) : grid;   // partials per moment slot
     const int64_t ps = units * R;
     TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
@@ -621,15 +718,34 @@ struct KpmRunner {
     if (s != TB_OK) return s;
     const real two_over_a = static_cast<real>(2.0 / a);
     const int last = dbl ? (M - 1) / 2 + 1 : M - 1;   // index of the last vector computed
-    for (int m = 2; m <= last; ++m) {
+    auto single = [&](int m) {
       // v_m is written over v_{m-2}: m even -> B, m odd -> A; v_2 reads prev = v0
       real *out = (m & 1) ? A : B;
       const real *x = (m & 1) ? B : A;
       const real *prev = (m == 2) ? v0 : out;
-      s = dbl ? step<false, true, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                       partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift, flags, ps, bt, st)
-              : step<false, false, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                        partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
+      return dbl ? step<false, true, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                          partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift, flags, ps, bt, st)
+                 : step<false, false, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                           partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
+    };
+    int m = 2;
+    if (!SEG && pw && last >= 4) {
+      // v_2 alone (its v_{m-2} is v0), then v_m and v_{m+1} per launch
+      s = single(2);
+      if (s != TB_OK) return s;
+      int pair = 0;
+      for (m = 3; m + 1 <= last; m += 2, ++pair) {
+        real *P = (m & 1) ? A : B;   // v_{m-2} -> v_m
+        real *Q = (m & 1) ? B : A;   // v_{m-1} -> v_{m+1}
+        s = launch_pair(n, slice_ptr, col, val, diag, P, Q, *pw, pair, two_over_a, shift, flags, st);
+        if (s != TB_OK) return s;
+        pair_reduce_kernel<<<(unsigned)((4 * units * R + 255) / 256), 256, 0, st>>>(
+            pw->bpart, pw->plan.nb, R, (int)units, partial + (size_t)(2 * (m - 1)) * ps, ps);
+        TB_CHECK_LAUNCH();
+      }
+    }
+    for (; m <= last; ++m) {
+      s = single(m);
       if (s != TB_OK) return s;
     }
     if (ev_end) TB_CUDA(cudaEventRecord(ev_end, st));
@@ -669,6 +785,8 @@ struct KpmRunner {
     real *B = cv.take<real>((size_t)np * R * 2);
     double *partial = cv.take<double>((size_t)(M + 1) * grid * R);
     int *flags = cv.take<int>(4);
+    PairWs pw;
+    carve_pair(cv, n, M, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments: workspace too small (%zu < %zu)", ws_bytes, cv.used);
     if (use_bulk() && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
       return fail(TB_ERR_INVALID_ARG, "kpm_moments: col and val must be 16-byte aligned");
@@ -678,8 +796,11 @@ struct KpmRunner {
       TB_CUDA(cudaEventCreate(&ev[0]));
       TB_CUDA(cudaEventCreate(&ev[1]));
     }
-    tb_status s = enqueue<false>(grid, n, slice_ptr, col, val, diag, a, b, M, seed, dbl, mu_r, v0, A, B, partial,
-                                 flags, BatchTables(), st, ev[0], ev[1]);
+    const bool paired = use_pair(dbl);
+    tb_status s = paired ? build_pair_plan(n, slice_ptr, col, pw, st) : TB_OK;
+    if (s == TB_OK)
+      s = enqueue<false>(grid, n, slice_ptr, col, val, diag, a, b, M, seed, dbl, mu_r, v0, A, B, partial, flags,
+                         BatchTables(), st, ev[0], ev[1], paired ? &pw : nullptr);
     if (s == TB_OK) s = check_flags(flags, st, "kpm_moments");
     if (step_ms) {
       float ms = 0.f;
@@ -833,7 +954,7 @@ struct RunOp {
 using namespace gputb;
 
 extern "C" tb_status tb_kpm_set_variant(int32_t variant) {
-  TB_REQUIRE(variant >= 0 && variant <= 2, "tb_kpm_set_variant: variant must be 0, 1 or 2");
+  TB_REQUIRE(variant >= 0 && variant <= 3, "tb_kpm_set_variant: variant must be 0, 1, 2 or 3");
   g_kpm_variant = variant;
   return TB_OK;
 }

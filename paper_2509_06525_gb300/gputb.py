@@ -220,7 +220,8 @@ def kpm_moments_batched(mats, a, b, M: int, R: int, seed: int, doubling: bool = 
 
 
 def kpm_set_variant(variant: int):
-    """0 = automatic, 1 = direct-load Chebyshev step, 2 = bulk-copy pipeline."""
+    """0 = automatic, 1 = direct-load Chebyshev step, 2 = bulk-copy pipeline,
+    3 = two steps per launch with the matrix read once (doubling mode)."""
     _check("tb_kpm_set_variant", lib().tb_kpm_set_variant(int(variant)))
 
 

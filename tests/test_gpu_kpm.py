@@ -38,8 +38,11 @@ def gputb():
     return g
 
 
-@pytest.fixture(params=[1, 2], ids=["direct", "pipelined"])
+@pytest.fixture(params=[1, 2, 3], ids=["direct", "pipelined", "paired"])
 def variant(request, gputb):
+    """Chebyshev-step kernels: one step per launch (direct loads or bulk-copy
+    pipeline), or two steps per launch (doubling mode only; the plain mode
+    falls back to single steps)."""
     gputb.kpm_set_variant(request.param)
     yield request.param
     gputb.kpm_set_variant(0)
