@@ -14,8 +14,10 @@ this path) on a bounded sample of the same workload.
 
 Launch: python bench.py [--gpus 1 --steps 3 --warmup 3]; for N > 1 under
 torch.distributed.run, one rank per GPU, each rank runs its own replica of
-the step with its own random-phase seed (the R vectors are independent, so
-they shard across ranks with no data-path collective).
+the step on its own block of R random vectors (vectors rank*R .. rank*R+R-1
+of one ensemble: the vectors are independent, so they shard across ranks
+with no data-path collective); after the timed region the moments of all
+ranks are gathered once into one ensemble.
 """
 from __future__ import annotations
 
@@ -149,7 +151,8 @@ class Pipeline:
         self.torch, self.g = torch, g
         self.s, self.w = s, w
         self.M, self.R = w["M"], w["R"]
-        self.seed = synth.KPM_SEED + 1000003 * rank
+        self.seed = synth.KPM_SEED
+        self.first_vector = rank * w["R"]
         self.teacher = teacher_for(s)
         self.hamiltonian = hamiltonian
         self.model = model
@@ -175,7 +178,8 @@ class Pipeline:
                                             with_diag=self.teacher_diag)
         bd = g.spectral_bounds(H, 64, synth.LANCZOS_SEED)
         timing = self.kpm_ms if record else None
-        mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing, doubling=self.doubling)
+        mu = g.kpm_moments(H, bd.a, bd.b, self.M, self.R, self.seed, timing=timing, doubling=self.doubling,
+                           first_vector=self.first_vector)
         E = energies if energies is not None else torch.linspace(bd.emin, bd.emax, self.w["K"],
                                                                  dtype=torch.float64, device="cuda")
         rho = g.kpm_dos(mu, bd.a, bd.b, E)
@@ -206,9 +210,8 @@ def timed(torch, dist, fn, steps, warmup):
         dist.barrier()
     ms = e0.elapsed_time(e1) / steps
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2509_06525_gb300.distributed import max_over_ranks
+        ms = max_over_ranks(ms, "cuda")
     return ms
 
 
@@ -321,6 +324,13 @@ def run_ours(args):
 
     if training is not None:
         out["training"] = training
+
+    if dist is not None:
+        # one ensemble from all ranks' vector blocks (outside the timed region)
+        from paper_2509_06525_gb300.distributed import gather_moments
+        mu_all = gather_moments(pipe.last["mu"], R * world)
+        out["ensemble"] = {"random_vectors": int(mu_all.shape[0]), "ranks": world,
+                           "mu0_mean": float(mu_all[:, 0].mean().item())}
 
     # plain FP64 teacher form on the same structure and GPU, and the DOS
     # error of the timed (learned FP32 by default) path against it

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 2
+#define GPUTB_ABI_VERSION 3
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -117,6 +117,10 @@ TB_API int64_t tb_launch_count(void);
  *   a, b         rescaling H~ = (H - b)/a; a > 0
  *   M            moments (>= 2);  R  vectors: 1, 2, 4, 8, 16 or 32
  *   seed         random-phase seed
+ *   first_vector index of this call's first random vector (0 .. 2^31):
+ *                vector r uses u(seed, first_vector + r, i), so calls (or
+ *                ranks) holding disjoint index ranges compute members of one
+ *                ensemble, identical to one call over the union
  *   mode         TB_KPM_DIRECT or TB_KPM_DOUBLING
  *   mu_r         device double [R*M] output (vector r, moment n at r*M+n)
  *   workspace    >= kpm_moments_workspace_size(n, M, R, precision) bytes
@@ -143,8 +147,8 @@ TB_API tb_status tb_kpm_set_variant(int32_t variant);
 TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col,
                       const void *val, const void *diag, int32_t precision,
                       double a, double b, int32_t M, int32_t R, uint64_t seed,
-                      int32_t mode, double *mu_r, void *workspace, size_t workspace_bytes,
-                      void *stream, double *step_ms);
+                      int64_t first_vector, int32_t mode, double *mu_r, void *workspace,
+                      size_t workspace_bytes, void *stream, double *step_ms);
 
 /* ---------------------------------------------------------------------
  * kpm_moments without any device allocation (no counterpart in the paper;

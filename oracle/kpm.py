@@ -49,10 +49,11 @@ def uniform(seed, r, i):
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
-def random_phase_vectors(seed, n, R):
-    """v0 [N, R] complex128 with unit-modulus entries."""
+def random_phase_vectors(seed, n, R, first=0):
+    """v0 [N, R] complex128 with unit-modulus entries: random vectors
+    first .. first + R - 1 of the ensemble."""
     i = np.arange(n, dtype=np.uint64)[:, None]
-    r = np.arange(R, dtype=np.uint64)[None, :]
+    r = np.arange(first, first + R, dtype=np.uint64)[None, :]
     phi = 2.0 * np.pi * uniform(seed, r, i)
     return np.cos(phi) + 1j * np.sin(phi)
 
@@ -102,9 +103,10 @@ def exact_trace_moments(Ht, M):
     return mu.sum(axis=0)
 
 
-def kpm_moments(H, a, b, M, R, seed):
-    """Full oracle step: rescale, draw v0, recurse.  Returns (mu [M], mu_r [R, M])."""
+def kpm_moments(H, a, b, M, R, seed, first=0):
+    """Full oracle step: rescale, draw v0 (vectors first .. first + R - 1),
+    recurse.  Returns (mu [M], mu_r [R, M])."""
     Ht = rescale(H, a, b)
-    v0 = random_phase_vectors(seed, H.shape[0], R)
+    v0 = random_phase_vectors(seed, H.shape[0], R, first)
     mu_r, _ = chebyshev_moments(Ht, v0, M)
     return mu_r.mean(axis=0), mu_r

@@ -46,11 +46,11 @@ struct BatchTables {
 constexpr int kBatchTile = 256;
 constexpr int kMaxPairGrid = 4096;   // CTAs of a cooperative pair launch (at most)
 
-// v0[i, r] = exp(2 pi i u(seed, r, i)) (batched: u(seed + s, r, i - row0[s])
+// v0[i, r] = exp(2 pi i u(seed, r0 + r, i)) (batched: u(seed + s, r, i - row0[s])
 // on the real rows of snapshot s, 0 on padding rows); partials of
 // Re <v0|v0> per CTA, or per RPB-row block when SEG.
 template <typename real, int R, int CPT, bool SEG>
-__global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_t seed, BatchTables bt,
+__global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_t seed, int64_t r0, BatchTables bt,
                                                               real *__restrict__ v0, double *__restrict__ partial) {
   constexpr int TPR = R / CPT;
   constexpr int RPB = kBlock / TPR;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
         const int r = part * CPT + c;
         double sn = 0.0, co = 0.0;
         if (real_row) {
-          const double phi = 2.0 * M_PI * phase_uniform(sd, (uint64_t)r, (uint64_t)li);
+          const double phi = 2.0 * M_PI * phase_uniform(sd, (uint64_t)(r0 + r), (uint64_t)li);
           sincos(phi, &sn, &co);
         }
         v[2 * c] = static_cast<real>(co);
@@ -698,13 +698,13 @@ struct KpmRunner {
   // The whole recursion: random phases, the Chebyshev steps, the reduction.
   template <bool SEG>
   static tb_status enqueue(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
-                           const valT *diag, double a, double b, int M, uint64_t seed, bool dbl, double *mu_r,
-                           real *v0, real *A, real *B, double *partial, int *flags, const BatchTables &bt,
+                           const valT *diag, double a, double b, int M, uint64_t seed, int64_t r0, bool dbl,
+                           double *mu_r, real *v0, real *A, real *B, double *partial, int *flags, const BatchTables &bt,
                            cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end, PairWs *pw = nullptr) {
     const int64_t units = SEG ? blocks(n) : grid;   // partials per moment slot
     const int64_t ps = units * R;
     TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
-    random_phase_kernel<real, R, CPT, SEG><<<grid, kBlock, 0, st>>>(n, seed, bt, v0, partial);
+    random_phase_kernel<real, R, CPT, SEG><<<grid, kBlock, 0, st>>>(n, seed, r0, bt, v0, partial);
     TB_CHECK_LAUNCH();
     if (ev_begin) TB_CUDA(cudaEventRecord(ev_begin, st));
     // v1 = H~ v0 -> A.  Direct mode: the step making v_m adds the partials of
@@ -774,7 +774,7 @@ struct KpmRunner {
   }
 
   static tb_status run(int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val, const valT *diag,
-                       double a, double b, int M, uint64_t seed, int mode, double *mu_r, void *ws,
+                       double a, double b, int M, uint64_t seed, int64_t r0, int mode, double *mu_r, void *ws,
                        size_t ws_bytes, cudaStream_t st, double *step_ms) {
     const int grid = grid_for(n);
     const int64_t np = padded_rows(n);
@@ -799,7 +799,7 @@ struct KpmRunner {
     const bool paired = use_pair(dbl);
     tb_status s = paired ? build_pair_plan(n, slice_ptr, col, pw, st) : TB_OK;
     if (s == TB_OK)
-      s = enqueue<false>(grid, n, slice_ptr, col, val, diag, a, b, M, seed, dbl, mu_r, v0, A, B, partial, flags,
+      s = enqueue<false>(grid, n, slice_ptr, col, val, diag, a, b, M, seed, r0, dbl, mu_r, v0, A, B, partial, flags,
                          BatchTables(), st, ev[0], ev[1], paired ? &pw : nullptr);
     if (s == TB_OK) s = check_flags(flags, st, "kpm_moments");
     if (step_ms) {
@@ -835,7 +835,7 @@ struct KpmRunner {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     tb_status s = TB_OK;
     if (e == cudaSuccess) {
-      s = enqueue<true>(grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, dbl, mu, v0, A, B, partial, flags,
+      s = enqueue<true>(grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, 0, dbl, mu, v0, A, B, partial, flags,
                         bt, cs, nullptr, nullptr);
       e = cudaStreamEndCapture(cs, &graph);
     }
@@ -940,10 +940,10 @@ struct WsOp {
 template <typename real, typename valT, int R>
 struct RunOp {
   static tb_status apply(int64_t n, const int64_t *sp, const int32_t *col, const void *val, const void *diag,
-                         double a, double b, int M, uint64_t seed, int mode, double *mu, void *ws, size_t wsb,
-                         cudaStream_t st, double *step_ms) {
+                         double a, double b, int M, uint64_t seed, int64_t r0, int mode, double *mu, void *ws,
+                         size_t wsb, cudaStream_t st, double *step_ms) {
     return KpmRunner<real, valT, R>::run(n, sp, col, static_cast<const valT *>(val),
-                                         static_cast<const valT *>(diag), a, b, M, seed, mode, mu, ws, wsb, st,
+                                         static_cast<const valT *>(diag), a, b, M, seed, r0, mode, mu, ws, wsb, st,
                                          step_ms);
   }
 };
@@ -970,8 +970,9 @@ extern "C" size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, in
 
 extern "C" tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col, const void *val,
                                  const void *diag, int32_t precision, double a, double b, int32_t M, int32_t R,
-                                 uint64_t seed, int32_t mode, double *mu_r, void *workspace,
+                                 uint64_t seed, int64_t first_vector, int32_t mode, double *mu_r, void *workspace,
                                  size_t workspace_bytes, void *stream, double *step_ms) {
+  TB_REQUIRE(first_vector >= 0 && first_vector <= (int64_t(1) << 31), "kpm_moments: first_vector out of range");
   TB_REQUIRE(mode == TB_KPM_DIRECT || mode == TB_KPM_DOUBLING, "kpm_moments: bad mode %d", mode);
   TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "kpm_moments: n=%lld out of range", (long long)n);
   TB_REQUIRE(M >= 2, "kpm_moments: M=%d must be >= 2", M);
@@ -983,11 +984,11 @@ extern "C" tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int3
   tb_status status = TB_OK;
   bool ok = precision == TB_F32
                 ? KpmDispatch<float, float>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                         seed, (int)mode, mu_r, workspace, workspace_bytes, st,
-                                                         step_ms)
+                                                         seed, first_vector, (int)mode, mu_r, workspace,
+                                                         workspace_bytes, st, step_ms)
                 : KpmDispatch<double, double>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                           seed, (int)mode, mu_r, workspace, workspace_bytes, st,
-                                                           step_ms);
+                                                           seed, first_vector, (int)mode, mu_r, workspace,
+                                                           workspace_bytes, st, step_ms);
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments: unsupported R=%d for precision %d", R, precision);
   return status;
 }
@@ -1063,10 +1064,10 @@ extern "C" tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, co
   // scratch word is written before it is read
   bool ok = precision == TB_F32
                 ? KpmDispatch<float, float>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                         seed, (int)TB_KPM_DIRECT, mu_r, scratch,
+                                                         seed, (int64_t)0, (int)TB_KPM_DIRECT, mu_r, scratch,
                                                          kNoAllocScratchBytes, st, nullptr)
                 : KpmDispatch<double, double>::call<RunOp>(R, status, n, slice_ptr, col, val, diag, a, b, (int)M,
-                                                           seed, (int)TB_KPM_DIRECT, mu_r, scratch,
+                                                           seed, (int64_t)0, (int)TB_KPM_DIRECT, mu_r, scratch,
                                                            kNoAllocScratchBytes, st, nullptr);
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_noalloc: unsupported R=%d", R);
   return status;

@@ -41,7 +41,7 @@ SIGNATURES = {
     "tb_launch_count": (_c_i64, []),
     "tb_kpm_set_variant": (_c_i32, [_c_i32]),
     "kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32,
-                             _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
+                             _c_u64, _c_i64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_moments_noalloc": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32,
                                      _c_i32, _c_u64, _c_vp, _c_vp]),
     "kpm_moments_batched_workspace_size": (_c_sz, [_c_i32, _c_vp, _c_vp, _c_i32, _c_i32, _c_i32, _c_vp]),
@@ -86,7 +86,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 2   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 3   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -159,8 +159,9 @@ KPM_DIRECT, KPM_DOUBLING = 0, 1
 
 def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
                 stream=None, workspace: Optional[torch.Tensor] = None, timing: Optional[list] = None,
-                doubling: bool = False) -> torch.Tensor:
-    """Per-vector KPM moments mu_r [R, M] (float64, device).
+                doubling: bool = False, first_vector: int = 0) -> torch.Tensor:
+    """Per-vector KPM moments mu_r [R, M] (float64, device) of random vectors
+    first_vector .. first_vector + R - 1.
 
     If `timing` is a list, the CUDA-event time (ms) of the Chebyshev-step
     launches is appended to it."""
@@ -173,7 +174,7 @@ def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
     mu = torch.empty((R, M), dtype=torch.float64, device=H.col.device)
     step_ms = ctypes.c_double(0.0)
     st = L.kpm_moments(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), prec,
-                       float(a), float(b), int(M), int(R), int(seed) & ((1 << 64) - 1),
+                       float(a), float(b), int(M), int(R), int(seed) & ((1 << 64) - 1), int(first_vector),
                        KPM_DOUBLING if doubling else KPM_DIRECT, _ptr(mu), _ptr(ws), ws.numel(), _stream(stream),
                        ctypes.byref(step_ms) if timing is not None else None)
     _check("kpm_moments", st)

@@ -1,0 +1,95 @@
+"""Multi-rank path on CPU: two gloo ranks split the random vectors of the
+KPM trace estimate (Sec. 2.4) with vector_shard, each computes its block
+with the FP64 oracle (vectors first .. first + count - 1), and
+gather_moments must give the moments of the whole ensemble as one oracle
+call over all vectors; max_over_ranks gives the slowest rank's time."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from oracle import kpm as okpm
+from paper_2509_06525_gb300.distributed import gather_moments, max_over_ranks, vector_shard
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _ring_hamiltonian(n=40, seed=3):
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(-1.2, -0.8, n)
+    rows = np.arange(n)
+    H = sp.csr_matrix((t, (rows, (rows + 1) % n)), shape=(n, n))
+    H = (H + H.T).tocsr()
+    H.setdiag(rng.uniform(-0.3, 0.3, n))
+    return H.tocsr()
+
+
+@pytest.mark.parametrize("r_total,world", [(8, 2), (3, 2), (5, 3), (4, 4), (7, 1)])
+def test_vector_shard_partitions_the_ensemble(r_total, world):
+    seen = []
+    for k in range(world):
+        first, count = vector_shard(r_total, k, world)
+        assert count >= 1
+        seen.extend(range(first, first + count))
+    assert seen == list(range(r_total))
+    counts = [vector_shard(r_total, k, world)[1] for k in range(world)]
+    assert max(counts) - min(counts) <= 1
+
+
+def test_vector_shard_rejects_bad_arguments():
+    with pytest.raises(ValueError):
+        vector_shard(2, 0, 3)
+    with pytest.raises(ValueError):
+        vector_shard(4, 2, 2)
+
+
+def test_oracle_vector_offset_selects_ensemble_members():
+    """Vectors first .. first + R - 1 are the same columns of the full draw."""
+    H = _ring_hamiltonian()
+    full = okpm.random_phase_vectors(11, H.shape[0], 6)
+    part = okpm.random_phase_vectors(11, H.shape[0], 2, first=3)
+    assert np.array_equal(part, full[:, 3:5])
+    _, mu_full = okpm.kpm_moments(H, 3.0, 0.0, 24, 6, 11)
+    _, mu_part = okpm.kpm_moments(H, 3.0, 0.0, 24, 2, 11, first=3)
+    np.testing.assert_allclose(mu_part, mu_full[3:5], rtol=0, atol=1e-15)
+
+
+def _worker(rank, world, port, r_total, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        H = _ring_hamiltonian()
+        first, count = vector_shard(r_total, rank, world)
+        _, mu_local = okpm.kpm_moments(H, 3.0, 0.1, 32, count, 2024, first=first)
+        mu_all = gather_moments(torch.tensor(mu_local), r_total)
+        t_max = max_over_ranks(1.5 + rank, "cpu")
+        if rank == 0:
+            np.save(out_path, mu_all.numpy())
+            with open(out_path + ".t", "w") as f:
+                f.write(repr(t_max))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("r_total", [4, 3])
+def test_two_gloo_ranks_reproduce_the_single_rank_ensemble(tmp_path, r_total):
+    world = 2
+    out = str(tmp_path / "mu.npy")
+    mp.start_processes(_worker, args=(world, _free_port(), r_total, out), nprocs=world, join=True,
+                       start_method="spawn")
+    mu_all = np.load(out)
+    _, mu_ref = okpm.kpm_moments(_ring_hamiltonian(), 3.0, 0.1, 32, r_total, 2024)
+    assert mu_all.shape == mu_ref.shape
+    np.testing.assert_allclose(mu_all, mu_ref, rtol=0, atol=1e-14)
+    with open(out + ".t") as f:
+        assert float(f.read()) == 2.5

@@ -185,3 +185,18 @@ def test_wide_rows_fall_back_inside_the_pipeline(gputb, variant):
     mu = gputb.kpm_moments(Hd, a, b, 64, 8, 77).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, 64, 8, 77)
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+def test_first_vector_blocks_compose_the_ensemble(gputb, cfg800, dtype, tol):
+    """Two calls over vectors 0-3 and 4-7 give the moments of one call over
+    0-7 (up to the grouping of the partial sums), and the second block
+    matches the oracle's vectors 4-7: how ranks split one ensemble."""
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, dtype)
+    full = gputb.kpm_moments(Hd, a, b, 128, 8, 5, doubling=True).cpu().numpy()
+    lo = gputb.kpm_moments(Hd, a, b, 128, 4, 5, doubling=True, first_vector=0).cpu().numpy()
+    hi = gputb.kpm_moments(Hd, a, b, 128, 4, 5, doubling=True, first_vector=4).cpu().numpy()
+    np.testing.assert_allclose(np.concatenate([lo, hi]), full, rtol=0, atol=tol)
+    _, ref = okpm.kpm_moments(H, a, b, 128, 4, 5, first=4)
+    assert np.max(np.abs(hi - ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
