@@ -107,6 +107,22 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
 // a plain loop.
 constexpr int kFastW = 16;
 
+// Resident CTAs per SM that the register budget is sized for (minimum
+// blocks of __launch_bounds__), chosen by timing on GB300: the kernels are
+// latency bound, so more resident warps pay where the tighter budget costs
+// no spills.  FP32 with one vector (1e8-atom workload): 4 CTAs (64
+// registers), 15% faster than 3; FP32 pipeline with two complex numbers per
+// thread and R >= 8: 4 CTAs, 5% faster than the compiler's own choice.
+// FP64 vectors keep 2 CTAs (no spills).
+template <typename real, int R, int CPT>
+constexpr int direct_min_blocks() {
+  return sizeof(real) == 8 ? 2 : (R == 1 ? 4 : (CPT >= 4 ? 2 : 3));
+}
+template <typename real, int R, int CPT>
+constexpr int bulk_min_blocks() {
+  return (sizeof(real) == 4 && CPT == 2 && R >= 8) ? 4 : 1;
+}
+
 // Write the CTA's partial sums as entry `idx` of the moment slot (and of the
 // next slot for the doubling pair), then restart the accumulators.  Every
 // thread of the CTA must call it.
@@ -150,7 +166,7 @@ __device__ __forceinline__ void segment_boundary(DotAcc<real> (&acc)[CPT], DotAc
 }
 
 template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 3) cheb_step_kernel(
+__global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) cheb_step_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x,
     const real *prev, const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha,
@@ -297,7 +313,7 @@ struct BulkGeom {
 };
 
 template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock) cheb_step_bulk_kernel(
+__global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_step_bulk_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
