@@ -24,6 +24,8 @@ Modules and the passages they follow (arXiv 2509.06525):
 * kpm          -- random-phase vectors and the Chebyshev moment recursion of
                   the LSQT/KPM method (Sec. 2.4).
 * dos          -- Jackson-damped KPM density of states, Eq. 4.
+* lsqt         -- velocity operator, time evolution and the velocity
+                  autocorrelation conductivity of Eq. 3 (sigma), Sec. 2.4.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, dense diagonalisation, invariants, brute force, independent

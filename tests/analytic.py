@@ -99,3 +99,67 @@ def rect_cell_bloch_levels(nx, ny, shell_hoppings, a_cc=1.42, onsite=0.0, chunk=
             Hk[:, b, bp] += t * np.exp(1j * (k @ d))
         out.append(np.linalg.eigvalsh(Hk).reshape(-1))
     return np.concatenate(out)
+
+
+HBAR_EV_FS = 0.6582119569   # CODATA 2018
+
+
+def _rect_cell_terms(shell_hoppings, a_cc=1.42):
+    h = 0.5 * np.sqrt(3.0) * a_cc
+    lx, ly = 3.0 * a_cc, np.sqrt(3.0) * a_cc
+    basis = np.array([[0.0, 0.0], [a_cc, 0.0], [1.5 * a_cc, h], [2.5 * a_cc, h]])
+    terms = []
+    for b in range(4):
+        for bp in range(4):
+            for tx in (-1, 0, 1):
+                for ty in (-1, 0, 1):
+                    d = basis[bp] + np.array([tx * lx, ty * ly]) - basis[b]
+                    r = float(np.hypot(*d))
+                    for dist, t in shell_hoppings.items():
+                        if abs(r - dist) < 1e-6:
+                            terms.append((b, bp, d, t))
+    return terms, lx, ly
+
+
+def rect_cell_bloch_vac_moments(nx, ny, shell_hoppings, a, b, M, times, direction=(1.0, 0.0), a_cc=1.42):
+    """Exact per-orbital VAC moments of pristine graphene on an nx x ny torus
+    of rectangular cells, by Bloch's theorem:
+        mu_n(t) = (1/N) Re Tr[T_n(H~) V U(t)^+ V U(t)],  U(t) = exp(-i H t / hbar),
+    with H(k)_{bb'} = sum t e^{i k.d} and the velocity V(k) = (1/hbar) dH(k)/dk
+    along `direction` (d = r_b' + T - r_b, the atomic positions in the phase).
+    In the eigenbasis of H(k): sum_{a,b} T_n(e~_a) |V_ab|^2 cos((e_b - e_a) t / hbar)."""
+    terms, lx, ly = _rect_cell_terms(shell_hoppings, a_cc)
+    e = np.asarray(direction, np.float64)
+    m1, m2 = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    k = np.stack([(2 * np.pi * m1 / (nx * lx)).reshape(-1), (2 * np.pi * m2 / (ny * ly)).reshape(-1)], axis=1)
+    Hk = np.zeros((k.shape[0], 4, 4), np.complex128)
+    Vk = np.zeros((k.shape[0], 4, 4), np.complex128)
+    for bb, bp, d, t in terms:
+        ph = np.exp(1j * (k @ d))
+        Hk[:, bb, bp] += t * ph
+        Vk[:, bb, bp] += (1j / HBAR_EV_FS) * float(d @ e) * t * ph
+    w, W = np.linalg.eigh(Hk)
+    Ve = np.conj(np.transpose(W, (0, 2, 1))) @ Vk @ W           # V in the eigenbasis
+    P = np.abs(Ve) ** 2                                           # |V_ab|^2
+    x = np.clip((w - b) / a, -1.0, 1.0)                           # [nk, 4]
+    Tn = np.cos(np.arange(M)[:, None, None] * np.arccos(x)[None])  # [M, nk, 4]
+    N = 4 * nx * ny
+    out = np.zeros((len(times), M))
+    for j, t in enumerate(times):
+        c = np.cos((w[:, None, :] - w[:, :, None]) * t / HBAR_EV_FS)   # [nk, a, b]: cos((e_b - e_a) t)
+        A = np.sum(P * c, axis=2)                                        # [nk, a]
+        out[j] = np.einsum("mka,ka->m", Tn, A) / N
+    return out
+
+
+def ring_vac_moments(n, t, eps0, a, b, M):
+    """Exact per-orbital VAC moments of a ring of n sites (spacing 1 A,
+    hopping t, onsite eps0): V = (i t / hbar)(S - S^+) commutes with H, so
+    mu_n(t) = (1/n) sum_k T_n(e~_k) v_k^2 for all t, with
+    e_k = eps0 + 2 t cos k, v_k = -2 t sin k / hbar, k = 2 pi m / n."""
+    kk = 2 * np.pi * np.arange(n) / n
+    ek = eps0 + 2 * t * np.cos(kk)
+    vk = -2 * t * np.sin(kk) / HBAR_EV_FS
+    x = np.clip((ek - b) / a, -1.0, 1.0)
+    Tn = np.cos(np.arange(M)[:, None] * np.arccos(x)[None, :])
+    return (Tn * vk[None, :] ** 2).sum(axis=1) / n
