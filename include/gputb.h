@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 3
+#define GPUTB_ABI_VERSION 4
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -224,6 +224,60 @@ TB_API tb_status kpm_dos(const double *mu_r, int32_t R, int32_t M, int32_t kerne
                   double lambda, double a, double b, const double *energy,
                   int32_t K, double *dos, void *stream);
 
+
+/* ---------------------------------------------------------------------
+ * Velocity-autocorrelation conductivity, Eq. 3 (sigma) of Sec. 2.4:
+ *   sigma(E, t) = (2 e^2 / Omega) int_0^t Tr[delta(E - H) Re(V V(tau))] dtau,
+ *   V(tau) = exp(i H tau/hbar) V exp(-i H tau/hbar),  V = (i/hbar)[H, X].
+ *
+ * tb_velocity_values: the real SELL values of V / (i/hbar) along the unit
+ * direction e: vval_ij = H_ij (d_ij . e), d_ij the minimum-image bond vector
+ * (same pattern as H; padding and phantom rows 0).
+ *   positions   device double [N][3];  box/pbc/rcut as tb_build_neighbors
+ *   val         device float/double SELL values of H;  vval  same layout, output
+ *   direction   host double [3]
+ *
+ * lsqt_vac: per-vector VAC moments
+ *   mu_out[j][r][n] = Re <V phi_L(t_j)| T_n(H~) |phi_R(t_j)> / N,  t_j = j dt,
+ * with phi_L(0) = V phi_r, phi_R(0) = phi_r, phi_r the random-phase vector
+ * first_vector + r of kpm_moments, both propagated by U(dt) = exp(-i H dt/hbar)
+ * (Chebyshev-Bessel series of exp(-i (a dt/hbar) H~) times exp(-i b dt/hbar),
+ * cut where |J_k| < 1e-17).  hbar = 0.6582119569 eV fs; H in eV, positions
+ * in Angstrom, dt in fs, so the moments are in Angstrom^2/fs^2.
+ *   n, slice_ptr, col, val, diag, precision, a, b, M, R, seed: as kpm_moments
+ *                (R: 1, 2, 4, 8 or 16; a dt / hbar <= 200)
+ *   vval         device, from tb_velocity_values
+ *   n_steps      time steps (n_steps + 1 time points, t_0 = 0)
+ *   mu_out       device double [(n_steps + 1) * R * M]
+ *   ms_out       host double or NULL: CUDA-event time of the whole loop (ms)
+ * Synchronises `stream`; TB_ERR_NOT_FINITE for non-finite moments,
+ * TB_ERR_TIMEOUT if a bounded pipeline wait gives up.
+ *
+ * lsqt_correlation: per-orbital C(E_k, t_j) = (1/N) Re Tr[delta(E - H) V V(t_j)]
+ * (the damped Chebyshev series of kpm_dos applied to the vector-averaged
+ * moments) and S(E_k, t_j) = int_0^{t_j} C dtau by the trapezoid rule
+ * (S(E, 0) = 0); sigma(E, t) = (2 e^2 N / Omega) S(E, t).
+ *   mu           device double [n_times][R][M] (lsqt_vac output)
+ *   energy       device double [K];  corr, sigma  device double [n_times][K]
+ *                (sigma may be NULL);  coef_ws device double [n_times * M]
+ * ------------------------------------------------------------------- */
+TB_API tb_status tb_velocity_values(const double *positions, int64_t n, const double *box,
+                                    const int32_t *pbc, double rcut, const int64_t *slice_ptr,
+                                    const int32_t *col, const void *val, int32_t precision,
+                                    const double *direction, void *vval, void *stream);
+
+TB_API size_t lsqt_vac_workspace_size(int64_t n, int32_t M, int32_t R, int32_t precision);
+
+TB_API tb_status lsqt_vac(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                          const void *val, const void *diag, const void *vval, int32_t precision,
+                          double a, double b, int32_t M, int32_t R, uint64_t seed,
+                          int64_t first_vector, int32_t n_steps, double dt_fs, double *mu_out,
+                          void *workspace, size_t workspace_bytes, void *stream, double *ms_out);
+
+TB_API tb_status lsqt_correlation(const double *mu, int32_t n_times, int32_t R, int32_t M,
+                                  int32_t kernel, double lambda, double a, double b,
+                                  const double *energy, int32_t K, double dt_fs, double *corr,
+                                  double *sigma, double *coef_ws, void *stream);
 
 /* ---------------------------------------------------------------------
  * Neighbour lists N(i) of Eq. 1 (Sec. 3): every j != i with a periodic

@@ -26,24 +26,16 @@
 #include <cstring>
 #include <vector>
 
-#include "kpm_common.cuh"
+#include "kpm_step.cuh"
 #include "kpm_fused.cuh"
 
 namespace gputb {
+namespace kpmdev {
+int g_kpm_variant = 0;
+}  // namespace kpmdev
 namespace {
 using namespace kpmdev;
 
-// Batch description (device tables) for kpm_moments_batched: rows of
-// snapshot s occupy [row0[s], row0[s] + padded) of the concatenated blocks,
-// the first rows[s] of them real; tile_snap maps each 256-row tile to its
-// snapshot.
-struct BatchTables {
-  const int32_t *tile_snap = nullptr;
-  const int64_t *row0 = nullptr;
-  const int64_t *rows = nullptr;
-  int n_snap = 0;
-};
-constexpr int kBatchTile = 256;
 constexpr int kMaxPairGrid = 4096;   // CTAs of a cooperative pair launch (at most)
 
 // v0[i, r] = exp(2 pi i u(seed, r0 + r, i)) (batched: u(seed + s, r, i - row0[s])
@@ -95,405 +87,6 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
   if (!SEG) cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
 }
 
-// One Chebyshev step over all rows:
-//   out = alpha * (sum_s val x[col] + (diag_i - shift) x_i) - (FIRST ? 0 : prev)
-// and the CTA partials of Re(conj(v0) out).  `prev` may alias `out`.
-//
-// The kernel is bound by HBM latency as much as by bandwidth: each row's
-// gathers depend on its column loads, which depend on the slice offset.  So
-// a row with at most kFastW slots issues all of its column and value loads
-// first (predicated, fully unrolled), then all of its neighbour gathers,
-// with the row's own v_{n-1} and v0 loads hoisted above them; wider rows take
-// a plain loop.
-constexpr int kFastW = 16;
-
-// Resident CTAs per SM that the register budget is sized for (minimum
-// blocks of __launch_bounds__), chosen by timing on GB300: the kernels are
-// latency bound, so more resident warps pay where the tighter budget costs
-// no spills.  FP32 with one vector (1e8-atom workload): 4 CTAs (64
-// registers), 15% faster than 3; FP32 pipeline with two complex numbers per
-// thread and R >= 8: 4 CTAs, 5% faster than the compiler's own choice.
-// FP64 vectors keep 2 CTAs (no spills).
-template <typename real, int R, int CPT>
-constexpr int direct_min_blocks() {
-  return sizeof(real) == 8 ? 2 : (R == 1 ? 4 : (CPT >= 4 ? 2 : 3));
-}
-template <typename real, int R, int CPT>
-constexpr int bulk_min_blocks() {
-  return (sizeof(real) == 4 && CPT == 2 && R >= 8) ? 4 : 1;
-}
-
-// Write the CTA's partial sums as entry `idx` of the moment slot (and of the
-// next slot for the doubling pair), then restart the accumulators.  Every
-// thread of the CTA must call it.
-template <typename real, int R, int CPT, bool DBL>
-__device__ __forceinline__ void flush_partials(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
-                                               double *partial, int64_t idx, int64_t slot_stride) {
-  double sum[CPT];
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) sum[c] = acc[c].value();
-  cta_partial<R, CPT>(sum, partial + idx * R);
-  __syncthreads();
-  if (DBL) {
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) sum[c] = acc2[c].value();
-    cta_partial<R, CPT>(sum, partial + slot_stride + idx * R);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
-}
-
-// Segmented mode: block `blk` of the current run of RPB-row blocks has just
-// been processed.  Every block of the run except its first gets zeros; when
-// the next block of this CTA starts another snapshot (or there is none) the
-// run's sums go into the entry of the run's first block.  Uniform across the
-// CTA.
-template <typename real, int R, int CPT, bool DBL>
-__device__ __forceinline__ void segment_boundary(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
-                                                 double *partial, int64_t slot_stride, const BatchTables &bt,
-                                                 int64_t blk, int rpb, int64_t blk_end, int64_t &run_head) {
-  const int64_t nxt = blk + 1;
-  const bool ends = nxt >= blk_end || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
-  if (blk != run_head && threadIdx.x < R) {  // every block but the run's first holds zero
-    partial[blk * R + threadIdx.x] = 0.0;
-    if (DBL) partial[slot_stride + blk * R + threadIdx.x] = 0.0;
-  }
-  if (ends) {
-    flush_partials<real, R, CPT, DBL>(acc, acc2, partial, run_head, slot_stride);
-    run_head = nxt;
-  }
-}
-
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) cheb_step_kernel(
-    int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
-    const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x,
-    const real *prev, const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha,
-    real shift, int64_t slot_stride, BatchTables bt) {
-  constexpr int TPR = R / CPT;
-  constexpr int RPB = kBlock / TPR;
-  const int part = threadIdx.x % TPR;
-  DotAcc<real> acc[CPT], acc2[CPT];
-  // SEG (batched): each CTA takes a contiguous run of blocks and reduces
-  // only where the snapshot changes; other blocks' entries are zero
-  const int64_t nblk = (n + RPB - 1) / RPB;
-  const int64_t b_first = SEG ? nblk * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t b_last = SEG ? nblk * (blockIdx.x + 1) / gridDim.x : nblk;
-  const int64_t b_step = SEG ? 1 : gridDim.x;
-  int64_t run_head = b_first;
-  for (int64_t blk = b_first; blk < b_last; blk += b_step) {
-    const int64_t row0 = blk * RPB;
-    const int64_t i = row0 + threadIdx.x / TPR;
-    if (i < n) {
-      const int64_t off = (i * R + part * CPT) * 2;
-      real p[2 * CPT], z[2 * CPT];
-      if (!FIRST) ld_stream<real, CPT>(prev + off, p);
-      if (!DBL) ld_stream<real, CPT>(v0 + off, z);
-      const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
-      const int64_t sb = __ldg(slice_ptr + (i >> 5));
-      const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
-      const int64_t e0 = sb + (i & 31);
-      real y[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
-      if (w <= kFastW) {
-        int32_t j[kFastW];
-        real h[kFastW];
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            j[s] = __ldcs(col + e0 + 32 * s);
-            h[s] = static_cast<real>(__ldcs(val + e0 + 32 * s));
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            real xv[2 * CPT];
-            ld_gather<real, CPT>(x + ((int64_t)j[s] * R + part * CPT) * 2, xv);
-#pragma unroll
-            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h[s], xv[c], y[c]);
-          }
-        }
-      } else {
-        int64_t e = e0;
-        for (int s = 0; s < w; ++s, e += 32) {
-          const int32_t jj = __ldcs(col + e);
-          const real hh = static_cast<real>(__ldcs(val + e));
-          real xv[2 * CPT];
-          ld_gather<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
-#pragma unroll
-          for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
-        }
-      }
-      real xi[2 * CPT];
-      ld_gather<real, CPT>(x + off, xi);
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
-      real o[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
-      st_stream<real, CPT>(out + off, o);
-      if (DBL) {
-        // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
-          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
-        }
-      } else {
-        // Re(conj(v0) * o) = z.re o.re + z.im o.im
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
-      }
-    }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head);
-  }
-  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
-}
-
-// ---------------------------------------------------------------------------
-// Pipelined variant: the streamed operands of a tile of TR rows -- the tile's
-// SELL slices of col and val (contiguous), and its rows of v_{n-1} and v0 --
-// are moved by one elected thread with cp.async.bulk into a kStages-deep
-// shared-memory ring whose stages complete on mbarriers (transaction
-// counts).  All warps compute on one stage while the next ones are in
-// flight, and the neighbour gathers take their indices from shared memory,
-// so a row's gathers are issued without waiting for its column loads.  A
-// tile whose slices are wider than kFastW falls back to direct loads of col
-// and val.  Every wait is bounded: on timeout the CTA drains its own copies
-// (bounded again), raises flags[0] |= 4 and returns.
-// ---------------------------------------------------------------------------
-constexpr int kStages = 3;
-constexpr long long kWaitPolls = 1ll << 21;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (long long k = 0; k < kWaitPolls; ++k)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-template <typename real, typename valT, int R, int CPT>
-struct BulkGeom {
-  static constexpr int TPR = R / CPT;
-  static constexpr int TR = kBlock / TPR;                       // rows per tile
-  static constexpr int kEl = TR * kFastW;                       // SELL elements per stage
-  static constexpr size_t kColBytes = kEl * sizeof(int32_t);
-  static constexpr size_t kValBytes = kEl * sizeof(valT);
-  static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
-  static constexpr size_t kStageBytes = kColBytes + kValBytes + 2 * kVecBytes;
-  static constexpr size_t kSmem = 128 + kStages * kStageBytes;  // mbarriers first
-  static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024;
-};
-
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_step_bulk_kernel(
-    int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
-    const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
-    const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
-    int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
-  using G = BulkGeom<real, valT, R, CPT>;
-  constexpr int TPR = G::TPR, TR = G::TR;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-  unsigned char *ring = smem + 128;
-  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes); };
-  auto s_val = [&](int st) { return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kColBytes); };
-  auto s_prev = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes);
-  };
-  auto s_v0 = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes + G::kVecBytes);
-  };
-  const int64_t ntiles = (n + TR - 1) / TR;
-  const int part = threadIdx.x % TPR;
-  const int lr = threadIdx.x / TPR;
-  // tiles of this CTA: grid-stride, or one contiguous run in SEG mode
-  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
-  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
-
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(full + st, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  // producer: stream the operands of local tile number kk into its stage
-  auto issue = [&](int64_t kk) {
-    const int64_t tile = tile_of(kk);
-    const int st = static_cast<int>(kk % kStages);
-    const int64_t r0 = tile * TR;
-    const int64_t k0 = r0 >> 5;
-    const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
-    const int64_t e0 = slice_ptr[k0], e1 = slice_ptr[k1];
-    const bool bulk = (e1 - e0) <= G::kEl;
-    const uint32_t ebytes = bulk ? static_cast<uint32_t>(e1 - e0) : 0u;
-    uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
-    if (bulk) tx += ebytes * static_cast<uint32_t>(sizeof(int32_t) + sizeof(valT));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(full + st, tx);
-    if (bulk && ebytes > 0) {
-      bulk_g2s(s_col(st), col + e0, ebytes * sizeof(int32_t), full + st);
-      bulk_g2s(s_val(st), val + e0, ebytes * sizeof(valT), full + st);
-    }
-    const size_t voff = (size_t)r0 * R * 2;
-    if (!FIRST) bulk_g2s(s_prev(st), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
-    if (!DBL) bulk_g2s(s_v0(st), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
-  };
-
-  const int64_t my_tiles =
-      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
-  int64_t run_head = t_begin;
-  int64_t issued = 0;
-  if (threadIdx.x == 0)
-    for (; issued < my_tiles && issued < kStages; ++issued) issue(issued);
-
-  DotAcc<real> acc[CPT], acc2[CPT];
-  bool ok = true;
-  int64_t kk = 0;
-  for (; kk < my_tiles; ++kk) {
-    const int st = static_cast<int>(kk % kStages);
-    const uint32_t parity = static_cast<uint32_t>((kk / kStages) & 1);
-    ok = __syncthreads_and(mbar_wait_bounded(full + st, parity)) != 0;
-    if (!ok) break;
-    const int64_t tile = tile_of(kk);
-    const int64_t r0 = tile * TR;
-    const int64_t i = r0 + lr;
-    if (i < n) {
-      const int64_t k0 = r0 >> 5;
-      const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
-      const int64_t e0 = __ldg(slice_ptr + k0);
-      const bool bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
-      const int loff = (lr * R + part * CPT) * 2;
-      real p[2 * CPT], z[2 * CPT];
-      if (!FIRST) memcpy(p, s_prev(st) + loff, sizeof(p));
-      if (!DBL) memcpy(z, s_v0(st) + loff, sizeof(z));
-      const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
-      const int64_t sb = __ldg(slice_ptr + (i >> 5));
-      const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
-      real y[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
-      if (bulk) {
-        const int32_t *cs = s_col(st) + (sb - e0) + (i & 31);
-        const valT *vs = s_val(st) + (sb - e0) + (i & 31);
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            real xv[2 * CPT];
-            const real h = static_cast<real>(vs[32 * s]);
-            ld_gather<real, CPT>(x + ((int64_t)cs[32 * s] * R + part * CPT) * 2, xv);
-#pragma unroll
-            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
-          }
-        }
-      } else {
-        int64_t e = sb + (i & 31);
-        for (int s = 0; s < w; ++s, e += 32) {
-          const int32_t jj = __ldcs(col + e);
-          const real hh = static_cast<real>(__ldcs(val + e));
-          real xv[2 * CPT];
-          ld_gather<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
-#pragma unroll
-          for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
-        }
-      }
-      const int64_t off = (i * R + part * CPT) * 2;
-      real xi[2 * CPT];
-      ld_gather<real, CPT>(x + off, xi);
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
-      real o[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
-      st_stream<real, CPT>(out + off, o);
-      if (DBL) {
-        // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
-          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
-        }
-      } else {
-        // Re(conj(v0) * o) = z.re o.re + z.im o.im
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
-      }
-    }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
-    __syncthreads();  // every thread is done with this stage
-    if (threadIdx.x == 0 && issued < my_tiles) issue(issued++);
-  }
-  if (!ok) {
-    // drain this CTA's own copies still in flight, bounded, then report
-    if (threadIdx.x == 0) {
-      atomicOr(flags, 4);
-      for (int64_t q = kk; q < issued; ++q)
-        mbar_wait_bounded(full + q % kStages, static_cast<uint32_t>((q / kStages) & 1));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
-  }
-  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
-}
-
-// mu_r[r, m] = (sum over CTAs in index order of partial[m, cta, r]) / n;
-// flags[0] |= 1 if |mu| > 1 + 1e-6, |= 2 if not finite.
-__device__ __forceinline__ double slot_sum(const double *__restrict__ partial, int grid, int R, int m, int r) {
-  const double *p = partial + (int64_t)m * grid * R + r;
-  double s = 0.0;
-  for (int c = 0; c < grid; ++c) s += p[(int64_t)c * R];
-  return s;
-}
-
-// direct mode: mu_m = S_m / n with S_m = sum_i Re conj(v0) v_m;
-// doubling mode: S_0, S_1 as above, S_2k = sum |v_k|^2, S_2k+1 = sum Re conj(v_k) v_k+1,
-// and mu_m = 2 S_m / n - mu_(m mod 2) for m >= 2 (Weisse et al. 2006)
-__global__ void moment_reduce_kernel(const double *__restrict__ partial, int grid, int R, int M, double inv_n,
-                                     int doubling, double *__restrict__ mu_r, int *__restrict__ flags) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)M * R) return;
-  const int m = static_cast<int>(t / R), r = static_cast<int>(t % R);
-  double mu = slot_sum(partial, grid, R, m, r) * inv_n;
-  if (doubling && m >= 2) mu = 2.0 * mu - slot_sum(partial, grid, R, m & 1, r) * inv_n;
-  mu_r[(int64_t)r * M + m] = mu;
-  if (!isfinite(mu)) atomicOr(flags, 2);
-  else if (fabs(mu) > 1.0 + 1e-6) atomicOr(flags, 1);
-}
-
-// kernel variant for the Chebyshev step: 0 = choose automatically,
-// 1 = direct loads, 2 = bulk-copy pipeline, 3 = two steps per launch
-// (doubling mode; set with tb_kpm_set_variant)
-int g_kpm_variant = 0;
-
 // batched: mu[s][r][m] from the RPB-row block partials of snapshot s (block order)
 __global__ void batched_reduce_kernel(BatchTables bt, int M, int R, int rpb, int64_t nblk,
                                       const double *__restrict__ partial, int doubling, double *__restrict__ mu,
@@ -521,52 +114,16 @@ __global__ void batched_reduce_kernel(BatchTables bt, int M, int R, int rpb, int
 }
 
 template <typename real, typename valT, int R>
-struct KpmRunner {
-  // complex numbers per thread, chosen by measurement on GB300 (10M-atom
-  // graphene): FP32 R = 4 -> 4 (two 16-byte accesses), other R >= 2 -> 2
-  // (one 16-byte access), R = 1 -> 1; FP64 2 when R >= 2, else 1
-  static constexpr int CPT = sizeof(real) == 4 ? (R == 4 ? 4 : (R >= 2 ? 2 : 1)) : (R >= 2 ? 2 : 1);
-  static constexpr int TPR = R / CPT;
-  static constexpr int RPB = kBlock / TPR;
-  using G = BulkGeom<real, valT, R, CPT>;
-  static constexpr int64_t kRowPad = 256;   // vector blocks hold whole tiles
-
-  // the pipeline wins where several threads share a row (R >= 8 in FP32 on
-  // GB300, measured); with one thread per row the direct kernel is faster
-  static bool use_bulk() {
-    if (!G::kOk || g_kpm_variant == 1) return false;
-    return g_kpm_variant == 2 || TPR >= 4;
-  }
-
-  static int grid_for(int64_t n) {
-    static int per_sm_direct = 0, per_sm_bulk = 0;
-    if (use_bulk()) {
-      if (per_sm_bulk == 0) {
-        int b = 0;
-        cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                                                          kBlock, G::kSmem) != cudaSuccess ||
-            b <= 0)
-          b = 1;
-        per_sm_bulk = b;
-      }
-      const int64_t need = (n + G::TR - 1) / G::TR;
-      const int64_t cap = (int64_t)per_sm_bulk * sm_count();
-      return static_cast<int>(need < cap ? need : cap);
-    }
-    if (per_sm_direct == 0) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_kernel<real, valT, R, CPT, false, false, false>, kBlock, 0) !=
-              cudaSuccess ||
-          b <= 0)
-        b = 4;
-      per_sm_direct = b;
-    }
-    const int64_t need = (n + RPB - 1) / RPB;
-    const int64_t cap = (int64_t)per_sm_direct * sm_count();
-    return static_cast<int>(need < cap ? need : cap);
-  }
+struct KpmRunner : StepKit<real, valT, R> {
+  using Kit = StepKit<real, valT, R>;
+  using Kit::CPT;
+  using Kit::TPR;
+  using Kit::RPB;
+  using typename Kit::G;
+  using Kit::use_bulk;
+  using Kit::grid_for;
+  using Kit::prepare;
+  static constexpr int64_t kRowPad = Kit::kRowPad;
 
   static int64_t padded_rows(int64_t n) { return (n + kRowPad - 1) / kRowPad * kRowPad; }
   static int64_t blocks(int64_t n) { return (n + RPB - 1) / RPB; }   // RPB == G::TR
@@ -673,44 +230,6 @@ struct KpmRunner {
     return TB_OK;
   }
 
-  // opt every pipelined instantiation into its shared-memory size (before any
-  // stream capture)
-  static void prepare() {
-    if (!use_bulk()) return;
-    const int sm = (int)G::kSmem;
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  }
-
-  template <bool FIRST, bool DBL, bool SEG>
-  static tb_status step(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
-                        const valT *diag, const real *x, const real *prev, const real *v0, real *out,
-                        double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
-                        const BatchTables &bt, cudaStream_t st) {
-    if (use_bulk())
-      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, G::kSmem, st>>>(
-          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt);
-    else
-      cheb_step_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
-          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
-    TB_CHECK_LAUNCH();
-    return TB_OK;
-  }
-
   // The whole recursion: random phases, the Chebyshev steps, the reduction.
   template <bool SEG>
   static tb_status enqueue(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
@@ -727,10 +246,11 @@ struct KpmRunner {
     // mu_m; doubling mode: the step reading v_k adds those of S_2k and S_2k+1.
     const real shift = static_cast<real>(b);
     const real inv_a = static_cast<real>(1.0 / a);
-    tb_status s = dbl ? step<true, true, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial, inv_a,
-                                              shift, flags, ps, bt, st)
-                      : step<true, false, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial + ps,
-                                               inv_a, shift, flags, ps, bt, st);
+    tb_status s =
+        dbl ? Kit::template step<true, true, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A, partial,
+                                                  inv_a, shift, flags, ps, bt, st)
+            : Kit::template step<true, false, SEG>(grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A,
+                                                   partial + ps, inv_a, shift, flags, ps, bt, st);
     if (s != TB_OK) return s;
     const real two_over_a = static_cast<real>(2.0 / a);
     const int last = dbl ? (M - 1) / 2 + 1 : M - 1;   // index of the last vector computed
@@ -739,10 +259,12 @@ struct KpmRunner {
       real *out = (m & 1) ? A : B;
       const real *x = (m & 1) ? B : A;
       const real *prev = (m == 2) ? v0 : out;
-      return dbl ? step<false, true, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                          partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift, flags, ps, bt, st)
-                 : step<false, false, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                           partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
+      return dbl ? Kit::template step<false, true, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                                        partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift,
+                                                        flags, ps, bt, st)
+                 : Kit::template step<false, false, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                                         partial + (size_t)m * ps, two_over_a, shift, flags, ps,
+                                                         bt, st);
     };
     int m = 2;
     if (!SEG && pw && last >= 4) {
@@ -772,7 +294,7 @@ struct KpmRunner {
     } else {
       const int total = M * R;
       moment_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, dbl ? 1 : 0,
-                                                                mu_r, flags);
+                                                                1.0 + 1e-6, mu_r, flags);
     }
     TB_CHECK_LAUNCH();
     return TB_OK;

@@ -48,6 +48,13 @@ SIGNATURES = {
     "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
+    "tb_velocity_values": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
+                                    _c_vp, _c_vp]),
+    "lsqt_vac_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
+    "lsqt_vac": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32, _c_u64,
+                          _c_i64, _c_i32, _c_dbl, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
+    "lsqt_correlation": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32,
+                                  _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp]),
     "tb_neighbors_workspace_size": (_c_sz, [_c_i64, _c_vp, _c_vp, _c_dbl, _c_i32]),
     "tb_build_neighbors": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_vp, _c_vp, _c_i64,
                                     _c_vp, _c_vp, ctypes.POINTER(_c_i64), _c_vp, _c_sz, _c_vp]),
@@ -86,7 +93,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 3   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 4   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -236,6 +243,63 @@ def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel
                    energy.numel(), _ptr(out), _stream(stream))
     _check("kpm_dos", st)
     return out
+
+
+# ------------------------------------------------------------------ conductivity (Eq. 3 (sigma))
+
+HBAR_EV_FS = 0.6582119569
+
+
+def velocity_values(positions: torch.Tensor, box, pbc, rcut: float, H: SellMatrix, direction=(1.0, 0.0, 0.0),
+                    stream=None) -> torch.Tensor:
+    """tb_velocity_values: SELL values H_ij (d_ij . e) of V / (i / hbar)."""
+    import numpy as np
+    L = lib()
+    b, p, bptr, pptr = _host_box(box, pbc)
+    e = np.ascontiguousarray(np.asarray(direction, np.float64).reshape(3))
+    vval = torch.empty_like(H.val)
+    st = L.tb_velocity_values(_ptr(positions), H.n, bptr, pptr, float(rcut), _ptr(H.slice_ptr), _ptr(H.col),
+                              _ptr(H.val), H.precision, e.ctypes.data_as(ctypes.c_void_p), _ptr(vval),
+                              _stream(stream))
+    _check("tb_velocity_values", st)
+    return vval
+
+
+def lsqt_vac(H: SellMatrix, vval: torch.Tensor, a: float, b: float, M: int, R: int, seed: int, n_steps: int,
+             dt: float, first_vector: int = 0, stream=None, timing: Optional[list] = None) -> torch.Tensor:
+    """Per-vector VAC moments [n_steps + 1, R, M] (float64, device, A^2/fs^2)."""
+    L = lib()
+    need = L.lsqt_vac_workspace_size(H.n, M, R, H.precision)
+    if need == 0:
+        raise GputbError("lsqt_vac_workspace_size", TB_ERR_INVALID_ARG, f"unsupported n={H.n} M={M} R={R}")
+    ws = _workspace(need, H.col.device)
+    mu = torch.empty((n_steps + 1, R, M), dtype=torch.float64, device=H.col.device)
+    ms = ctypes.c_double(0.0)
+    st = L.lsqt_vac(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), _ptr(vval), H.precision,
+                    float(a), float(b), int(M), int(R), int(seed) & ((1 << 64) - 1), int(first_vector), int(n_steps),
+                    float(dt), _ptr(mu), _ptr(ws), ws.numel(), _stream(stream),
+                    ctypes.byref(ms) if timing is not None else None)
+    _check("lsqt_vac", st)
+    if timing is not None:
+        timing.append(ms.value)
+    return mu
+
+
+def lsqt_correlation(mu: torch.Tensor, a: float, b: float, energy: torch.Tensor, dt: float,
+                     kernel: str = "jackson", lam: float = 4.0, stream=None):
+    """(C [n_times, K], S [n_times, K]): per-orbital velocity correlation and
+    its running time integral on `energy` from lsqt_vac moments."""
+    L = lib()
+    mu = mu.contiguous()
+    n_t, R, M = mu.shape
+    K = energy.numel()
+    corr = torch.empty((n_t, K), dtype=torch.float64, device=mu.device)
+    sig = torch.empty((n_t, K), dtype=torch.float64, device=mu.device)
+    coef = torch.empty((n_t * M,), dtype=torch.float64, device=mu.device)
+    st = L.lsqt_correlation(_ptr(mu), n_t, R, M, KERNELS[kernel], float(lam), float(a), float(b),
+                            _ptr(energy), K, float(dt), _ptr(corr), _ptr(sig), _ptr(coef), _stream(stream))
+    _check("lsqt_correlation", st)
+    return corr, sig
 
 
 def _host_box(box, pbc):
