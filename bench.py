@@ -44,6 +44,15 @@ METRIC = "KPM atom*moments/s on 1 GB300 (learned FP32 vs plain FP64), % HBM roof
 UNIT = "atom*moments/s"
 L2_BYTES = 126 * 1024 * 1024
 
+# DRAM bytes (read + write) of one launch of the timed step's Chebyshev kernel,
+# from full-size ncu captures of these exact configurations with the current
+# kernels (profiles/traffic_cheb_step_bench_workloads.md); any other
+# configuration, or a changed kernel, reports null.
+MEASURED_TRAFFIC = {
+    ("graphene-10M-learned", "mlp", "doubling", 1024, 8): 2_898_499_584,
+    ("graphene-100M", "teacher", "doubling", 1024, 1): 11_994_291_456,
+}
+
 
 def parse_args():
     p = argparse.ArgumentParser()
@@ -62,6 +71,8 @@ def parse_args():
                    help="epochs of the untimed model training (default: the training default); fewer for profiling")
     p.add_argument("--M", type=int, default=None, help="override the workload's moment count (profiling)")
     p.add_argument("--R", type=int, default=None, help="override the workload's vector count (profiling)")
+    p.add_argument("--lsqt-steps", type=int, default=2,
+                   help="VAC conductivity time steps of 0.1 fs measured after the main line (0: skip)")
     return p.parse_args()
 
 
@@ -215,6 +226,47 @@ def timed(torch, dist, fn, steps, warmup):
     return ms
 
 
+def lsqt_measurement(pipe, n_steps, torch, g, dt=0.1):
+    """VAC conductivity (Eq. 3 (sigma)) on the last step's Hamiltonian: x
+    velocity, the workload's M and R, n_steps time steps of 0.1 fs; CUDA-event
+    time of the whole loop (after one warm-up call with no time step)."""
+    H, bd, s = pipe.last["H"], pipe.last["bd"], pipe.s
+    vval = g.velocity_values(pipe.pos, s.box, s.pbc, pipe.teacher.rcut, H, (1.0, 0.0, 0.0))
+    g.lsqt_vac(H, vval, bd.a, bd.b, pipe.M, pipe.R, pipe.seed, 0, dt, first_vector=pipe.first_vector)
+    ms = []
+    mu = g.lsqt_vac(H, vval, bd.a, bd.b, pipe.M, pipe.R, pipe.seed, n_steps, dt, first_vector=pipe.first_vector,
+                    timing=ms)
+    E = torch.tensor([bd.b - 0.3 * bd.a, bd.b, bd.b + 0.3 * bd.a], dtype=torch.float64, device="cuda")
+    C, S = g.lsqt_correlation(mu, bd.a, bd.b, E, dt)
+    t = ms[0] * 1e-3
+    pts = n_steps + 1
+    # launches of the matrix: M - 1 moment steps per time point, and per time
+    # step two propagations of K Chebyshev-Bessel terms (the library's cut:
+    # |J_k(a dt / hbar)| < 1e-17 beyond k = a dt / hbar + 2)
+    from scipy.special import jv
+    x = bd.a * dt / g.HBAR_EV_FS
+    K = 0
+    while not (K > x + 2 and abs(jv(K, x)) < 1e-17):
+        K += 1
+    spmv = pts * (pipe.M - 1) + 2 * n_steps * K
+    nnz = int(pipe.last["nb"].cnt.sum().item())
+    sv, sc = (4, 8) if H.val.dtype == torch.float32 else (8, 16)
+    step_bytes = nnz * (sv + 4) + (s.n * sv if H.diag is not None else 0) + 4 * s.n * pipe.R * sc
+    per_spmv_ms = ms[0] / spmv
+    peak, peak_src = hbm_peak()
+    return {"time_points": pts, "dt_fs": dt, "moments": pipe.M, "random_vectors": pipe.R, "direction": "x",
+            "ms": ms[0], "ms_per_time_point": ms[0] / pts,
+            "atom_moments_timepoints_per_s": s.n * pipe.M * pts / t,
+            "matrix_launches": spmv, "bessel_terms": K,
+            "roofline": {"bound": "hbm", "kernel": "Chebyshev step (direct mode, dot with V phi_L)",
+                         "bytes_per_launch": step_bytes, "ms_per_launch": per_spmv_ms,
+                         "achieved": step_bytes / (per_spmv_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": step_bytes / (per_spmv_ms * 1e-3) / 1e9 / peak, "peak_source": peak_src,
+                         "note": "whole-loop time over all matrix launches (moment steps, propagation terms)"},
+            "C_at_E": [float(v) for v in C[0].cpu()], "S_end_at_E": [float(v) for v in S[-1].cpu()],
+            "units": "C: A^2/fs^2/eV per orbital, S: A^2/fs/eV per orbital (sigma = 2 e^2 N / Omega * S)"}
+
+
 def cpu_baseline(workload, budget_s=15.0):
     """The FP64 oracle's KPM on a bounded sample of the same workload."""
     from oracle import hamiltonian as oha, kpm as okpm, neighbors as onb, teacher as ote
@@ -315,7 +367,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (ELL and vector blocks >> 126 MB)",
                    "step": "neighbours + H build + FP64 bounds + KPM + Jackson DOS"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "cheb_step (fused Chebyshev step + moment dots)",
+                     "frac": achieved / peak,
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, args.hamiltonian, args.kpm, M, R)),
+                     "kernel": "cheb_step (fused Chebyshev step + moment dots)",
                      "bytes_per_launch": step_bytes, "launch_ms": launch_ms, "peak_source": peak_src,
                      "kpm_share_of_step": kpm_frac_of_step},
         "gpu_launches": launches,
@@ -331,6 +385,11 @@ def run_ours(args):
         mu_all = gather_moments(pipe.last["mu"], R * world)
         out["ensemble"] = {"random_vectors": int(mu_all.shape[0]), "ranks": world,
                            "mu0_mean": float(mu_all[:, 0].mean().item())}
+
+    # the conductivity on the timed step's own (FP32) Hamiltonian, before the
+    # FP64 comparison below replaces it
+    if args.lsqt_steps > 0:
+        out["lsqt"] = lsqt_measurement(pipe, args.lsqt_steps, torch, g)
 
     # plain FP64 teacher form on the same structure and GPU, and the DOS
     # error of the timed (learned FP32 by default) path against it
