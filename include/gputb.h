@@ -225,6 +225,16 @@ TB_API tb_status kpm_dos(const double *mu_r, int32_t R, int32_t M, int32_t kerne
                   int32_t K, double *dos, void *stream);
 
 
+/* Test hook (no counterpart in the paper): runs the bounded wait of the
+ * two-step kernel (which = 0: stage-1 flags) or of the pipelined step
+ * (which = 1: an mbarrier phase) on flags / a phase that nothing completes,
+ * with a limit of `polls` polls.  Returns TB_ERR_TIMEOUT when the wait gave
+ * up (the expected outcome; the context stays usable), TB_OK if it completed.
+ *   workspace   device, >= 512 bytes (zeroed by the call)
+ * Synchronises `stream`. */
+TB_API tb_status tb_debug_wait_timeout(int32_t which, int64_t polls, void *workspace,
+                                       size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * Velocity-autocorrelation conductivity, Eq. 3 (sigma) of Sec. 2.4:
  *   sigma(E, t) = (2 e^2 / Omega) int_0^t Tr[delta(E - H) Re(V V(tau))] dtau,

@@ -751,3 +751,51 @@ extern "C" tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows, 
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: unsupported R=%d", R);
   return status;
 }
+
+// ---------------------------------------------------------------------------
+// Test hook for failure handling: the same bounded waits that the pipelined
+// step (mbarrier phase) and the two-step kernel (stage-1 flags) use, run on
+// a barrier phase or flags that nothing completes, must give up after
+// `polls` polls and report, leaving the context usable.
+// ---------------------------------------------------------------------------
+namespace gputb {
+namespace {
+
+__global__ void wait_probe_kernel(int which, long long polls, PairPlan plan, int *__restrict__ status) {
+  __shared__ unsigned long long s_tot;
+  __shared__ __align__(8) uint64_t bar;
+  bool ok;
+  if (which == 0) {
+    ok = pair_wait(plan, make_int2(0, 63), 1, 0, polls, &s_tot);   // flags stay 0, epoch 1
+  } else {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);                       // one arrival expected, none made
+    __syncthreads();
+    ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, polls)) != 0;
+  }
+  if (threadIdx.x == 0) *status = ok ? 1 : 0;
+}
+
+}  // namespace
+}  // namespace gputb
+
+extern "C" tb_status tb_debug_wait_timeout(int32_t which, int64_t polls, void *workspace, size_t workspace_bytes,
+                                           void *stream) {
+  TB_REQUIRE(which == 0 || which == 1, "tb_debug_wait_timeout: which must be 0 (flags) or 1 (mbarrier)");
+  TB_REQUIRE(polls >= 1 && polls <= (int64_t(1) << 24), "tb_debug_wait_timeout: polls out of range");
+  TB_REQUIRE(workspace && workspace_bytes >= 512, "tb_debug_wait_timeout: need 512 bytes of workspace");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int *done = static_cast<int *>(workspace);   // 64 flags, then the status word
+  TB_CUDA(cudaMemsetAsync(done, 0, 512, st));
+  PairPlan plan;
+  plan.done = done;
+  plan.cta_s1 = done;
+  plan.nb = 64;
+  wait_probe_kernel<<<1, kBlock, 0, st>>>(which, (long long)polls, plan, done + 64);
+  TB_CHECK_LAUNCH();
+  int h = -1;
+  TB_CUDA(cudaMemcpyAsync(&h, done + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  if (h == 0) return fail(TB_ERR_TIMEOUT, "tb_debug_wait_timeout: the %s wait gave up after %lld polls",
+                          which == 0 ? "flag" : "mbarrier", (long long)polls);
+  return TB_OK;
+}

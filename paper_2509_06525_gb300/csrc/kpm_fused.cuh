@@ -173,6 +173,33 @@ __device__ __noinline__ void pair_stage(int64_t blk, int64_t n, const int64_t *_
   __syncthreads();
 }
 
+// Bounded wait of a whole CTA for stage 1 on the blocks of the interval w
+// (done flags equal to `epoch`; a wide interval instead waits for the
+// per-CTA stage-1 counts to reach s1_target).  Polls with relaxed loads and
+// a short sleep; true when the condition held, false after `polls` polls.
+// Uniform across the CTA; s_tot is a shared scratch word.
+__device__ __forceinline__ bool pair_wait(const PairPlan &plan, int2 w, int epoch, int64_t s1_target, long long polls,
+                                          unsigned long long *s_tot) {
+  const bool wide = w.y - w.x > kBigSpan;
+  for (long long it = 0; it < polls; ++it) {
+    bool mine = true;
+    if (wide) {
+      if (threadIdx.x == 0) *s_tot = 0;
+      __syncthreads();
+      unsigned long long tot = 0;
+      for (int c = threadIdx.x; c < (int)gridDim.x; c += kBlock) tot += (unsigned)ld_relaxed(plan.cta_s1 + c);
+      atomicAdd(s_tot, tot);
+      __syncthreads();
+      mine = *s_tot >= (unsigned long long)s1_target;
+    } else {
+      for (int b = w.x + (int)threadIdx.x; b <= w.y; b += kBlock) mine &= ld_relaxed(plan.done + b) == epoch;
+    }
+    if (__syncthreads_and(mine)) return true;
+    __nanosleep(200);
+  }
+  return false;
+}
+
 template <typename real, typename valT, int R, int CPT>
 __global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 4)
     cheb_pair_kernel(int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
@@ -197,28 +224,7 @@ __global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 4
       }
     } else {
       const int64_t blk = ~task;
-      const int2 w = plan.wait[blk];
-      const bool wide = w.y - w.x > kBigSpan;
-      bool ok = false;
-      for (long long it = 0; it < kPairPolls; ++it) {
-        bool mine = true;
-        if (wide) {
-          if (threadIdx.x == 0) s_tot = 0;
-          __syncthreads();
-          unsigned long long tot = 0;
-          for (int c = threadIdx.x; c < G; c += kBlock) tot += (unsigned)ld_relaxed(plan.cta_s1 + c);
-          atomicAdd(&s_tot, tot);
-          __syncthreads();
-          mine = s_tot >= (unsigned long long)s1_target;
-        } else {
-          for (int b = w.x + (int)threadIdx.x; b <= w.y; b += kBlock) mine &= ld_relaxed(plan.done + b) == epoch;
-        }
-        if (__syncthreads_and(mine)) {
-          ok = true;
-          break;
-        }
-        __nanosleep(200);
-      }
+      const bool ok = pair_wait(plan, plan.wait[blk], epoch, s1_target, kPairPolls, &s_tot);
       // acquire: the flags were observed with relaxed loads; the fence orders
       // this thread's later loads after them, the barrier the CTA's
       __threadfence();

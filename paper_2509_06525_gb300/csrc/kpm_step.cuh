@@ -228,8 +228,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (long long k = 0; k < kWaitPolls; ++k)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long polls = kWaitPolls) {
+  for (long long k = 0; k < polls; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

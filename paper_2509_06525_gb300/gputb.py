@@ -48,6 +48,7 @@ SIGNATURES = {
     "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
+    "tb_debug_wait_timeout": (_c_i32, [_c_i32, _c_i64, _c_vp, _c_sz, _c_vp]),
     "tb_velocity_values": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
                                     _c_vp, _c_vp]),
     "lsqt_vac_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
@@ -243,6 +244,14 @@ def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel
                    energy.numel(), _ptr(out), _stream(stream))
     _check("kpm_dos", st)
     return out
+
+
+def debug_wait_timeout(which: int, polls: int, stream=None):
+    """Test hook: a bounded wait on flags (0) or an mbarrier phase (1) that
+    nothing completes; raises GputbError(TB_ERR_TIMEOUT) when it gives up."""
+    ws = torch.zeros(512, dtype=torch.uint8, device="cuda")
+    _check("tb_debug_wait_timeout", lib().tb_debug_wait_timeout(int(which), int(polls), _ptr(ws), 512,
+                                                                 _stream(stream)))
 
 
 # ------------------------------------------------------------------ conductivity (Eq. 3 (sigma))

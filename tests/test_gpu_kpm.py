@@ -200,3 +200,19 @@ def test_first_vector_blocks_compose_the_ensemble(gputb, cfg800, dtype, tol):
     np.testing.assert_allclose(np.concatenate([lo, hi]), full, rtol=0, atol=tol)
     _, ref = okpm.kpm_moments(H, a, b, 128, 4, 5, first=4)
     assert np.max(np.abs(hi - ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
+
+
+@pytest.mark.parametrize("which", [0, 1], ids=["flag_wait", "mbarrier_wait"])
+def test_bounded_waits_give_up_and_leave_the_context_usable(gputb, cfg800, which):
+    """The waits of the two-step kernel (stage-1 flags) and of the pipelined
+    step (mbarrier phase) run on a flag / phase that nothing completes: they
+    must give up after their poll limit with TB_ERR_TIMEOUT, and the next
+    call must work."""
+    with pytest.raises(gputb.GputbError) as ei:
+        gputb.debug_wait_timeout(which, 2000)
+    assert ei.value.status == gputb.TB_ERR_TIMEOUT
+    s, indptr, idx, t, eps, H, a, b, w = cfg800
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
+    mu = gputb.kpm_moments(Hd, a, b, 64, 2, 3).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, 64, 2, 3)
+    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
