@@ -452,6 +452,12 @@ TB_API tb_status tb_adamw_step(float *params, const float *grad, float *m, float
 /* BF16 weight copy from the FP32 parameters. */
 TB_API tb_status tb_mlp_pack_weights(const float *params, void *w_bf16, void *stream);
 
+/* Tuning hook for the forward pass of tb_build_hamiltonian: 0 = 5th-
+ * generation tensor cores (tcgen05, accumulators in TMEM; default),
+ * 1 = mma.sync tiles.  Both compute the same MLP in BF16 with FP32
+ * accumulation (sums in a different order).  Process-wide. */
+TB_API tb_status tb_mlp_set_variant(int32_t variant);
+
 /* Workspace bytes of tb_build_hamiltonian. */
 TB_API size_t tb_build_hamiltonian_workspace_size(int64_t total_elements);
 

@@ -59,4 +59,37 @@ __device__ __forceinline__ double3 bond_vector(const Box &B, const double *__res
   return min_image(B, d);
 }
 
+// |r_j - r_i| (minimum image) in FP32 for the learned-H features: the
+// coordinate differences in FP64 (exact for nearby atoms), the image shift
+// decided from their FP32 values and applied in FP64 only when it is not
+// zero (a periodic seam), then FP32 for the length.  The shift agrees with
+// min_image for every pair closer than half a periodic width.
+__device__ __forceinline__ float bond_length_f32(const Box &B, const double *__restrict__ pos, int64_t i,
+                                                 int64_t j) {
+  double dx = __ldg(pos + 3 * j) - __ldg(pos + 3 * i);
+  double dy = __ldg(pos + 3 * j + 1) - __ldg(pos + 3 * i + 1);
+  double dz = __ldg(pos + 3 * j + 2) - __ldg(pos + 3 * i + 2);
+  if (B.p3) {
+    const float n3 = rintf((float)dz * (float)B.icz);
+    if (n3 != 0.0f) {
+      dx -= (double)n3 * B.cx;
+      dy -= (double)n3 * B.cy;
+      dz -= (double)n3 * B.cz;
+    }
+  }
+  if (B.p2) {
+    const float n2 = rintf((float)dy * (float)B.iby);
+    if (n2 != 0.0f) {
+      dx -= (double)n2 * B.bx;
+      dy -= (double)n2 * B.by;
+    }
+  }
+  if (B.p1) {
+    const float n1 = rintf((float)dx * (float)B.iax);
+    if (n1 != 0.0f) dx -= (double)n1 * B.ax;
+  }
+  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+  return sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
+}
+
 }  // namespace gputb

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include "geometry.cuh"
+#include "tcgen05.cuh"
 
 namespace gputb {
 namespace {
@@ -49,6 +50,10 @@ using bf16 = __nv_bfloat16;
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+__device__ __forceinline__ uint32_t smem_u32_generic(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   uint32_t u;
@@ -64,7 +69,16 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// logistic function as 1/2 + tanh(z/2)/2 with the single-instruction
+// hardware tanh (relative error about 2^-11, far below the BF16 rounding of
+// the activations it feeds); forward, backward and the learned-H kernels
+// all use it, so training and inference see the same network
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
 __device__ __forceinline__ float silu(float z) { return z * sigm(z); }
 __device__ __forceinline__ float dsilu(float z) {
   const float s = sigm(z);
@@ -209,7 +223,7 @@ __global__ void descriptor_kernel(const double *__restrict__ pos, const int32_t 
   for (int s = 0; s < m; ++s) {
     const int32_t j = col[e0 + 32 * s];
     const int zj = min(max(species[j], 0), 2);
-    const float r = static_cast<float>(sqrt(sq_norm(bond_vector(B, pos, i, j))));
+    const float r = bond_length_f32(B, pos, i, j);
     float C[8];
     bond_descriptor(r, rcut, sc + (zi * 3 + zj) * 64, C);
 #pragma unroll
@@ -225,7 +239,7 @@ __device__ __forceinline__ void edge_features(const double *__restrict__ pos, co
                                               const Box &B, float rcut, const float *sc,
                                               const float *__restrict__ v, int64_t i, int32_t j, float (&x)[32]) {
   const int zi = min(max(species[i], 0), 2), zj = min(max(species[j], 0), 2);
-  const float r = static_cast<float>(sqrt(sq_norm(bond_vector(B, pos, i, j))));
+  const float r = bond_length_f32(B, pos, i, j);
   float C[8];
   bond_descriptor(r, rcut, sc + (zi * 3 + zj) * 64, C);
   const float4 *vi4 = reinterpret_cast<const float4 *>(v + i * 8);
@@ -788,6 +802,188 @@ __global__ void __launch_bounds__(kThreads) mlp_hamiltonian_kernel(
   }
 }
 
+// The same forward pass on the 5th-generation tensor cores (tcgen05).  A CTA
+// of 4 warps owns a tile of 128 edges = the 128 TMEM lanes; thread t builds
+// edge t's features and owns row t of every accumulator.  Per tile:
+//   X (128 x 32, BF16, shared) . W1^T -> D1 (TMEM cols 0..63)      2 MMAs (K = 16)
+//   silu(D1 + b1) -> H (shared, the A operand of the next layer)
+//   H . W2^T -> D2 (cols 64..127)                                   4 MMAs
+//   silu(D2 + b2) -> H;  H . W3^T -> D3 (cols 0..15, W3 padded)     4 MMAs
+//   y = D3[:, 0:2] + b3
+// One thread issues each layer's MMAs and commits them to an mbarrier that
+// every thread waits on (bounded: on timeout the CTA raises flags[0] |= 2,
+// waits once more for its MMAs, frees its TMEM and stops).  Operands use the
+// K-major core-matrix layout without swizzle; the weights stay in shared
+// memory for the whole kernel.  128 TMEM columns per CTA; the dynamic
+// shared-memory request keeps at most 4 CTAs (512 columns) on an SM.
+struct TcSmem {
+  bf16 w1[64 * 32];
+  bf16 w2[64 * 64];
+  bf16 w3[16 * 64];
+  bf16 xa[TILE * 32];
+  bf16 ha[TILE * 64];
+  float b1[64], b2[64], b3[2];
+  float sc[9 * 64];
+  float smean[32], sinv[32];
+  uint64_t bar;
+  uint32_t tmem;
+};
+// kernel of the learned-H forward: 0 = tcgen05 (default), 1 = mma.sync
+int g_mlp_variant = 0;
+
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 128 > 47 * 1024 ? sizeof(TcSmem) + 128 : 47 * 1024;
+constexpr long long kTcPolls = 1ll << 22;
+
+__device__ __forceinline__ void store_row8(bf16 *tile, int row, int k0, int kdim, const float (&v)[8]) {
+  uint4 u = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  *reinterpret_cast<uint4 *>(tile + tc::core_index(row, k0, kdim)) = u;
+}
+
+// every thread: all of this CTA's MMAs issued so far have completed?
+__device__ __forceinline__ bool tc_layer_wait(TcSmem &S, uint32_t &phase, int *flags) {
+  const bool ok = __syncthreads_and(tc::mbar_wait(&S.bar, phase, kTcPolls)) != 0;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(flags, 2);
+    tc::mbar_wait(&S.bar, phase, kTcPolls);   // drain the MMAs in flight before TMEM is freed
+  }
+  phase ^= 1u;
+  tc::fence_after_sync();
+  return ok;
+}
+
+// generic writes of the A operand done: make them visible to the tensor core
+__device__ __forceinline__ void tc_operands_ready() {
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+__global__ void __launch_bounds__(kThreads) mlp_hamiltonian_tc_kernel(
+    const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n, int64_t n_slices, Box B,
+    float rcut, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const int32_t *__restrict__ cnt, const float *__restrict__ cmix, const float *__restrict__ v,
+    const float *__restrict__ mean, const float *__restrict__ inv_std, const bf16 *__restrict__ wb,
+    const float *__restrict__ p, float *__restrict__ y0, float *__restrict__ y1, int *__restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw + ((128 - (smem_u32_generic(tc_raw) & 127)) & 127));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < 64 * 32; e += kThreads) S.w1[tc::core_index(e >> 5, e & 31, 32)] = wb[WB_W1 + e];
+  for (int e = tid; e < 64 * 64; e += kThreads) S.w2[tc::core_index(e >> 6, e & 63, 64)] = wb[WB_W2 + e];
+  for (int e = tid; e < 16 * 64; e += kThreads)
+    S.w3[tc::core_index(e >> 6, e & 63, 64)] = (e >> 6) < 2 ? wb[WB_W3 + e] : __float2bfloat16(0.0f);
+  for (int e = tid; e < 64; e += kThreads) {
+    S.b1[e] = p[OFF_B1 + e];
+    S.b2[e] = p[OFF_B2 + e];
+  }
+  if (tid < 2) S.b3[tid] = p[OFF_B3 + tid];
+  load_mixing(S.sc, cmix);
+  if (tid < 32) {
+    S.smean[tid] = mean ? mean[tid] : 0.0f;
+    S.sinv[tid] = inv_std ? inv_std[tid] : 1.0f;
+  }
+  if (tid == 0) tc::mbar_init(&S.bar, 1);
+  if (warp == 0) tc::alloc(&S.tmem, 128);
+  tc_operands_ready();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t id64 = tc::idesc_bf16(TILE, 64), id16 = tc::idesc_bf16(TILE, 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t k = blockIdx.x; k < n_slices && ok; k += gridDim.x) {
+    const int64_t sb = slice_ptr[k];
+    const int w = static_cast<int>((slice_ptr[k + 1] - sb) >> 5);
+    for (int c0 = 0; c0 < w && ok; c0 += 4) {
+      // features of edge tid: slot c0 + warp of row k*32 + lane
+      const int slot = c0 + warp;
+      const int64_t i = k * 32 + (tid & 31);
+      const bool valid = slot < w && i < n && slot < cnt[i];
+      {
+        float x[32];
+        if (valid) {
+          edge_features(pos, species, B, rcut, S.sc, v, i, col[sb + 32 * slot + (tid & 31)], x);
+#pragma unroll
+          for (int f = 0; f < 32; ++f) x[f] = (x[f] - S.smean[f]) * S.sinv[f];
+        } else {
+#pragma unroll
+          for (int f = 0; f < 32; ++f) x[f] = 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float c8[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) c8[j] = x[8 * q + j];
+          store_row8(S.xa, tid, 8 * q, 32, c8);
+        }
+      }
+      tc_operands_ready();
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          tc::mma_bf16(tmem, tc::desc_kmajor(S.xa + ks * 128, 32), tc::desc_kmajor(S.w1 + ks * 128, 32), id64,
+                       ks > 0);
+        tc::commit(&S.bar);
+      }
+      if (!(ok = tc_layer_wait(S, phase, flags))) break;
+      // layer 1 epilogue: H = silu(D1 + b1)
+#pragma unroll 1
+      for (int c = 0; c < 64; c += 16) {
+        float d[16];
+        tc::ld16(tmem + lane_base + (uint32_t)c, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float c8[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) c8[j] = silu(d[8 * h + j] + S.b1[c + 8 * h + j]);
+          store_row8(S.ha, tid, c + 8 * h, 64, c8);
+        }
+      }
+      tc_operands_ready();
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          tc::mma_bf16(tmem + 64, tc::desc_kmajor(S.ha + ks * 128, 64), tc::desc_kmajor(S.w2 + ks * 128, 64), id64,
+                       ks > 0);
+        tc::commit(&S.bar);
+      }
+      if (!(ok = tc_layer_wait(S, phase, flags))) break;
+      // layer 2 epilogue: H = silu(D2 + b2) (layer 2 has finished reading H)
+#pragma unroll 1
+      for (int c = 0; c < 64; c += 16) {
+        float d[16];
+        tc::ld16(tmem + lane_base + 64u + (uint32_t)c, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float c8[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) c8[j] = silu(d[8 * h + j] + S.b2[c + 8 * h + j]);
+          store_row8(S.ha, tid, c + 8 * h, 64, c8);
+        }
+      }
+      tc_operands_ready();
+      if (tid == 0) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          tc::mma_bf16(tmem, tc::desc_kmajor(S.ha + ks * 128, 64), tc::desc_kmajor(S.w3 + ks * 128, 64), id16,
+                       ks > 0);
+        tc::commit(&S.bar);
+      }
+      if (!(ok = tc_layer_wait(S, phase, flags))) break;
+      float o[2];
+      tc::ld2(tmem + lane_base, o);
+      if (valid) {
+        const int64_t e = sb + 32 * slot + (tid & 31);
+        y0[e] = o[0] + S.b3[0];
+        y1[e] = o[1] + S.b3[1];
+      }
+      tc::fence_before_sync();   // D3 read before the next tile's layer 1 overwrites it
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, 128);
+}
+
 // val = (y0(i->j) + y0(j->i)) / 2, diag = eps0[Z_i] + sum_j y1(i->j)
 template <typename valT>
 __global__ void learned_assemble_kernel(int64_t n, int64_t n_slices, const int64_t *__restrict__ slice_ptr,
@@ -1004,10 +1200,17 @@ extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t
   int *flags = cv.take<int>(4);
   TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
   const int64_t n_slices = (n + 31) / 32;
-  const int grid = grid_cap(n_slices, 8);
-  mlp_hamiltonian_kernel<<<grid, kThreads, 0, st>>>(positions, species, n, n_slices, B, (float)rcut, slice_ptr, col,
-                                                    cnt, cmix, v, mean, inv_std, static_cast<const bf16 *>(w_bf16),
-                                                    params, y0, y1);
+  if (g_mlp_variant == 1) {
+    const int grid = grid_cap(n_slices, 8);
+    mlp_hamiltonian_kernel<<<grid, kThreads, 0, st>>>(positions, species, n, n_slices, B, (float)rcut, slice_ptr,
+                                                      col, cnt, cmix, v, mean, inv_std,
+                                                      static_cast<const bf16 *>(w_bf16), params, y0, y1);
+  } else {
+    const int grid = grid_cap(n_slices, 4);
+    mlp_hamiltonian_tc_kernel<<<grid, kThreads, kTcSmemBytes, st>>>(
+        positions, species, n, n_slices, B, (float)rcut, slice_ptr, col, cnt, cmix, v, mean, inv_std,
+        static_cast<const bf16 *>(w_bf16), params, y0, y1, flags);
+  }
   TB_CHECK_LAUNCH();
   const unsigned nb = (unsigned)((n_slices * 32 + 255) / 256);
   if (precision == TB_F32)
@@ -1021,6 +1224,13 @@ extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t
   int h = 0;
   TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
   TB_CUDA(cudaStreamSynchronize(st));
+  if (h & 2) return fail(TB_ERR_TIMEOUT, "tb_build_hamiltonian: a tensor-core completion wait timed out");
   if (h & 1) return fail(TB_ERR_INVALID_ARG, "tb_build_hamiltonian: neighbour relation is not symmetric");
+  return TB_OK;
+}
+
+extern "C" tb_status tb_mlp_set_variant(int32_t variant) {
+  TB_REQUIRE(variant == 0 || variant == 1, "tb_mlp_set_variant: variant must be 0 (tcgen05) or 1 (mma.sync)");
+  g_mlp_variant = variant;
   return TB_OK;
 }

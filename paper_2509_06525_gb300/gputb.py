@@ -48,6 +48,7 @@ SIGNATURES = {
     "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
+    "tb_mlp_set_variant": (_c_i32, [_c_i32]),
     "tb_debug_wait_timeout": (_c_i32, [_c_i32, _c_i64, _c_vp, _c_sz, _c_vp]),
     "tb_velocity_values": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
                                     _c_vp, _c_vp]),
@@ -244,6 +245,11 @@ def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel
                    energy.numel(), _ptr(out), _stream(stream))
     _check("kpm_dos", st)
     return out
+
+
+def mlp_set_variant(variant: int):
+    """Forward kernel of build_hamiltonian: 0 = tcgen05 (TMEM), 1 = mma.sync."""
+    _check("tb_mlp_set_variant", lib().tb_mlp_set_variant(int(variant)))
 
 
 def debug_wait_timeout(which: int, polls: int, stream=None):

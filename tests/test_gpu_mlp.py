@@ -162,7 +162,16 @@ def test_adamw_matches_oracle(g):
     np.testing.assert_array_equal(wb[:2048], torch.tensor(got["W1"].reshape(-1)).to(torch.bfloat16).float().numpy())
 
 
-def test_learned_hamiltonian_matches_oracle(g):
+@pytest.fixture(params=[0, 1], ids=["tcgen05", "mma_sync"])
+def mlp_variant(request, g):
+    """Forward kernel of the learned H: 5th-generation tensor cores (TMEM
+    accumulators) or mma.sync tiles."""
+    g.mlp_set_variant(request.param)
+    yield request.param
+    g.mlp_set_variant(0)
+
+
+def test_learned_hamiltonian_matches_oracle(g, mlp_variant):
     s = synth.graphene_primitive(20, 20, 0.1, 8)
     cm = synth.descriptor_mixing("identity")
     p, model = _model(g, 4)
@@ -185,3 +194,24 @@ def test_learned_hamiltonian_matches_oracle(g):
     lookup = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(np.repeat(np.arange(s.n), np.diff(indptr)), idx))}
     for (i, j), k in list(lookup.items())[:2000]:
         assert hop[k] == hop[lookup[(j, i)]]
+
+
+def test_tcgen05_and_mma_sync_forward_agree_on_many_tiles(g):
+    """9600-atom junction-free sheet (75 x 32 tiles, ragged last chunks of
+    each slice): both forward kernels give the same learned H up to the
+    order of the FP32 sums (and the BF16 roundings that order can flip)."""
+    s = synth.graphene_rect(60, 40, 0.1, 12)
+    cm = synth.descriptor_mixing("identity")
+    p, model = _model(g, 9)
+    pos = torch.tensor(s.positions, device="cuda")
+    spc = torch.tensor(s.species, device="cuda")
+    nb = g.build_neighbors(pos, s.box, s.pbc, 3.0, r_count=1.8)
+    out = []
+    for variant in (0, 1):
+        g.mlp_set_variant(variant)
+        H = g.build_hamiltonian(pos, spc, s.box, s.pbc, 3.0, nb, model, dtype=torch.float32)
+        out.append((H.val.cpu().numpy().astype(np.float64), H.diag.cpu().numpy().astype(np.float64)))
+    g.mlp_set_variant(0)
+    assert rel_l2(out[0][0], out[1][0]) <= 5e-3
+    assert rel_l2(out[0][1], out[1][1]) <= 5e-3
+    assert np.all(np.isfinite(out[0][0]))
