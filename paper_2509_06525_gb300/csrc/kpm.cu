@@ -22,6 +22,7 @@
 //   (no extra read of v_{n+1}), accumulated in FP64, reduced by warp
 //   shuffles and shared memory to one partial per CTA and step, and summed
 //   in a fixed order by a final kernel: results are bitwise reproducible.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -131,7 +132,8 @@ struct KpmRunner : StepKit<real, valT, R> {
   static size_t workspace(int64_t n, int M, bool segmented) {
     Carver cv(nullptr, 0);
     for (int k = 0; k < 3; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
-    cv.take<double>((size_t)(M + 1) * (segmented ? blocks(n) : grid_for(n)) * R);
+    const int64_t units = segmented ? blocks(n) : std::max(grid_for(n, false), grid_for(n, true));
+    cv.take<double>((size_t)(M + 1) * units * R);
     cv.take<int>(4);
     if (!segmented) {
       PairWs pw;
@@ -314,9 +316,9 @@ struct KpmRunner : StepKit<real, valT, R> {
   static tb_status run(int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val, const valT *diag,
                        double a, double b, int M, uint64_t seed, int64_t r0, int mode, double *mu_r, void *ws,
                        size_t ws_bytes, cudaStream_t st, double *step_ms) {
-    const int grid = grid_for(n);
-    const int64_t np = padded_rows(n);
     const bool dbl = mode == TB_KPM_DOUBLING;
+    const int grid = grid_for(n, dbl);
+    const int64_t np = padded_rows(n);
     Carver cv(ws, ws_bytes);
     real *v0 = cv.take<real>((size_t)np * R * 2);
     real *A = cv.take<real>((size_t)np * R * 2);
@@ -356,8 +358,8 @@ struct KpmRunner : StepKit<real, valT, R> {
   static tb_status run_batched(int64_t n_pad, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                                const valT *diag, int M, uint64_t seed, int mode, const BatchTables &bt,
                                double *mu, void *ws, size_t ws_bytes, cudaStream_t st, double *graph_ms) {
-    const int grid = grid_for(n_pad);
     const bool dbl = mode == TB_KPM_DOUBLING;
+    const int grid = grid_for(n_pad, dbl);
     Carver cv(ws, ws_bytes);
     real *v0 = cv.take<real>((size_t)n_pad * R * 2);
     real *A = cv.take<real>((size_t)n_pad * R * 2);

@@ -55,7 +55,10 @@ constexpr int direct_min_blocks() {
 }
 template <typename real, int R, int CPT>
 constexpr int bulk_min_blocks() {
-  return (sizeof(real) == 4 && CPT == 2 && R >= 8) ? 4 : 1;
+#ifndef TB_BULK_MINB_R8
+#define TB_BULK_MINB_R8 4
+#endif
+  return (sizeof(real) == 4 && CPT == 2 && R >= 8) ? TB_BULK_MINB_R8 : 1;
 }
 
 // Write the CTA's partial sums as entry `idx` of the moment slot (and of the
@@ -200,7 +203,13 @@ __global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) che
 // and val.  Every wait is bounded: on timeout the CTA drains its own copies
 // (bounded again), raises flags[0] |= 4 and returns.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 3;
+#ifndef TB_KPM_STAGES
+#define TB_KPM_STAGES 3
+#endif
+// pipeline depth (tuning macro): measured on GB300 at 10M atoms, R = 8, doubling
+// mode: 3 stages 375 ms, 4 stages 392 ms (the extra shared memory costs
+// resident CTAs)
+constexpr int kStages = TB_KPM_STAGES;
 constexpr long long kWaitPolls = 1ll << 21;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -234,7 +243,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-template <typename real, typename valT, int R, int CPT>
+// NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode)
+template <typename real, typename valT, int R, int CPT, int NV = 2>
 struct BulkGeom {
   static constexpr int TPR = R / CPT;
   static constexpr int TR = kBlock / TPR;                       // rows per tile
@@ -242,7 +252,7 @@ struct BulkGeom {
   static constexpr size_t kColBytes = kEl * sizeof(int32_t);
   static constexpr size_t kValBytes = kEl * sizeof(valT);
   static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
-  static constexpr size_t kStageBytes = kColBytes + kValBytes + 2 * kVecBytes;
+  static constexpr size_t kStageBytes = kColBytes + kValBytes + NV * kVecBytes;
   static constexpr size_t kSmem = 128 + kStages * kStageBytes;  // mbarriers first
   static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024;
 };
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
     int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
-  using G = BulkGeom<real, valT, R, CPT>;
+  using G = BulkGeom<real, valT, R, CPT, DBL ? 1 : 2>;
   constexpr int TPR = G::TPR, TR = G::TR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -434,6 +444,8 @@ struct StepKit {
   static constexpr int TPR = R / CPT;
   static constexpr int RPB = kBlock / TPR;
   using G = BulkGeom<real, valT, R, CPT>;
+  template <bool DBL>
+  using GB = BulkGeom<real, valT, R, CPT, DBL ? 1 : 2>;   // the stage size of each mode
   static constexpr int64_t kRowPad = 256;   // vector blocks hold whole tiles
 
   // the pipeline wins where several threads share a row (R >= 8 in FP32 on
@@ -443,21 +455,30 @@ struct StepKit {
     return g_kpm_variant == 2 || TPR >= 4;
   }
 
-  static int grid_for(int64_t n) {
-    static int per_sm_direct = 0, per_sm_bulk = 0;
+  // resident CTAs x SMs (doubling mode streams one vector less per stage,
+  // so its pipelined kernel may fit more CTAs)
+  static int grid_for(int64_t n, bool dbl = false) {
+    static int per_sm_direct = 0, per_sm_bulk[2] = {0, 0};
     if (use_bulk()) {
-      if (per_sm_bulk == 0) {
+      int &pb = per_sm_bulk[dbl ? 1 : 0];
+      if (pb == 0) {
         int b = 0;
-        cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                                                          kBlock, G::kSmem) != cudaSuccess ||
-            b <= 0)
-          b = 1;
-        per_sm_bulk = b;
+        cudaError_t e;
+        if (dbl) {
+          cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<true>::kSmem);
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &b, cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>, kBlock, GB<true>::kSmem);
+        } else {
+          cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<false>::kSmem);
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>, kBlock, GB<false>::kSmem);
+        }
+        pb = (e != cudaSuccess || b <= 0) ? 1 : b;
       }
       const int64_t need = (n + G::TR - 1) / G::TR;
-      const int64_t cap = (int64_t)per_sm_bulk * sm_count();
+      const int64_t cap = (int64_t)pb * sm_count();
       return static_cast<int>(need < cap ? need : cap);
     }
     if (per_sm_direct == 0) {
@@ -477,23 +498,23 @@ struct StepKit {
   // stream capture)
   static void prepare() {
     if (!use_bulk()) return;
-    const int sm = (int)G::kSmem;
+    const int s1 = (int)GB<true>::kSmem, s2 = (int)GB<false>::kSmem;
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
     cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
   }
 
   template <bool FIRST, bool DBL, bool SEG>
@@ -502,7 +523,7 @@ struct StepKit {
                         double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
                         const BatchTables &bt, cudaStream_t st) {
     if (use_bulk())
-      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, G::kSmem, st>>>(
+      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, GB<DBL>::kSmem, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt);
     else
       cheb_step_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
