@@ -49,6 +49,7 @@ L2_BYTES = 126 * 1024 * 1024
 # kernels (profiles/traffic_cheb_step_bench_workloads.md); any other
 # configuration, or a changed kernel, reports null.
 MEASURED_TRAFFIC = {
+    ("graphene-10M-learned", "mlp", "doubling", 1024, 8): 2_897_906_176,
     ("graphene-100M", "teacher", "doubling", 1024, 1): 11_994_291_456,
 }
 
