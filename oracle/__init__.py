@@ -26,6 +26,8 @@ Modules and the passages they follow (arXiv 2509.06525):
 * dos          -- Jackson-damped KPM density of states, Eq. 4.
 * lsqt         -- velocity operator, time evolution and the velocity
                   autocorrelation conductivity of Eq. 3 (sigma), Sec. 2.4.
+* slater_koster -- the s, p, d Slater-Koster Hamiltonian (angular factors
+                  of Sec. 3) by rotation of the bond-frame block.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, dense diagonalisation, invariants, brute force, independent

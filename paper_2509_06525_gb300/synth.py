@@ -188,6 +188,25 @@ def teacher_hbn_graphene() -> TeacherParams:
     return TeacherParams(p, onsite)
 
 
+@dataclass
+class SKTeacher:
+    """Synthetic s, p, d Slater-Koster teacher for carbon (no trained
+    network here): the ten two-centre integrals (eV) in the order ss_sigma,
+    sp_sigma, pp_sigma, pp_pi, sd_sigma, pd_sigma, pd_pi, dd_sigma, dd_pi,
+    dd_delta, each with the distance form V0 exp(-beta (r/a_cc - 1)) f_c(r),
+    and onsite energies E_s, E_p, E_d.  The numbers are synthetic."""
+    v0: np.ndarray
+    onsite: np.ndarray
+    a_cc: float = 1.42
+    beta: float = 3.0
+    rcut: float = 3.0
+
+
+def teacher_sk_graphene() -> SKTeacher:
+    return SKTeacher(np.array([-5.0, 5.4, 6.2, -2.9, -2.0, -2.4, 1.2, -1.8, 1.0, -0.3]),
+                     np.array([-7.5, 0.0, 14.0]))
+
+
 N_BASIS = 8          # radial Chebyshev functions f_0..f_7
 N_FEAT = 32          # per-edge MLP input width
 N_HIDDEN = 64
