@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 4
+#define GPUTB_ABI_VERSION 5
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -288,6 +288,48 @@ TB_API tb_status lsqt_correlation(const double *mu, int32_t n_times, int32_t R, 
                                   int32_t kernel, double lambda, double a, double b,
                                   const double *energy, int32_t K, double dt_fs, double *corr,
                                   double *sigma, double *coef_ws, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Multi-orbital (s, p, d) Slater-Koster Hamiltonian, matrix-free (the SK
+ * angular factors of Sec. 3; orbitals per atom: s, p_x, p_y, p_z, d_xy,
+ * d_yz, d_zx, d_x2-y2, d_3z2-r2, orbital index 9 i + a).  Each SELL element
+ * of the neighbour structure keeps the compressed SK form of its bond --
+ * direction cosines l, m, n of d_ij = r_j - r_i and the ten two-centre
+ * integrals V_k(r) = v0[k] exp(-beta (r/a_cc - 1)) f_c(r) in the order
+ * ss_sigma, sp_sigma, pp_sigma, pp_pi, sd_sigma, pd_sigma, pd_pi, dd_sigma,
+ * dd_pi, dd_delta -- and every use rebuilds the 9 x 9 block from the
+ * closed-form Slater-Koster table.
+ *
+ * tb_sk_geometry: geom = device float [13][total] planes (l, m, n, V_0..V_9;
+ *   zero for padding slots and phantom rows); positions/box/pbc/rcut as
+ *   tb_build_neighbors; v0 host double [10].  Synchronises `stream`.
+ * tb_sk_bounds: Gershgorin enclosure of the spectrum (onsite host double [3]:
+ *   E_s, E_p, E_d) -> bounds_out host double [4] = {E_min, E_max, a, b} with
+ *   a = (E_max - E_min)/(2 - 0.01), b = midpoint; workspace >= 4 KB +
+ *   16 bytes per CTA (use sk_kpm_workspace_size).  Synchronises `stream`.
+ * sk_kpm_moments: KPM moments of the 9N-orbital H for random-phase vector
+ *   first_vector (orbital index as the row: u(seed, first_vector, 9 i + a)),
+ *   moment doubling, complex FP32 vectors, FP64 sums:
+ *   mu_out device double [M] = Re <v0|T_n(H~)|v0> / (9N).  Checks |mu| <= 1
+ *   + 1e-6 (TB_ERR_BOUNDS) and finiteness.  ms_out as lsqt_vac.
+ * ------------------------------------------------------------------- */
+TB_API tb_status tb_sk_geometry(const double *positions, int64_t n, const double *box,
+                                const int32_t *pbc, double rcut, const int64_t *slice_ptr,
+                                const int32_t *col, int64_t total, const double *v0, double a_cc,
+                                double beta, float *geom, void *stream);
+
+TB_API tb_status tb_sk_bounds(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                              const float *geom, int64_t total, const double *onsite,
+                              double *bounds_out, void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+TB_API size_t sk_kpm_workspace_size(int64_t n, int32_t M);
+
+TB_API tb_status sk_kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                                const float *geom, int64_t total, const double *onsite, double a,
+                                double b, int32_t M, uint64_t seed, int64_t first_vector,
+                                double *mu_out, void *workspace, size_t workspace_bytes,
+                                void *stream, double *ms_out);
 
 /* ---------------------------------------------------------------------
  * Neighbour lists N(i) of Eq. 1 (Sec. 3): every j != i with a periodic

@@ -49,6 +49,12 @@ SIGNATURES = {
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
     "tb_mlp_set_variant": (_c_i32, [_c_i32]),
+    "tb_sk_geometry": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_i64, _c_vp, _c_dbl, _c_dbl,
+                                _c_vp, _c_vp]),
+    "tb_sk_bounds": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "sk_kpm_workspace_size": (_c_sz, [_c_i64, _c_i32]),
+    "sk_kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_i64, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_u64, _c_i64,
+                                _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "tb_debug_wait_timeout": (_c_i32, [_c_i32, _c_i64, _c_vp, _c_sz, _c_vp]),
     "tb_velocity_values": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
                                     _c_vp, _c_vp]),
@@ -95,7 +101,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 4   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 5   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -245,6 +251,55 @@ def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel
                    energy.numel(), _ptr(out), _stream(stream))
     _check("kpm_dos", st)
     return out
+
+
+# ------------------------------------------------------------------ s, p, d Slater-Koster model
+
+def sk_geometry(positions: torch.Tensor, box, pbc, nb: "Neighbors", sk, stream=None) -> torch.Tensor:
+    """tb_sk_geometry: [13, total] float32 planes (l, m, n, V_0..V_9)."""
+    import numpy as np
+    L = lib()
+    b, p, bptr, pptr = _host_box(box, pbc)
+    v0 = np.ascontiguousarray(np.asarray(sk.v0, np.float64).reshape(10))
+    geom = torch.empty((13, max(nb.total, 1)), dtype=torch.float32, device=positions.device)
+    st = L.tb_sk_geometry(_ptr(positions), nb.n, bptr, pptr, float(sk.rcut), _ptr(nb.slice_ptr), _ptr(nb.col),
+                          nb.total, v0.ctypes.data_as(ctypes.c_void_p), float(sk.a_cc), float(sk.beta), _ptr(geom),
+                          _stream(stream))
+    _check("tb_sk_geometry", st)
+    return geom
+
+
+def sk_bounds(nb: "Neighbors", geom: torch.Tensor, sk, stream=None):
+    """(E_min, E_max, a, b) from the Gershgorin row sums of the SK blocks."""
+    import numpy as np
+    L = lib()
+    on = np.ascontiguousarray(np.asarray(sk.onsite, np.float64).reshape(3))
+    ws = _workspace(L.sk_kpm_workspace_size(nb.n, 2), geom.device)
+    out = np.zeros(4, np.float64)
+    st = L.tb_sk_bounds(nb.n, _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(geom), nb.total,
+                        on.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p), _ptr(ws),
+                        ws.numel(), _stream(stream))
+    _check("tb_sk_bounds", st)
+    return tuple(float(v) for v in out)
+
+
+def sk_kpm_moments(nb: "Neighbors", geom: torch.Tensor, sk, a: float, b: float, M: int, seed: int,
+                   first_vector: int = 0, stream=None, timing: Optional[list] = None) -> torch.Tensor:
+    """KPM moments [M] of the 9N-orbital SK Hamiltonian for one random vector."""
+    import numpy as np
+    L = lib()
+    on = np.ascontiguousarray(np.asarray(sk.onsite, np.float64).reshape(3))
+    ws = _workspace(L.sk_kpm_workspace_size(nb.n, M), geom.device)
+    mu = torch.empty(M, dtype=torch.float64, device=geom.device)
+    ms = ctypes.c_double(0.0)
+    st = L.sk_kpm_moments(nb.n, _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(geom), nb.total,
+                          on.ctypes.data_as(ctypes.c_void_p), float(a), float(b), int(M),
+                          int(seed) & ((1 << 64) - 1), int(first_vector), _ptr(mu), _ptr(ws), ws.numel(),
+                          _stream(stream), ctypes.byref(ms) if timing is not None else None)
+    _check("sk_kpm_moments", st)
+    if timing is not None:
+        timing.append(ms.value)
+    return mu
 
 
 def mlp_set_variant(variant: int):
