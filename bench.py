@@ -71,6 +71,7 @@ def parse_args():
                    help="epochs of the untimed model training (default: the training default); fewer for profiling")
     p.add_argument("--M", type=int, default=None, help="override the workload's moment count (profiling)")
     p.add_argument("--R", type=int, default=None, help="override the workload's vector count (profiling)")
+    p.add_argument("--sk", type=int, default=1, help="measure the s, p, d Slater-Koster KPM (1) or skip it (0)")
     p.add_argument("--lsqt-steps", type=int, default=2,
                    help="VAC conductivity time steps of 0.1 fs measured after the main line (0: skip)")
     return p.parse_args()
@@ -224,6 +225,39 @@ def timed(torch, dist, fn, steps, warmup):
         from paper_2509_06525_gb300.distributed import max_over_ranks
         ms = max_over_ranks(ms, "cuda")
     return ms
+
+
+def sk_measurement(pipe, torch, g):
+    """The s, p, d Slater-Koster model on the same structure (9 orbitals per
+    atom, matrix-free): compressed SK form, Gershgorin bounds and the KPM
+    moments of one random vector with the workload's M; CUDA-event time of the
+    moments (after a warm-up call)."""
+    s = pipe.s
+    sk = synth.teacher_sk_graphene()
+    nb = g.build_neighbors(pipe.pos, s.box, s.pbc, sk.rcut, r_count=0.0)
+    geom = g.sk_geometry(pipe.pos, s.box, s.pbc, nb, sk)
+    emin, emax, a, b = g.sk_bounds(nb, geom, sk)
+    g.sk_kpm_moments(nb, geom, sk, a, b, 64, pipe.seed, first_vector=pipe.first_vector)
+    ms = []
+    mu = g.sk_kpm_moments(nb, geom, sk, a, b, pipe.M, pipe.seed, first_vector=pipe.first_vector, timing=ms)
+    launches = (pipe.M - 1) // 2 + 1
+    per = ms[0] / launches
+    nnz = nb.total
+    step_bytes = nnz * (13 * 4 + 4) + 3 * s.n * 9 * 8      # compressed SK form + col, x gathered once, v_{n-1}, v_{n+1}
+    flops = nnz * 700                                       # ~45 table entries + 81 complex MACs per pair
+    peak, src = hbm_peak()
+    achieved = step_bytes / (per * 1e-3) / 1e9
+    out = {"orbitals": 9 * s.n, "moments": pipe.M, "random_vectors": 1, "ms": ms[0],
+           "orbital_moments_per_s": 9 * s.n * pipe.M / (ms[0] * 1e-3),
+           "bounds": {"emin": emin, "emax": emax},
+           "roofline": {"bound": "hbm", "kernel": "sk_step (matrix-free SK block SpMV + moment dots)",
+                        "bytes_per_launch": step_bytes, "ms_per_launch": per, "achieved": achieved,
+                        "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                        "fp32_tflops": flops / (per * 1e-3) / 1e12},
+           "mu1": float(mu[1].item())}
+    del geom, nb
+    torch.cuda.empty_cache()
+    return out
 
 
 def lsqt_measurement(pipe, n_steps, torch, g, dt=0.1):
@@ -390,6 +424,8 @@ def run_ours(args):
     # FP64 comparison below replaces it
     if args.lsqt_steps > 0:
         out["lsqt"] = lsqt_measurement(pipe, args.lsqt_steps, torch, g)
+    if args.sk:
+        out["sk"] = sk_measurement(pipe, torch, g)
 
     # plain FP64 teacher form on the same structure and GPU, and the DOS
     # error of the timed (learned FP32 by default) path against it
