@@ -185,11 +185,17 @@ struct KpmRunner : StepKit<real, valT, R> {
     static int per_sm = 0;
     if (per_sm == 0) {
       int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_pair_kernel<real, valT, R, CPT>, kBlock, 0) !=
-              cudaSuccess ||
-          b <= 0)
-        b = 1;
-      per_sm = b;
+      cudaError_t e;
+      if (use_bulk()) {
+        using GP = BulkGeom<real, valT, R, CPT, 1>;
+        cudaFuncSetAttribute(cheb_pair_bulk_kernel<real, valT, R, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GP::kSmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_pair_bulk_kernel<real, valT, R, CPT>, kBlock,
+                                                          GP::kSmem);
+      } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_pair_kernel<real, valT, R, CPT>, kBlock, 0);
+      }
+      per_sm = (e != cudaSuccess || b <= 0) ? 1 : b;
     }
     const int g = per_sm * sm_count();
     return g < kMaxPairGrid ? g : kMaxPairGrid;
@@ -226,8 +232,14 @@ struct KpmRunner : StepKit<real, valT, R> {
     PairPlan plan = w.plan;
     double *bpart = w.bpart;
     void *args[] = {&n, &slice_ptr, &col, &val, &diag, &P, &Q, &plan, &pair, &bpart, &alpha, &shift, &flags};
-    TB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(cheb_pair_kernel<real, valT, R, CPT>),
-                                        dim3(pair_grid()), dim3(kBlock), args, 0, st));
+    if (use_bulk()) {
+      using GP = BulkGeom<real, valT, R, CPT, 1>;
+      TB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(cheb_pair_bulk_kernel<real, valT, R, CPT>),
+                                          dim3(pair_grid()), dim3(kBlock), args, GP::kSmem, st));
+    } else {
+      TB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(cheb_pair_kernel<real, valT, R, CPT>),
+                                          dim3(pair_grid()), dim3(kBlock), args, 0, st));
+    }
     note_launch();
     return TB_OK;
   }

@@ -44,6 +44,7 @@
 #include <climits>
 
 #include "kpm_common.cuh"
+#include "kpm_step.cuh"
 
 namespace gputb {
 namespace kpmdev {
@@ -234,6 +235,186 @@ __global__ void __launch_bounds__(kBlock, (2 * CPT * sizeof(real) >= 32) ? 2 : 4
       else if (threadIdx.x == 0)
         atomicOr(flags, 4);
     }
+  }
+}
+
+// The same two-step scheme on the bulk-copy pipeline (several threads per
+// row, R >= 8): the CTA's task positions are static, so its issuing thread
+// streams the next kStages tasks' matrix slices and v_{n-1} rows (stage 1:
+// P rows, stage 2: Q rows -- only the task itself writes them) into the
+// shared-memory ring while the CTA computes; a stage-2 task then waits for
+// its stage-1 dependencies (flags) before it gathers the fresh v_m.
+template <typename real, typename valT, int R, int CPT, bool STAGE2>
+__device__ __forceinline__ void pair_bulk_tile(int64_t blk, int64_t n, const int64_t *__restrict__ slice_ptr,
+                                               const int32_t *__restrict__ col, const valT *__restrict__ val,
+                                               const valT *__restrict__ diag, const int32_t *scol, const valT *sval,
+                                               const real *sprev, const real *x, real *out,
+                                               double *__restrict__ bpart, int64_t nb, real alpha, real shift) {
+  using G = BulkGeom<real, valT, R, CPT, 1>;
+  constexpr int TPR = G::TPR, TR = G::TR;
+  const int part = threadIdx.x % TPR;
+  const int lr = threadIdx.x / TPR;
+  DotAcc<real> acc[CPT], acc2[CPT];
+  const int64_t r0 = blk * TR;
+  const int64_t i = r0 + lr;
+  if (i < n) {
+    const int64_t k0 = r0 >> 5;
+    const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
+    const int64_t e0 = __ldg(slice_ptr + k0);
+    const bool bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
+    real p[2 * CPT];
+    memcpy(p, sprev + (lr * R + part * CPT) * 2, sizeof(p));
+    const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
+    const int64_t sb = __ldg(slice_ptr + (i >> 5));
+    const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
+    real y[2 * CPT];
+#pragma unroll
+    for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
+    if (bulk) {
+      const int32_t *cs = scol + (sb - e0) + (i & 31);
+      const valT *vs = sval + (sb - e0) + (i & 31);
+#pragma unroll
+      for (int s = 0; s < kFastW; ++s) {
+        if (s < w) {
+          real xv[2 * CPT];
+          const real h = static_cast<real>(vs[32 * s]);
+          ld_weak<real, CPT>(x + ((int64_t)cs[32 * s] * R + part * CPT) * 2, xv);
+#pragma unroll
+          for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+        }
+      }
+    } else {
+      int64_t e = sb + (i & 31);
+      for (int s = 0; s < w; ++s, e += 32) {
+        const int32_t jj = __ldg(col + e);
+        const real hh = static_cast<real>(__ldg(val + e));
+        real xv[2 * CPT];
+        ld_weak<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
+#pragma unroll
+        for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
+      }
+    }
+    const int64_t off = (i * R + part * CPT) * 2;
+    real xi[2 * CPT];
+    ld_weak<real, CPT>(x + off, xi);
+#pragma unroll
+    for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
+    real o[2 * CPT];
+#pragma unroll
+    for (int c = 0; c < 2 * CPT; ++c) o[c] = fma(alpha, y[c], -p[c]);
+    if (STAGE2)
+      st_stream<real, CPT>(out + off, o);
+    else
+      st_l2<real, CPT>(out + off, o);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
+      acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
+    }
+  }
+  double sum[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) sum[c] = acc[c].value();
+  double *slot = bpart + (STAGE2 ? 2 : 0) * nb * R;
+  cta_partial<R, CPT>(sum, slot + blk * R);
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) sum[c] = acc2[c].value();
+  cta_partial<R, CPT>(sum, slot + nb * R + blk * R);
+  __syncthreads();
+}
+
+template <typename real, typename valT, int R, int CPT>
+__global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>())
+    cheb_pair_bulk_kernel(int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+                          const valT *__restrict__ val, const valT *__restrict__ diag, real *P, real *Q,
+                          PairPlan plan, int pair, double *__restrict__ bpart, real alpha, real shift, int *flags) {
+  using G = BulkGeom<real, valT, R, CPT, 1>;
+  constexpr int TR = G::TR;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long s_tot;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *ring = smem + 128;
+  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes); };
+  auto s_val = [&](int st) { return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kColBytes); };
+  auto s_prev = [&](int st) {
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes);
+  };
+  const int epoch = pair + 1;
+  const int64_t ntask = 2 * plan.nb;
+  const int grid = gridDim.x;
+  const int64_t s1_target = (int64_t)epoch * plan.nb;
+  int s1_mine = (pair == 0 || threadIdx.x != 0) ? 0 : plan.cta_s1[blockIdx.x];
+  const int64_t my_tasks = blockIdx.x < ntask ? (ntask - 1 - blockIdx.x) / grid + 1 : 0;
+  auto task_at = [&](int64_t kk) { return __ldg(plan.tasks + blockIdx.x + kk * grid); };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(full + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // issuing thread: matrix slices and v_{n-1} rows of local task kk
+  auto issue = [&](int64_t kk) {
+    const int task = task_at(kk);
+    const int64_t blk = task >= 0 ? task : ~task;
+    const real *prev_src = task >= 0 ? P : Q;
+    const int st = static_cast<int>(kk % kStages);
+    const int64_t r0 = blk * TR;
+    const int64_t k0 = r0 >> 5;
+    const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
+    const int64_t e0 = slice_ptr[k0], e1 = slice_ptr[k1];
+    const bool bulk = (e1 - e0) <= G::kEl;
+    const uint32_t ebytes = bulk ? static_cast<uint32_t>(e1 - e0) : 0u;
+    uint32_t tx = static_cast<uint32_t>(G::kVecBytes);
+    if (bulk) tx += ebytes * static_cast<uint32_t>(sizeof(int32_t) + sizeof(valT));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(full + st, tx);
+    if (bulk && ebytes > 0) {
+      bulk_g2s(s_col(st), col + e0, ebytes * sizeof(int32_t), full + st);
+      bulk_g2s(s_val(st), val + e0, ebytes * sizeof(valT), full + st);
+    }
+    bulk_g2s(s_prev(st), prev_src + (size_t)r0 * R * 2, static_cast<uint32_t>(G::kVecBytes), full + st);
+  };
+
+  int64_t issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < my_tasks && issued < kStages; ++issued) issue(issued);
+  bool ok = true;
+  int64_t kk = 0;
+  for (; kk < my_tasks; ++kk) {
+    const int st = static_cast<int>(kk % kStages);
+    const uint32_t parity = static_cast<uint32_t>((kk / kStages) & 1);
+    ok = __syncthreads_and(mbar_wait_bounded(full + st, parity)) != 0;
+    if (!ok) break;
+    const int task = task_at(kk);
+    if (task >= 0) {
+      const int64_t blk = task;
+      pair_bulk_tile<real, valT, R, CPT, false>(blk, n, slice_ptr, col, val, diag, s_col(st), s_val(st),
+                                                s_prev(st), Q, P, bpart, plan.nb, alpha, shift);
+      if (threadIdx.x == 0) {   // pair_bulk_tile ends with __syncthreads(): the block is written
+        st_release(plan.done + blk, epoch);
+        st_release(plan.cta_s1 + blockIdx.x, ++s1_mine);
+      }
+    } else {
+      const int64_t blk = ~task;
+      ok = pair_wait(plan, plan.wait[blk], epoch, s1_target, kPairPolls, &s_tot);
+      __threadfence();   // acquire after the relaxed flag polls
+      __syncthreads();
+      if (!ok) break;
+      pair_bulk_tile<real, valT, R, CPT, true>(blk, n, slice_ptr, col, val, diag, s_col(st), s_val(st),
+                                               s_prev(st), P, Q, bpart, plan.nb, alpha, shift);
+    }
+    if (threadIdx.x == 0 && issued < my_tasks) issue(issued++);   // the stage of task kk is free
+  }
+  if (!ok) {
+    // drain this CTA's own copies still in flight (bounded), then report
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 4);
+      for (int64_t q = kk; q < issued; ++q)
+        mbar_wait_bounded(full + q % kStages, static_cast<uint32_t>((q / kStages) & 1));
+    }
+    __syncthreads();
   }
 }
 
