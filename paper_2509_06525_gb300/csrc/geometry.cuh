@@ -59,6 +59,37 @@ __device__ __forceinline__ double3 bond_vector(const Box &B, const double *__res
   return min_image(B, d);
 }
 
+// |r_j - r_i|^2 (minimum image) in FP64, equal to sq_norm(bond_vector()) for
+// every pair closer than half a periodic width: the image shift is decided
+// from FP32 copies of the differences and applied (with the same explicitly
+// rounded operations as min_image) only where it is not zero, which saves
+// the FP64 multiplies and roundings of the common unshifted case.
+__device__ __forceinline__ double bond_r2(const Box &B, const double *__restrict__ pos, int64_t i, int64_t j) {
+  double dx = __dsub_rn(__ldg(pos + 3 * j), __ldg(pos + 3 * i));
+  double dy = __dsub_rn(__ldg(pos + 3 * j + 1), __ldg(pos + 3 * i + 1));
+  double dz = __dsub_rn(__ldg(pos + 3 * j + 2), __ldg(pos + 3 * i + 2));
+  if (B.p3) {
+    const float n3 = rintf((float)dz * (float)B.icz);
+    if (n3 != 0.0f) {
+      dx = __dsub_rn(dx, __dmul_rn((double)n3, B.cx));
+      dy = __dsub_rn(dy, __dmul_rn((double)n3, B.cy));
+      dz = __dsub_rn(dz, __dmul_rn((double)n3, B.cz));
+    }
+  }
+  if (B.p2) {
+    const float n2 = rintf((float)dy * (float)B.iby);
+    if (n2 != 0.0f) {
+      dx = __dsub_rn(dx, __dmul_rn((double)n2, B.bx));
+      dy = __dsub_rn(dy, __dmul_rn((double)n2, B.by));
+    }
+  }
+  if (B.p1) {
+    const float n1 = rintf((float)dx * (float)B.iax);
+    if (n1 != 0.0f) dx = __dsub_rn(dx, __dmul_rn((double)n1, B.ax));
+  }
+  return sq_norm(make_double3(dx, dy, dz));
+}
+
 // |r_j - r_i| (minimum image) in FP32 for the learned-H features: the
 // coordinate differences in FP64 (exact for nearby atoms), the image shift
 // decided from their FP32 values and applied in FP64 only when it is not

@@ -67,13 +67,10 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         const int r = part * CPT + c;
-        double sn = 0.0, co = 0.0;
-        if (real_row) {
-          const double phi = 2.0 * M_PI * phase_uniform(sd, (uint64_t)(r0 + r), (uint64_t)li);
-          sincos(phi, &sn, &co);
-        }
-        v[2 * c] = static_cast<real>(co);
-        v[2 * c + 1] = static_cast<real>(sn);
+        real sn = real(0), co = real(0);
+        if (real_row) phase_cis<real>(sd, (uint64_t)(r0 + r), (uint64_t)li, co, sn);
+        v[2 * c] = co;
+        v[2 * c + 1] = sn;
         acc[c] += (double)v[2 * c] * (double)v[2 * c] + (double)v[2 * c + 1] * (double)v[2 * c + 1];
       }
       st_stream<real, CPT>(v0 + (i * R + part * CPT) * 2, v);

@@ -25,6 +25,31 @@ __device__ __forceinline__ double phase_uniform(uint64_t seed, uint64_t r, uint6
   return static_cast<double>(z >> 11) * 0x1.0p-53;
 }
 
+// the same deviate truncated to its top 24 bits, exactly representable in
+// FP32 (for FP32 vectors: phase error below 2 pi 2^-24)
+__device__ __forceinline__ float phase_uniform24(uint64_t seed, uint64_t r, uint64_t i) {
+  const uint64_t z = splitmix64(seed ^ splitmix64((r << 32) + i));
+  return static_cast<float>(z >> 40) * 0x1.0p-24f;
+}
+
+// (cos, sin) of the random phase 2 pi u in the vector precision: FP64
+// sincos for FP64 vectors, FP32 sincospi of the 24-bit deviate for FP32
+// vectors (the FP64 pipe of GB300 is narrow)
+template <typename real>
+__device__ __forceinline__ void phase_cis(uint64_t seed, uint64_t r, uint64_t i, real &co, real &sn) {
+  if constexpr (sizeof(real) == 8) {
+    double s, c;
+    sincos(2.0 * M_PI * phase_uniform(seed, r, i), &s, &c);
+    co = c;
+    sn = s;
+  } else {
+    float s, c;
+    sincospif(2.0f * phase_uniform24(seed, r, i), &s, &c);
+    co = c;
+    sn = s;
+  }
+}
+
 // Each thread moves CPT complex numbers of one row: one 8-byte access
 // (FP32, CPT = 1) or CPT*8/16 (FP32) / CPT (FP64) 16-byte accesses.
 template <typename real, int CPT> struct Vec { using T = float4; static constexpr int kChunks = CPT / 2; };

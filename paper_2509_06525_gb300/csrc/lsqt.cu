@@ -198,10 +198,10 @@ __global__ void lsqt_phase_kernel(int64_t n, uint64_t seed, int64_t r0, real *__
   if (t >= n * R) return;
   const int64_t i = t / R;
   const int r = static_cast<int>(t % R);
-  double sn, co;
-  sincos(2.0 * M_PI * phase_uniform(seed, (uint64_t)(r0 + r), (uint64_t)i), &sn, &co);
-  phi[2 * t] = static_cast<real>(co);
-  phi[2 * t + 1] = static_cast<real>(sn);
+  real sn, co;
+  phase_cis<real>(seed, (uint64_t)(r0 + r), (uint64_t)i, co, sn);
+  phi[2 * t] = co;
+  phi[2 * t + 1] = sn;
 }
 
 // coef[j][n] = g_n (2 - delta_n0) mean_r mu[j][r][n]

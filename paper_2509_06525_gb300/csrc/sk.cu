@@ -214,9 +214,9 @@ __global__ void __launch_bounds__(kSkThreads) sk_phase_kernel(int64_t n, uint64_
                                                               float2 *__restrict__ v0, double *__restrict__ partial) {
   double acc = 0.0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * kNO; t += (int64_t)gridDim.x * blockDim.x) {
-    double sn, co;
-    sincos(2.0 * M_PI * phase_uniform(seed, (uint64_t)r0, (uint64_t)t), &sn, &co);
-    const float2 v = make_float2((float)co, (float)sn);
+    float sn, co;
+    phase_cis<float>(seed, (uint64_t)r0, (uint64_t)t, co, sn);
+    const float2 v = make_float2(co, sn);
     v0[t] = v;
     acc += (double)v.x * v.x + (double)v.y * v.y;
   }

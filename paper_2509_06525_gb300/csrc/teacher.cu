@@ -47,8 +47,7 @@ __global__ void teacher_kernel(const double *__restrict__ pos, const int32_t *__
     if (s < m) {
       const int32_t j = col[e];
       const int zj = min(max(species[j], 0), T.n_species - 1);
-      const double3 d = bond_vector(B, pos, i, j);
-      const double r2 = sq_norm(d);
+      const double r2 = bond_r2(B, pos, i, j);
       if (sizeof(valT) == 8) {
         const double r = sqrt(r2);
         const double env = 1.0 + T.gamma * ((double)(ni + ncount[j]) - 6.0) / 6.0;
