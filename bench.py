@@ -45,9 +45,9 @@ UNIT = "atom*moments/s"
 L2_BYTES = 126 * 1024 * 1024
 
 # DRAM bytes (read + write) of one launch of the timed step's Chebyshev kernel,
-# from full-size ncu captures of these exact configurations with the current
-# kernels (profiles/traffic_cheb_step_bench_workloads.md); any other
-# configuration, or a changed kernel, reports null.
+# from full-size ncu captures (dram__bytes_read.sum + dram__bytes_write.sum,
+# one launch of the timed step) of these exact configurations with the current
+# kernels; any other configuration, or a changed kernel, reports null.
 MEASURED_TRAFFIC = {
     ("graphene-10M-learned", "mlp", "doubling", 1024, 8): 2_897_906_176,
     ("graphene-100M", "teacher", "doubling", 1024, 1): 11_994_291_456,
