@@ -28,6 +28,10 @@ Modules and the passages they follow (arXiv 2509.06525):
                   autocorrelation conductivity of Eq. 3 (sigma), Sec. 2.4.
 * slater_koster -- the s, p, d Slater-Koster Hamiltonian (angular factors
                   of Sec. 3) by rotation of the bond-frame block.
+* env_bands    -- the environment network of Eq. 2, the SK-form pz hopping
+                  and onsite networks of Sec. 3, the Bloch sum H(k), bands
+                  by dense diagonalisation, the band loss of Eq. 3 and its
+                  Hellmann-Feynman gradient.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, dense diagonalisation, invariants, brute force, independent

@@ -247,6 +247,51 @@ def init_mlp(seed: int):
     return out
 
 
+
+# Shapes of the environment-network model, in the order of its flat
+# parameter vector (weights [out][in] row-major, then biases): environment
+# network 8-32-8, hopping network 8-32-32-2 (sigma, pi), onsite network 8-32-3.
+ENV_SHAPES = ((32, 8), (32,), (8, 32), (8,),
+              (32, 8), (32,), (32, 32), (32,), (2, 32), (2,),
+              (32, 8), (32,), (3, 32), (3,))
+ENV_NPARAM = sum(int(np.prod(s)) for s in ENV_SHAPES)
+
+
+def init_env_mlp(seed: int, bias_pi: float = 0.0) -> np.ndarray:
+    """He-uniform weights of the environment-network model as one flat
+    float32 vector (biases zero except the pi output's, set to bias_pi)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in ENV_SHAPES:
+        if len(s) == 2:
+            lim = math.sqrt(6.0 / s[1])
+            out.append(rng.uniform(-lim, lim, size=s).reshape(-1))
+        else:
+            out.append(np.zeros(s))
+    flat = np.concatenate(out).astype(np.float32)
+    # the pi output bias sits after Wh3 in the hopping network's block
+    off = sum(int(np.prod(s)) for s in ENV_SHAPES[:9]) + 1
+    flat[off] = bias_pi
+    return flat
+
+
+def band_kgrid(box: np.ndarray, n1: int, n2: int) -> np.ndarray:
+    """Shifted Monkhorst-Pack grid (k_z = 0) of an orthorhombic in-plane cell,
+    Cartesian k in 1/Angstrom, [n1 * n2, 3] float64."""
+    b1 = 2.0 * math.pi / box[0, 0]
+    b2 = 2.0 * math.pi / box[1, 1]
+    f1 = (np.arange(n1) + 0.5) / n1 - 0.5
+    f2 = (np.arange(n2) + 0.5) / n2 - 0.5
+    k1, k2 = np.meshgrid(f1, f2, indexing="ij")
+    return np.stack([k1.reshape(-1) * b1, k2.reshape(-1) * b2, np.zeros(n1 * n2)], axis=1)
+
+
+def band_training_cells(count: int, seed_base: int = 5000, nx: int = 2, ny: int = 3, sigma: float = 0.1):
+    """Periodic graphene cells of nx * ny rectangular 4-atom cells (24 atoms
+    at 2 x 3), displaced with sigma: the finite-temperature training cells
+    of the band-energy fit."""
+    return [graphene_rect(nx, ny, sigma, seed_base + s) for s in range(count)]
+
 # --------------------------------------------------------------------------
 # The five workloads (sizes and seeds).
 # --------------------------------------------------------------------------
