@@ -72,6 +72,8 @@ def parse_args():
     p.add_argument("--M", type=int, default=None, help="override the workload's moment count (profiling)")
     p.add_argument("--R", type=int, default=None, help="override the workload's vector count (profiling)")
     p.add_argument("--sk", type=int, default=1, help="measure the s, p, d Slater-Koster KPM (1) or skip it (0)")
+    p.add_argument("--env", type=int, default=600,
+                   help="environment-network model: band-training steps (0 skips the measurement)")
     p.add_argument("--batched", type=int, default=1,
                    help="measure the 64-snapshot h-BN/graphene junction batch in one graph (1) or skip it (0)")
     p.add_argument("--lsqt-steps", type=int, default=2,
@@ -299,6 +301,58 @@ def sk_measurement(pipe, torch, g):
     return out
 
 
+def env_measurement(pipe, torch, g, train_steps):
+    """The environment-network model (Eq. 2 edge feature, SK-form hopping and
+    onsite networks): its H on the workload's structure straight from the
+    positions (CUDA-event time after a warm-up call), then band-energy
+    training (Eq. 3) of a fresh model on 64 disordered 24-atom cells x 16
+    k-points against the teacher's bands, timed per step."""
+    from paper_2509_06525_gb300 import bands as bands_mod
+    s, nb = pipe.s, pipe.last["nb"]
+    cm = synth.descriptor_mixing("identity")
+    model = g.EnvModel(synth.init_env_mlp(11, -1.0), cm, np.zeros(3))
+    v = g.compute_descriptors(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model.cmix)
+    g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    H = g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_h = e0.elapsed_time(e1)
+    nnz = int(nb.cnt.sum().item())
+    # FMAs per bond: 8x32 + 32x8 (environment) + 8x32 + 32x32 + 32x2 (hopping); per atom 8x32 + 32
+    flops = 2 * (nnz * 1856 + s.n * 288)
+    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
+    h_out = {"atoms": s.n, "bonds": nnz, "ms": ms_h, "bonds_per_s": nnz / (ms_h * 1e-3),
+             "roofline": {"bound": "alu", "kernel": "env_forward_kernel (from positions)",
+                          "achieved": flops / (ms_h * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                          "frac": flops / (ms_h * 1e-3) / 1e12 / peak_alu,
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
+    del H, v
+    cells = synth.band_training_cells(64, 5000)
+    kpts = synth.band_kgrid(cells[0].box, 4, 4)
+    batch = bands_mod.build_cell_batch(cells, pipe.teacher, cm, kpts)
+    fresh = g.EnvModel(synth.init_env_mlp(12, -1.0), cm, np.zeros(3))
+    mae0 = bands_mod.band_mae(fresh, batch)
+    third = max(train_steps // 3, 1)
+    schedule = [(third, (8, 16)), (third, (4, 20)), (train_steps - 2 * third, (0, 24))]
+    torch.cuda.synchronize()
+    e0.record()
+    bands_mod.train_bands(fresh, batch, schedule, lr=3e-3, log_every=max(train_steps, 1))
+    e1.record()
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1)
+    mae1 = bands_mod.band_mae(fresh, batch)
+    spectra = len(cells) * len(kpts)
+    return {"hamiltonian": h_out,
+            "band_training": {"cells": len(cells), "atoms_per_cell": cells[0].n, "k_points": len(kpts),
+                              "steps": train_steps, "ms_per_step": ms_t / train_steps,
+                              "spectra_per_s": spectra * train_steps / (ms_t * 1e-3),
+                              "band_mae_ev": {"before": mae0, "after": mae1},
+                              "schedule": [[n_, list(w_)] for n_, w_ in schedule]}}
+
+
 def lsqt_measurement(pipe, n_steps, torch, g, dt=0.1):
     """VAC conductivity (Eq. 3 (sigma)) on the last step's Hamiltonian: x
     velocity, the workload's M and R, n_steps time steps of 0.1 fs; CUDA-event
@@ -467,6 +521,8 @@ def run_ours(args):
         out["sk"] = sk_measurement(pipe, torch, g)
     if args.batched:
         out["batched"] = batched_measurement(torch, g, rank)
+    if args.env > 0:
+        out["env_model"] = env_measurement(pipe, torch, g, args.env)
 
     # plain FP64 teacher form on the same structure and GPU, and the DOS
     # error of the timed (learned FP32 by default) path against it

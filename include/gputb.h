@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 5
+#define GPUTB_ABI_VERSION 6
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -67,6 +67,7 @@ typedef int32_t tb_status;
 #define TB_ERR_BOUNDS         6   /* |mu_n| > 1 + 1e-6: spectrum outside [-1,1] after rescaling */
 #define TB_ERR_NOT_FINITE     7   /* NaN/Inf met in an input or result       */
 #define TB_ERR_TIMEOUT        8   /* a bounded device-side wait gave up      */
+#define TB_ERR_NOT_CONVERGED  9   /* an iteration stopped at its sweep limit */
 
 /* precision of Hamiltonian values and KPM vectors */
 #define TB_F32 0
@@ -516,6 +517,110 @@ TB_API tb_status tb_build_hamiltonian(const double *positions, const int32_t *sp
                                       const float *params, const float *eps0, int32_t precision,
                                       void *val, void *diag, void *workspace, size_t workspace_bytes,
                                       void *stream);
+
+/* ====================================================================
+ * Environment network and band-energy training (Eq. 2 edge feature, the
+ * SK form H_ij = sum_lambda MLP_lambda(e_ij) P_lambda(r_ij_hat) and the
+ * onsite H_ii = MLP_alpha(v_i) of Sec. 3, the band loss of Eq. 3), for one
+ * pz orbital per atom:
+ *   u_ij = v_i + v_j   (= sum_{k in N(i)} C(r_ik) + sum_{l in N(j)} C(r_jl))
+ *   m = MLP_e(u): 8 -> 32 (SiLU) -> 8;  e_ij = C(r_ij) * m  (elementwise)
+ *   y = MLP_lambda(e): 8 -> 32 (SiLU) -> 32 (SiLU) -> 2  (sigma, pi)
+ *   t_ij = y_sigma n_z^2 + y_pi (1 - n_z^2),  n_z = d_z / r
+ *   eps_i = eps0[Z_i] + MLP_alpha(v_i)[Z_i]: 8 -> 32 (SiLU) -> 3
+ * SiLU(z) = z / (1 + e^{-z}).  The mixing c^{Z_i Z_j} must be symmetric in
+ * the species pair for H to be symmetric (u, r and n_z^2 are).
+ *
+ * Parameters: one device float vector [TB_ENV_NPARAM] in the order
+ *   We1 [32][8], be1 [32], We2 [8][32], be2 [8],
+ *   Wh1 [32][8], bh1 [32], Wh2 [32][32], bh2 [32], Wh3 [2][32], bh3 [2],
+ *   Wo1 [32][8], bo1 [32], Wo2 [3][32], bo2 [3]   (weights [out][in]).
+ * Bond inputs ("feat"): device float [total][TB_ENV_NFEAT] in SELL element
+ * order: C[8], u[8], n_z^2, d[3] (bond vector r_j + T - r_i, Angstrom).
+ * ==================================================================== */
+#define TB_ENV_NPARAM 2349
+#define TB_ENV_NFEAT 20
+
+/* Bond inputs of every real SELL element of one structure (v from
+ * tb_compute_descriptors with the same cmix); padding slots untouched.
+ * col may be NULL when no row has a neighbour. */
+TB_API tb_status tb_env_edge_inputs(const double *positions, const int32_t *species, int64_t n,
+                                    const double *box, const int32_t *pbc, double rcut,
+                                    const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                    const float *cmix, const float *v, float *feat, void *stream);
+
+/* H of the model from stored bond inputs: val (device, `precision`,
+ * SELL order, padding untouched) and, when diag is not NULL, diag [n]
+ * (then v [n][8], species and eps0 (device float [3]) are required). */
+TB_API tb_status tb_env_forward(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, const float *feat,
+                                const float *v, const int32_t *species, const float *params,
+                                const float *eps0, int32_t precision, void *val, void *diag,
+                                void *stream);
+
+/* The same H computed straight from positions (inference at any size: no
+ * stored bond inputs).  diag may be NULL; col may be NULL when no row has
+ * a neighbour. */
+TB_API tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,
+                                          const double *box, const int32_t *pbc, double rcut,
+                                          const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                          const float *cmix, const float *v, const float *params,
+                                          const float *eps0, int32_t precision, void *val, void *diag,
+                                          void *stream);
+
+/* Workspace bytes of tb_env_backward. */
+TB_API size_t tb_env_backward_workspace_size(int64_t n, int64_t total_elements);
+
+/* grad (device float [TB_ENV_NPARAM]) = dL/dparams from dL/dt per real
+ * element (g_val, SELL order) and dL/deps per row (g_diag [n]; rows that
+ * carry no atom must have g_diag = 0 and finite v).  The forward pass is
+ * recomputed; per-CTA partial sums are added in a fixed order. */
+TB_API tb_status tb_env_backward(int64_t n, const int64_t *slice_ptr, const int32_t *cnt,
+                                 int64_t total_elements, const float *feat, const float *v,
+                                 const int32_t *species, const float *params, const float *g_val,
+                                 const float *g_diag, float *grad, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
+/* Bands of a batch of periodic cells (Sec. 3: H(R) -> H(k) -> E_pre).
+ * Cell c owns SELL rows [c rows_per_cell, c rows_per_cell + n_atoms)
+ * (rows_per_cell a multiple of 32, n_atoms <= 64) and its neighbours must
+ * lie in those rows (TB_ERR_INVALID_ARG otherwise); at most 32 neighbours
+ * per row (TB_ERR_ELL_OVERFLOW).  Every stored neighbour adds
+ * t e^{i k.d} with d from feat; diag (device [rows], may be NULL) adds the
+ * onsite terms.  kpts: device float [n_k][3] (1/Angstrom, shared by all
+ * cells).  Output: evals (device float [n_cells][n_k][n_atoms], ascending)
+ * and evecs (device complex float [n_cells][n_k][n_atoms][n_atoms]:
+ * component a of band b at [a][b]).  Cyclic Jacobi in FP32 until the
+ * off-diagonal mass is below 1e-13 of the total (TB_ERR_NOT_CONVERGED after
+ * max_sweeps sweeps).  flags: device int32 [1] scratch.  Synchronises. */
+TB_API tb_status tb_bloch_bands(int32_t n_cells, int32_t n_atoms, int32_t rows_per_cell,
+                                const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                const float *feat, const float *val, const float *diag, int32_t n_k,
+                                const float *kpts, int32_t max_sweeps, float *evals, void *evecs,
+                                int32_t *flags, void *stream);
+
+/* Eq. 3 over n_spectra spectra of n_bands bands (device float arrays
+ * [n_spectra][n_bands]) with band weights w (device float [n_bands]):
+ *   D = E - E_ref, S = sum w_b |D|, L = S^2 + sum w_b D^2,
+ *   dLdE = 2 S w_b sign(D) + 2 w_b D  (sign(0) = 0);
+ * stats (device double [3]) = {S, sum w_b D^2, L}, sums in FP64. */
+TB_API tb_status tb_band_loss(int64_t n_spectra, int32_t n_bands, const float *evals, const float *e_ref,
+                              const float *weights, float *dLdE, double *stats, void *stream);
+
+/* Hellmann-Feynman gradients of the cells of tb_bloch_bands (same layout
+ * and evecs): g_val[e] = sum_k sum_b dLdE Re(conj(psi_b[i]) psi_b[j]
+ * e^{i k.d_e}) for every real element e = (i, j), g_diag[row] =
+ * sum_k sum_b dLdE |psi_b[i]|^2 (0 on rows without an atom).  Valid for
+ * non-degenerate bands. */
+TB_API tb_status tb_band_gradient(int32_t n_cells, int32_t n_atoms, int32_t rows_per_cell,
+                                  const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                  const float *feat, int32_t n_k, const float *kpts, const void *evecs,
+                                  const float *dLdE, float *g_val, float *g_diag, void *stream);
+
+/* AdamW step on a flat FP32 parameter vector of n entries (same update as
+ * tb_adamw_step, no BF16 copy). */
+TB_API tb_status tb_adamw_flat(int64_t n, float *params, const float *grad, float *m, float *v, int64_t step,
+                               double lr, double beta1, double beta2, double eps, double weight_decay,
+                               void *stream);
 
 #ifdef __cplusplus
 }

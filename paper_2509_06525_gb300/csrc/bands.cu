@@ -1,0 +1,898 @@
+// Environment-network model and band-energy training (Eq. 2 edge feature,
+// the SK form of the hopping and the onsite network of Sec. 3, the band loss
+// of Eq. 3):
+//
+//   u_ij = v_i + v_j,  m = MLP_e(u) (8-32-8),  e_ij = C(r_ij) * m,
+//   y = MLP_lambda(e) (8-32-32-2),  t_ij = y_sigma n_z^2 + y_pi (1 - n_z^2),
+//   eps_i = eps0[Z_i] + MLP_alpha(v_i)[Z_i] (8-32-3),
+//   H(k)_ij = sum over stored (i, j, d) of t e^{i k.d} + eps_i delta_ij,
+//   bands = eigenvalues of H(k),  L = (sum w_b |D|)^2 + sum w_b D^2.
+//
+// The networks are a few thousand FP32 operations per bond with widths of
+// 8 and 32, so they run on the FP32 pipes with the weights in shared memory
+// (a warp reads one weight at a time: broadcast).  Bloch matrices are at
+// most 64 x 64: one CTA builds H(k) in shared memory and diagonalises it by
+// cyclic Jacobi rotations in the round-robin order (n/2 disjoint rotations
+// per round, applied by all threads), so a whole batch of cells and k-points
+// is one launch with no host round trip.  Gradients: Hellmann-Feynman for
+// the bands, then the networks' backward pass with per-CTA partial sums
+// reduced in a fixed order (reproducible).
+#include <cmath>
+#include <cstddef>
+
+#include "common.cuh"
+#include "descriptor.cuh"
+#include "geometry.cuh"
+
+namespace gputb {
+namespace {
+
+// flat parameter layout (weights [out][in] row-major, then biases)
+constexpr int oWe1 = 0, obe1 = 256, oWe2 = 288, obe2 = 544;
+constexpr int oWh1 = 552, obh1 = 808, oWh2 = 840, obh2 = 1864, oWh3 = 1896, obh3 = 1960;
+constexpr int oWo1 = 1962, obo1 = 2218, oWo2 = 2250, obo2 = 2346;
+constexpr int kNP = TB_ENV_NPARAM;
+static_assert(obo2 + 3 == kNP, "parameter layout");
+constexpr int kNF = TB_ENV_NFEAT;  // C[8], u[8], n_z^2, d[3]
+constexpr int kMaxBand = 64;
+constexpr int kMaxCnt = 32;
+
+__device__ __forceinline__ float sig(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sig(z); }
+__device__ __forceinline__ float dsilu(float z) {
+  const float s = sig(z);
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ void stage_params(float *P, const float *__restrict__ params) {
+  for (int k = threadIdx.x; k < kNP; k += blockDim.x) P[k] = params[k];
+}
+
+// t_ij from the inputs of one bond (weights P in shared memory)
+__device__ float hop_forward(const float *P, const float (&C)[8], const float (&u)[8], float nz2) {
+  float h1[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obe1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(P[oWe1 + o * 8 + i], u[i], z);
+    h1[o] = silu(z);
+  }
+  float e[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float z = P[obe2 + o];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z = fmaf(P[oWe2 + o * 32 + i], h1[i], z);
+    e[o] = C[o] * z;
+  }
+  float h2[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obh1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(P[oWh1 + o * 8 + i], e[i], z);
+    h2[o] = silu(z);
+  }
+  float y0 = P[obh3], y1 = P[obh3 + 1];
+#pragma unroll 4
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obh2 + o];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z = fmaf(P[oWh2 + o * 32 + i], h2[i], z);
+    const float h3 = silu(z);
+    y0 = fmaf(P[oWh3 + o], h3, y0);
+    y1 = fmaf(P[oWh3 + 32 + o], h3, y1);
+  }
+  return y0 * nz2 + y1 * (1.0f - nz2);
+}
+
+// MLP_alpha(v_i)[Z_i]
+__device__ float onsite_forward(const float *P, const float (&v)[8], int z) {
+  float out = P[obo2 + z];
+#pragma unroll 4
+  for (int o = 0; o < 32; ++o) {
+    float s = P[obo1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s = fmaf(P[oWo1 + o * 8 + i], v[i], s);
+    out = fmaf(P[oWo2 + z * 32 + o], silu(s), out);
+  }
+  return out;
+}
+
+__device__ __forceinline__ void load8(const float *__restrict__ p, float (&x)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+
+// inputs of bond (i, j): C(r_ij) (species-pair mixing), u = v_i + v_j,
+// n_z^2 = (d_z / r)^2 and the bond vector d = r_j + T - r_i (FP32)
+__device__ __forceinline__ void bond_inputs(const double *__restrict__ pos, const int32_t *__restrict__ species,
+                                            const Box &B, float rcut, const float *sc,
+                                            const float *__restrict__ v, int64_t i, int32_t j, float (&C)[8],
+                                            float (&u)[8], float &nz2, float3 &d) {
+  const int zi = min(max(species[i], 0), 2), zj = min(max(species[j], 0), 2);
+  const float r = bond_length_f32(B, pos, i, j);
+  bond_descriptor(r, rcut, sc + (zi * 3 + zj) * 64, C);
+  float vi[8], vj[8];
+  load8(v + i * 8, vi);
+  load8(v + (int64_t)j * 8, vj);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) u[k] = vi[k] + vj[k];
+  const double3 dd = bond_vector(B, pos, i, j);
+  const double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
+  nz2 = r2 > 0.0 ? (float)(dd.z * dd.z / r2) : 0.0f;
+  d = make_float3((float)dd.x, (float)dd.y, (float)dd.z);
+}
+
+__global__ void env_inputs_kernel(const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n,
+                                  Box B, float rcut, const int64_t *__restrict__ slice_ptr,
+                                  const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
+                                  const float *__restrict__ cmix, const float *__restrict__ v,
+                                  float *__restrict__ feat) {
+  __shared__ float sc[9 * 64];
+  load_mixing(sc, cmix);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e0 = slice_ptr[i >> 5] + (i & 31);
+  const int m = cnt[i];
+  for (int s = 0; s < m; ++s) {
+    const int64_t e = e0 + 32 * s;
+    float C[8], u[8], nz2;
+    float3 d;
+    bond_inputs(pos, species, B, rcut, sc, v, i, col[e], C, u, nz2, d);
+    float *f = feat + e * kNF;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      f[k] = C[k];
+      f[8 + k] = u[k];
+    }
+    f[16] = nz2;
+    f[17] = d.x;
+    f[18] = d.y;
+    f[19] = d.z;
+  }
+}
+
+// H from stored inputs (training) or from positions (inference), one thread
+// per row; padding slots are left untouched
+template <typename valT, bool FROM_POS>
+__global__ void __launch_bounds__(128) env_forward_kernel(
+    int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ cnt,
+    const float *__restrict__ feat, const double *__restrict__ pos, const int32_t *__restrict__ species, Box B,
+    float rcut, const int32_t *__restrict__ col, const float *__restrict__ cmix, const float *__restrict__ v,
+    const float *__restrict__ params, const float *__restrict__ eps0, valT *__restrict__ val,
+    valT *__restrict__ diag) {
+  __shared__ float P[kNP];
+  __shared__ float sc[9 * 64];
+  stage_params(P, params);
+  if (FROM_POS) load_mixing(sc, cmix);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = slice_ptr[i >> 5] + (i & 31);
+    const int m = cnt[i];
+    for (int s = 0; s < m; ++s) {
+      const int64_t e = e0 + 32 * s;
+      float C[8], u[8], nz2;
+      if (FROM_POS) {
+        float3 d;
+        bond_inputs(pos, species, B, rcut, sc, v, i, col[e], C, u, nz2, d);
+      } else {
+        load8(feat + e * kNF, C);
+        load8(feat + e * kNF + 8, u);
+        nz2 = feat[e * kNF + 16];
+      }
+      val[e] = (valT)hop_forward(P, C, u, nz2);
+    }
+    if (diag) {
+      float vi[8];
+      load8(v + i * 8, vi);
+      const int z = min(max(species[i], 0), 2);
+      diag[i] = (valT)(eps0[z] + onsite_forward(P, vi, z));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ backward
+//
+// A CTA of 64 threads takes tiles of 64 items (SELL slots, or rows for the
+// onsite network).  Phase 1: each thread runs its item's forward and
+// backward pass and leaves, in its shared-memory row, every layer's input
+// and output delta (a constant-1 slot serves the biases).  Phase 2: thread t
+// owns parameters t, t + 64, ... and adds sum over the tile of delta[o] *
+// input[i] into registers.  Rows have an odd stride (no bank conflicts).
+constexpr int kBT = 64;
+constexpr int kRow = 221;
+constexpr int kOwn = (kNP + kBT - 1) / kBT;  // 37
+// edge item row: u | dz1 | h1 | dm | e | dz2 | h2 | dz3 | h3 | dy | 1 | 0
+constexpr int sU = 0, sDZ1 = 8, sH1 = 40, sDM = 72, sE = 80, sDZ2 = 88, sH2 = 120, sDZ3 = 152, sH3 = 184,
+              sDY = 216, sOne = 218, sZero = 219;
+// onsite item row: v | dz | h | dout
+constexpr int rV = 0, rDZ = 8, rH = 40, rDO = 72;
+
+// shared-memory slots of parameter p for an item kind: input slot and delta
+// slot; delta = sZero when the item kind does not touch p
+__device__ __forceinline__ void param_slots(int p, bool rows, int &in, int &dl) {
+  in = sOne;
+  dl = sZero;
+  if (!rows) {
+    if (p < obe1) { dl = sDZ1 + (p - oWe1) / 8; in = sU + (p - oWe1) % 8; }
+    else if (p < oWe2) { dl = sDZ1 + (p - obe1); }
+    else if (p < obe2) { dl = sDM + (p - oWe2) / 32; in = sH1 + (p - oWe2) % 32; }
+    else if (p < oWh1) { dl = sDM + (p - obe2); }
+    else if (p < obh1) { dl = sDZ2 + (p - oWh1) / 8; in = sE + (p - oWh1) % 8; }
+    else if (p < oWh2) { dl = sDZ2 + (p - obh1); }
+    else if (p < obh2) { dl = sDZ3 + (p - oWh2) / 32; in = sH2 + (p - oWh2) % 32; }
+    else if (p < oWh3) { dl = sDZ3 + (p - obh2); }
+    else if (p < obh3) { dl = sDY + (p - oWh3) / 32; in = sH3 + (p - oWh3) % 32; }
+    else if (p < oWo1) { dl = sDY + (p - obh3); }
+  } else {
+    if (p < oWo1) return;
+    if (p < obo1) { dl = rDZ + (p - oWo1) / 8; in = rV + (p - oWo1) % 8; }
+    else if (p < oWo2) { dl = rDZ + (p - obo1); }
+    else if (p < obo2) { dl = rDO + (p - oWo2) / 32; in = rH + (p - oWo2) % 32; }
+    else { dl = rDO + (p - obo2); }
+  }
+}
+
+// forward + backward of one bond, activations and deltas into row R
+__device__ void hop_backward_item(const float *P, float *R, const float (&C)[8], const float (&u)[8], float nz2,
+                                  float g) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) R[sU + k] = u[k];
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obe1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(P[oWe1 + o * 8 + i], u[i], z);
+    R[sH1 + o] = silu(z);
+    R[sDZ1 + o] = dsilu(z);  // multiplier, becomes dz1 below
+  }
+  for (int o = 0; o < 8; ++o) {
+    float z = P[obe2 + o];
+    for (int i = 0; i < 32; ++i) z = fmaf(P[oWe2 + o * 32 + i], R[sH1 + i], z);
+    R[sE + o] = C[o] * z;
+  }
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obh1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(P[oWh1 + o * 8 + i], R[sE + i], z);
+    R[sH2 + o] = silu(z);
+    R[sDZ2 + o] = dsilu(z);
+  }
+  for (int o = 0; o < 32; ++o) {
+    float z = P[obh2 + o];
+    for (int i = 0; i < 32; ++i) z = fmaf(P[oWh2 + o * 32 + i], R[sH2 + i], z);
+    R[sH3 + o] = silu(z);
+    R[sDZ3 + o] = dsilu(z);
+  }
+  // backward
+  const float dy0 = g * nz2, dy1 = g * (1.0f - nz2);
+  R[sDY] = dy0;
+  R[sDY + 1] = dy1;
+  for (int i = 0; i < 32; ++i)
+    R[sDZ3 + i] *= fmaf(P[oWh3 + i], dy0, P[oWh3 + 32 + i] * dy1);
+  for (int i = 0; i < 32; ++i) {
+    float s = 0.0f;
+    for (int o = 0; o < 32; ++o) s = fmaf(P[oWh2 + o * 32 + i], R[sDZ3 + o], s);
+    R[sDZ2 + i] *= s;
+  }
+  for (int i = 0; i < 8; ++i) {
+    float s = 0.0f;
+    for (int o = 0; o < 32; ++o) s = fmaf(P[oWh1 + o * 8 + i], R[sDZ2 + o], s);
+    R[sDM + i] = s * C[i];
+  }
+  for (int i = 0; i < 32; ++i) {
+    float s = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) s = fmaf(P[oWe2 + o * 32 + i], R[sDM + o], s);
+    R[sDZ1 + i] *= s;
+  }
+}
+
+__device__ void onsite_backward_item(const float *P, float *R, const float (&v)[8], int z, float g) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) R[rV + k] = v[k];
+  for (int o = 0; o < 32; ++o) {
+    float s = P[obo1 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s = fmaf(P[oWo1 + o * 8 + i], v[i], s);
+    R[rH + o] = silu(s);
+    R[rDZ + o] = dsilu(s) * P[oWo2 + z * 32 + o] * g;
+  }
+  for (int a = 0; a < 3; ++a) R[rDO + a] = a == z ? g : 0.0f;
+}
+
+template <bool ROWS>
+__global__ void __launch_bounds__(kBT) env_backward_kernel(
+    int64_t n, int64_t n_slices, int64_t total, const int64_t *__restrict__ slice_ptr,
+    const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ v,
+    const int32_t *__restrict__ species, const float *__restrict__ params, const float *__restrict__ g_val,
+    const float *__restrict__ g_diag, float *__restrict__ partial) {
+  extern __shared__ float smem[];
+  float *P = smem;
+  float *rows = smem + kNP;
+  stage_params(P, params);
+  float *R = rows + threadIdx.x * kRow;
+  R[sOne] = 1.0f;
+  R[sZero] = 0.0f;
+  float acc[kOwn];
+#pragma unroll
+  for (int m = 0; m < kOwn; ++m) acc[m] = 0.0f;
+  const int64_t items = ROWS ? n : total;
+  const int64_t tiles = (items + kBT - 1) / kBT;
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t it = tile * kBT + threadIdx.x;
+    if (ROWS) {
+      float vi[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      float g = 0.0f;
+      int z = 0;
+      if (it < n) {
+        g = g_diag[it];
+        load8(v + it * 8, vi);
+        z = min(max(species[it], 0), 2);
+      }
+      onsite_backward_item(P, R, vi, z, g);
+    } else {
+      // locate the slot's slice, row and position in the row
+      float C[8] = {0, 0, 0, 0, 0, 0, 0, 0}, u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      float nz2 = 0.0f, g = 0.0f;
+      if (it < total) {
+        int64_t lo = 0, hi = n_slices - 1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) >> 1;
+          if (slice_ptr[mid] <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        const int64_t off = it - slice_ptr[lo];
+        const int64_t row = lo * 32 + (off & 31);
+        const int s = (int)(off >> 5);
+        if (row < n && s < cnt[row]) {
+          load8(feat + it * kNF, C);
+          load8(feat + it * kNF + 8, u);
+          nz2 = feat[it * kNF + 16];
+          g = g_val[it];
+        }
+      }
+      hop_backward_item(P, R, C, u, nz2, g);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kOwn; ++m) {
+      const int p = threadIdx.x + kBT * m;
+      if (p >= kNP) break;
+      int in, dl;
+      param_slots(p, ROWS, in, dl);
+      if (dl == sZero) continue;
+      float s = 0.0f;
+      for (int k = 0; k < kBT; ++k) s = fmaf(rows[k * kRow + dl], rows[k * kRow + in], s);
+      acc[m] += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < kOwn; ++m) {
+    const int p = threadIdx.x + kBT * m;
+    if (p < kNP) partial[(int64_t)blockIdx.x * kNP + p] = acc[m];
+  }
+}
+
+__global__ void partial_sum_kernel(const float *__restrict__ partial, int nblocks, float *__restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= kNP) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += (double)partial[(int64_t)b * kNP + p];
+  grad[p] = (float)s;
+}
+
+// ------------------------------------------------------------------ Bloch bands
+
+// H(k) of cell c into A (row stride ld); error bits: 1 = a neighbour outside
+// the cell's rows, 4 = a row with more than kMaxCnt neighbours
+__device__ int build_bloch(float2 *A, int ld, int n, int c, int rows_per_cell, const int64_t *__restrict__ slice_ptr,
+                           const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
+                           const float *__restrict__ feat, const float *__restrict__ val,
+                           const float *__restrict__ diag, float3 k) {
+  int err = 0;
+  for (int idx = threadIdx.x; idx < n * ld; idx += blockDim.x) A[idx] = make_float2(0.0f, 0.0f);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t row = (int64_t)c * rows_per_cell + i;
+    const int64_t e0 = slice_ptr[row >> 5] + (row & 31);
+    const int m = cnt[row];
+    if (m > kMaxCnt) err |= 4;
+    for (int s = 0; s < m; ++s) {
+      const int64_t e = e0 + 32 * s;
+      const int64_t j = (int64_t)col[e] - (int64_t)c * rows_per_cell;
+      if (j < 0 || j >= n) {
+        err |= 1;
+        continue;
+      }
+      const float *f = feat + e * kNF;
+      float sn, cs;
+      sincosf(k.x * f[17] + k.y * f[18] + k.z * f[19], &sn, &cs);
+      const float t = val[e];
+      float2 &a = A[i * ld + j];
+      a.x = fmaf(t, cs, a.x);
+      a.y = fmaf(t, sn, a.y);
+    }
+    if (diag) A[i * ld + i].x += diag[row];
+  }
+  __syncthreads();
+  return err;
+}
+
+// one CTA per (k-point, cell): Bloch matrix, cyclic Jacobi, sorted output
+__global__ void __launch_bounds__(256) bloch_eigh_kernel(
+    int n, int rows_per_cell, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ val,
+    const float *__restrict__ diag, int n_k, const float *__restrict__ kpts, int max_sweeps,
+    float *__restrict__ evals, float2 *__restrict__ evecs, int *__restrict__ flags) {
+  extern __shared__ float2 sh[];
+  const int ld = n + 1;
+  float2 *A = sh;
+  float2 *V = A + n * ld;
+  float4 *rot = reinterpret_cast<float4 *>(V + n * ld);  // c, s, cos(phi), sin(phi) per pair
+  float2 *newdiag = reinterpret_cast<float2 *>(rot + kMaxBand / 2);
+  float *red = reinterpret_cast<float *>(newdiag + kMaxBand / 2);  // [2][8]
+  const int q = blockIdx.x, c = blockIdx.y;
+  const float3 k = make_float3(kpts[3 * q], kpts[3 * q + 1], kpts[3 * q + 2]);
+  const int err = build_bloch(A, ld, n, c, rows_per_cell, slice_ptr, col, cnt, feat, val, diag, k);
+  if (err) atomicOr(flags, err);
+  for (int idx = threadIdx.x; idx < n * ld; idx += blockDim.x) {
+    const int i = idx / ld, j = idx % ld;
+    V[idx] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+  }
+  // the diagonal of a Hermitian matrix is real
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * ld + i].y = 0.0f;
+  __syncthreads();
+
+  const int m = (n + 1) & ~1;  // players, with one idle slot when n is odd
+  const int half = m / 2;
+  bool converged = false;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    for (int round = 0; round < m - 1; ++round) {
+      // pair p of this round: positions p and m-1-p of the rotated circle
+      if (threadIdx.x < half) {
+        const int pp = threadIdx.x;
+        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
+        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        float4 r = make_float4(1.0f, 0.0f, 1.0f, 0.0f);
+        float2 dg = make_float2(0.0f, 0.0f);
+        if (b < n) {
+          const float2 h = A[a * ld + b];
+          const float ah = hypotf(h.x, h.y);
+          const float app = A[a * ld + a].x, aqq = A[b * ld + b].x;
+          dg = make_float2(app, aqq);
+          if (ah > 0.0f) {
+            const float tau = (aqq - app) / (2.0f * ah);
+            const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            // correctly rounded square root and divide: the rotation stays
+            // orthogonal to rounding (no drift of the norms over the sweeps)
+            const float cth = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+            r = make_float4(cth, t * cth, h.x / ah, h.y / ah);
+            // rotated diagonal in closed form (Rutishauser)
+            dg = make_float2(app - t * ah, aqq + t * ah);
+          }
+        }
+        rot[pp] = r;
+        newdiag[pp] = dg;
+      }
+      __syncthreads();
+      // rows: A <- U^H A  (new_p = c A_p - s e^{i phi} A_q, new_q = s A_p + c e^{i phi} A_q)
+      for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
+        const int pp = idx / n, j = idx % n;
+        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
+        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= n) continue;
+        const float4 r = rot[pp];
+        const float2 x = A[a * ld + j], y = A[b * ld + j];
+        // e^{i phi} y
+        const float2 ey = make_float2(r.z * y.x - r.w * y.y, r.z * y.y + r.w * y.x);
+        A[a * ld + j] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
+        A[b * ld + j] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
+      }
+      __syncthreads();
+      // columns: A <- A U and V <- V U  (new col p = c A_p - s e^{-i phi} A_q,
+      // new col q = s A_p + c e^{-i phi} A_q)
+      for (int idx = threadIdx.x; idx < 2 * half * n; idx += blockDim.x) {
+        const int which = idx / (half * n);
+        const int rem = idx % (half * n);
+        const int pp = rem / n, i = rem % n;
+        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
+        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= n) continue;
+        const float4 r = rot[pp];
+        float2 *M = which ? V : A;
+        const float2 x = M[i * ld + a], y = M[i * ld + b];
+        // e^{-i phi} y
+        const float2 ey = make_float2(r.z * y.x + r.w * y.y, r.z * y.y - r.w * y.x);
+        M[i * ld + a] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
+        M[i * ld + b] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
+      }
+      __syncthreads();
+      // the rotated 2 x 2 block is diagonal and real up to rounding
+      if (threadIdx.x < half) {
+        const int pp = threadIdx.x;
+        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
+        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b < n && rot[pp].y != 0.0f) {
+          A[a * ld + b] = make_float2(0.0f, 0.0f);
+          A[b * ld + a] = make_float2(0.0f, 0.0f);
+          A[a * ld + a] = make_float2(newdiag[pp].x, 0.0f);
+          A[b * ld + b] = make_float2(newdiag[pp].y, 0.0f);
+        }
+      }
+      __syncthreads();
+    }
+    // off-diagonal mass against the total
+    float off = 0.0f, tot = 0.0f;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      const float2 a = A[i * ld + j];
+      const float s = a.x * a.x + a.y * a.y;
+      tot += s;
+      if (i != j) off += s;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = off;
+      red[8 + (threadIdx.x >> 5)] = tot;
+    }
+    __syncthreads();
+    float so = 0.0f, st = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      so += red[w];
+      st += red[8 + w];
+    }
+    converged = so <= 1e-13f * st;
+    __syncthreads();
+  }
+  if (!converged && threadIdx.x == 0) atomicOr(flags, 2);
+  // ascending order: rank of each diagonal entry (ties by index)
+  const int64_t base = ((int64_t)c * n_k + q) * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float li = A[i * ld + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float lj = A[j * ld + j].x;
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    evals[base + rank] = li;
+    for (int a = 0; a < n; ++a) evecs[(base + a) * n + rank] = V[a * ld + i];
+  }
+}
+
+// Eq. 3 over all (cell, k, band) items: stats = {S, sum w D^2, L}
+__global__ void __launch_bounds__(1024) band_loss_kernel(int64_t items, int nb, const float *__restrict__ E,
+                                                         const float *__restrict__ Eref,
+                                                         const float *__restrict__ w, float *__restrict__ dLdE,
+                                                         double *__restrict__ stats) {
+  __shared__ double red[2][32];
+  __shared__ double S_all;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t x = threadIdx.x; x < items; x += blockDim.x) {
+    const double d = (double)E[x] - (double)Eref[x];
+    const double wb = (double)w[x % nb];
+    s1 += wb * fabs(d);
+    s2 += wb * d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    S_all = a;
+    stats[0] = a;
+    stats[1] = b;
+    stats[2] = a * a + b;
+  }
+  __syncthreads();
+  const double S = S_all;
+  for (int64_t x = threadIdx.x; x < items; x += blockDim.x) {
+    const double d = (double)E[x] - (double)Eref[x];
+    const double wb = (double)w[x % nb];
+    const double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
+    dLdE[x] = (float)(2.0 * S * wb * sg + 2.0 * wb * d);
+  }
+}
+
+// Hellmann-Feynman: dL/dt_e = sum_k sum_b g_b Re(conj(psi_b[i]) psi_b[j] e^{i k.d_e}),
+// dL/deps_i = sum_k sum_b g_b |psi_b[i]|^2; one CTA per cell, k-points in turn
+constexpr int kGradItems = kMaxBand * kMaxCnt / 256;  // slots per thread
+__global__ void __launch_bounds__(256) band_gradient_kernel(
+    int n, int rows_per_cell, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const int32_t *__restrict__ cnt, const float *__restrict__ feat, int n_k, const float *__restrict__ kpts,
+    const float2 *__restrict__ evecs, const float *__restrict__ dLdE, float *__restrict__ g_val,
+    float *__restrict__ g_diag) {
+  extern __shared__ float2 sh[];
+  const int ld = n + 1;
+  float2 *Psi = sh;
+  float *g = reinterpret_cast<float *>(Psi + n * ld);
+  const int c = blockIdx.x;
+  float acc[kGradItems];
+#pragma unroll
+  for (int m = 0; m < kGradItems; ++m) acc[m] = 0.0f;
+  float acc_eps = 0.0f;
+  for (int q = 0; q < n_k; ++q) {
+    const int64_t base = ((int64_t)c * n_k + q) * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Psi[(idx / n) * ld + idx % n] = evecs[base * n + idx];
+    for (int b = threadIdx.x; b < n; b += blockDim.x) g[b] = dLdE[base + b];
+    __syncthreads();
+    const float kx = kpts[3 * q], ky = kpts[3 * q + 1], kz = kpts[3 * q + 2];
+#pragma unroll
+    for (int m = 0; m < kGradItems; ++m) {
+      const int item = threadIdx.x + 256 * m;
+      const int i = item / kMaxCnt, s = item % kMaxCnt;
+      if (i >= n) continue;
+      const int64_t row = (int64_t)c * rows_per_cell + i;
+      if (s >= cnt[row]) continue;
+      const int64_t e = slice_ptr[row >> 5] + (row & 31) + 32 * s;
+      const int64_t j = (int64_t)col[e] - (int64_t)c * rows_per_cell;
+      if (j < 0 || j >= n) continue;
+      float zr = 0.0f, zi = 0.0f;
+      for (int b = 0; b < n; ++b) {
+        const float2 pi = Psi[i * ld + b], pj = Psi[j * ld + b];
+        // conj(pi) pj
+        zr = fmaf(g[b], pi.x * pj.x + pi.y * pj.y, zr);
+        zi = fmaf(g[b], pi.x * pj.y - pi.y * pj.x, zi);
+      }
+      const float *f = feat + e * kNF;
+      float sn, cs;
+      sincosf(kx * f[17] + ky * f[18] + kz * f[19], &sn, &cs);
+      acc[m] += zr * cs - zi * sn;
+    }
+    if (threadIdx.x < n) {
+      const int i = threadIdx.x;
+      float s = 0.0f;
+      for (int b = 0; b < n; ++b) {
+        const float2 p = Psi[i * ld + b];
+        s = fmaf(g[b], p.x * p.x + p.y * p.y, s);
+      }
+      acc_eps += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < kGradItems; ++m) {
+    const int item = threadIdx.x + 256 * m;
+    const int i = item / kMaxCnt, s = item % kMaxCnt;
+    if (i >= n) continue;
+    const int64_t row = (int64_t)c * rows_per_cell + i;
+    if (s >= cnt[row]) continue;
+    g_val[slice_ptr[row >> 5] + (row & 31) + 32 * s] = acc[m];
+  }
+  for (int i = threadIdx.x; i < rows_per_cell; i += blockDim.x)
+    g_diag[(int64_t)c * rows_per_cell + i] = i < n ? acc_eps : 0.0f;
+}
+
+__global__ void adamw_flat_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                                  float *__restrict__ v, float lr, float b1, float b2, float eps, float wd, float c1,
+                                  float c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+  const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] * (1.0f - lr * wd);
+  p[i] = pi - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+size_t eigh_smem(int n) {
+  return (size_t)2 * n * (n + 1) * sizeof(float2) + kMaxBand / 2 * (sizeof(float4) + sizeof(float2)) + 16 * 4;
+}
+size_t grad_smem(int n) { return (size_t)n * (n + 1) * sizeof(float2) + n * sizeof(float); }
+int backward_grid(int64_t items) {
+  const int64_t tiles = (items + kBT - 1) / kBT;
+  const int64_t g = (int64_t)sm_count() * 3;
+  return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
+}
+constexpr size_t kBackSmem = (size_t)(kNP + kBT * kRow) * sizeof(float);
+
+tb_status check_sell(int64_t n, const int64_t *slice_ptr, const int32_t *cnt) {
+  TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "bad row count");
+  TB_REQUIRE(slice_ptr && cnt, "slice_ptr and cnt are required");
+  return TB_OK;
+}
+
+}  // namespace
+}  // namespace gputb
+
+using namespace gputb;
+
+extern "C" tb_status tb_env_edge_inputs(const double *positions, const int32_t *species, int64_t n,
+                                        const double *box, const int32_t *pbc, double rcut,
+                                        const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                        const float *cmix, const float *v, float *feat, void *stream) {
+  tb_status s = check_sell(n, slice_ptr, cnt);
+  if (s != TB_OK) return s;
+  TB_REQUIRE(positions && species && cmix && v && feat, "tb_env_edge_inputs: null pointer");
+  Box B;
+  s = make_box(box, pbc, rcut, &B);
+  if (s != TB_OK) return s;
+  env_inputs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      positions, species, n, B, (float)rcut, slice_ptr, col, cnt, cmix, v, feat);
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}
+
+namespace {
+template <typename valT, bool FROM_POS>
+tb_status launch_env_forward(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, const float *feat,
+                             const double *pos, const int32_t *species, const Box &B, float rcut,
+                             const int32_t *col, const float *cmix, const float *v, const float *params,
+                             const float *eps0, void *val, void *diag, cudaStream_t st) {
+  const int64_t want = (n + 127) / 128;
+  const int64_t cap = (int64_t)sm_count() * 16;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  env_forward_kernel<valT, FROM_POS><<<grid, 128, 0, st>>>(n, slice_ptr, cnt, feat, pos, species, B, rcut, col,
+                                                          cmix, v, params, eps0, static_cast<valT *>(val),
+                                                          static_cast<valT *>(diag));
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}
+}  // namespace
+
+extern "C" tb_status tb_env_forward(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, const float *feat,
+                                    const float *v, const int32_t *species, const float *params, const float *eps0,
+                                    int32_t precision, void *val, void *diag, void *stream) {
+  tb_status s = check_sell(n, slice_ptr, cnt);
+  if (s != TB_OK) return s;
+  TB_REQUIRE(feat && params && val, "tb_env_forward: null pointer");
+  TB_REQUIRE(!diag || (v && species && eps0), "tb_env_forward: diag needs v, species and eps0");
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_env_forward: bad precision");
+  Box B{};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == TB_F32)
+    return launch_env_forward<float, false>(n, slice_ptr, cnt, feat, nullptr, species, B, 0.0f, nullptr, nullptr, v,
+                                            params, eps0, val, diag, st);
+  return launch_env_forward<double, false>(n, slice_ptr, cnt, feat, nullptr, species, B, 0.0f, nullptr, nullptr, v,
+                                           params, eps0, val, diag, st);
+}
+
+extern "C" tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,
+                                              const double *box, const int32_t *pbc, double rcut,
+                                              const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                              const float *cmix, const float *v, const float *params,
+                                              const float *eps0, int32_t precision, void *val, void *diag,
+                                              void *stream) {
+  tb_status s = check_sell(n, slice_ptr, cnt);
+  if (s != TB_OK) return s;
+  TB_REQUIRE(positions && species && cmix && v && params && eps0 && val,
+             "tb_build_hamiltonian_env: null pointer");
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian_env: bad precision");
+  Box B;
+  s = make_box(box, pbc, rcut, &B);
+  if (s != TB_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == TB_F32)
+    return launch_env_forward<float, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col, cmix,
+                                           v, params, eps0, val, diag, st);
+  return launch_env_forward<double, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col, cmix,
+                                          v, params, eps0, val, diag, st);
+}
+
+extern "C" size_t tb_env_backward_workspace_size(int64_t n, int64_t total_elements) {
+  if (n < 0 || total_elements < 0) return 0;
+  return (size_t)(backward_grid(total_elements) + backward_grid(n)) * kNP * sizeof(float) + 256;
+}
+
+extern "C" tb_status tb_env_backward(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, int64_t total_elements,
+                                     const float *feat, const float *v, const int32_t *species, const float *params,
+                                     const float *g_val, const float *g_diag, float *grad, void *workspace,
+                                     size_t workspace_bytes, void *stream) {
+  tb_status s = check_sell(n, slice_ptr, cnt);
+  if (s != TB_OK) return s;
+  TB_REQUIRE(total_elements >= 1 && feat && v && species && params && g_val && g_diag && grad && workspace,
+             "tb_env_backward: bad argument");
+  if (workspace_bytes < tb_env_backward_workspace_size(n, total_elements))
+    return fail(TB_ERR_WORKSPACE, "tb_env_backward: workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ge = backward_grid(total_elements), gr = backward_grid(n);
+  float *partial = static_cast<float *>(workspace);
+  const int64_t n_slices = (n + 31) / 32;
+  TB_CUDA(cudaFuncSetAttribute(env_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kBackSmem));
+  TB_CUDA(cudaFuncSetAttribute(env_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kBackSmem));
+  env_backward_kernel<false><<<ge, kBT, kBackSmem, st>>>(n, n_slices, total_elements, slice_ptr, cnt, feat, v,
+                                                         species, params, g_val, g_diag, partial);
+  TB_CHECK_LAUNCH();
+  env_backward_kernel<true><<<gr, kBT, kBackSmem, st>>>(n, n_slices, total_elements, slice_ptr, cnt, feat, v,
+                                                        species, params, g_val, g_diag,
+                                                        partial + (int64_t)ge * kNP);
+  TB_CHECK_LAUNCH();
+  partial_sum_kernel<<<(kNP + 255) / 256, 256, 0, st>>>(partial, ge + gr, grad);
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}
+
+extern "C" tb_status tb_bloch_bands(int32_t n_cells, int32_t n_atoms, int32_t rows_per_cell,
+                                    const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                    const float *feat, const float *val, const float *diag, int32_t n_k,
+                                    const float *kpts, int32_t max_sweeps, float *evals, void *evecs,
+                                    int32_t *flags, void *stream) {
+  TB_REQUIRE(n_cells >= 1 && n_k >= 1 && n_k <= 65535 && n_cells <= 65535, "tb_bloch_bands: bad batch size");
+  TB_REQUIRE(n_atoms >= 1 && n_atoms <= kMaxBand, "tb_bloch_bands: n_atoms must be 1..64");
+  TB_REQUIRE(rows_per_cell >= n_atoms && rows_per_cell % 32 == 0, "tb_bloch_bands: rows_per_cell must be a multiple of 32 >= n_atoms");
+  TB_REQUIRE(max_sweeps >= 1 && max_sweeps <= 100, "tb_bloch_bands: max_sweeps must be 1..100");
+  TB_REQUIRE(slice_ptr && col && cnt && feat && val && kpts && evals && evecs && flags,
+             "tb_bloch_bands: null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = eigh_smem(n_atoms);
+  TB_CUDA(cudaFuncSetAttribute(bloch_eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t), st));
+  bloch_eigh_kernel<<<dim3(n_k, n_cells), 256, smem, st>>>(n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, val,
+                                                          diag, n_k, kpts, max_sweeps, evals,
+                                                          static_cast<float2 *>(evecs), flags);
+  TB_CHECK_LAUNCH();
+  int32_t h = 0;
+  TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  if (h & 1) return fail(TB_ERR_INVALID_ARG, "tb_bloch_bands: a neighbour lies outside its cell's rows");
+  if (h & 4) return fail(TB_ERR_ELL_OVERFLOW, "tb_bloch_bands: a row has more than 32 neighbours");
+  if (h & 2) return fail(TB_ERR_NOT_CONVERGED, "tb_bloch_bands: Jacobi rotations did not converge in max_sweeps");
+  return TB_OK;
+}
+
+extern "C" tb_status tb_band_loss(int64_t n_spectra, int32_t n_bands, const float *evals, const float *e_ref,
+                                  const float *weights, float *dLdE, double *stats, void *stream) {
+  TB_REQUIRE(n_spectra >= 1 && n_bands >= 1 && evals && e_ref && weights && dLdE && stats,
+             "tb_band_loss: bad argument");
+  band_loss_kernel<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(n_spectra * n_bands, n_bands, evals, e_ref,
+                                                                     weights, dLdE, stats);
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}
+
+extern "C" tb_status tb_band_gradient(int32_t n_cells, int32_t n_atoms, int32_t rows_per_cell,
+                                      const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
+                                      const float *feat, int32_t n_k, const float *kpts, const void *evecs,
+                                      const float *dLdE, float *g_val, float *g_diag, void *stream) {
+  TB_REQUIRE(n_cells >= 1 && n_k >= 1, "tb_band_gradient: bad batch size");
+  TB_REQUIRE(n_atoms >= 1 && n_atoms <= kMaxBand, "tb_band_gradient: n_atoms must be 1..64");
+  TB_REQUIRE(rows_per_cell >= n_atoms && rows_per_cell % 32 == 0, "tb_band_gradient: bad rows_per_cell");
+  TB_REQUIRE(slice_ptr && col && cnt && feat && kpts && evecs && dLdE && g_val && g_diag,
+             "tb_band_gradient: null pointer");
+  const size_t smem = grad_smem(n_atoms);
+  TB_CUDA(cudaFuncSetAttribute(band_gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  band_gradient_kernel<<<n_cells, 256, smem, static_cast<cudaStream_t>(stream)>>>(
+      n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, n_k, kpts, static_cast<const float2 *>(evecs), dLdE, g_val,
+      g_diag);
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}
+
+extern "C" tb_status tb_adamw_flat(int64_t n, float *params, const float *grad, float *m, float *v, int64_t step,
+                                   double lr, double beta1, double beta2, double eps, double weight_decay,
+                                   void *stream) {
+  TB_REQUIRE(n >= 1 && params && grad && m && v && step >= 1, "tb_adamw_flat: bad argument");
+  const double c1 = 1.0 - std::pow(beta1, (double)step), c2 = 1.0 - std::pow(beta2, (double)step);
+  adamw_flat_kernel<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, params, grad, m, v, (float)lr, (float)beta1, (float)beta2, (float)eps, (float)weight_decay, (float)c1,
+      (float)c2);
+  TB_CHECK_LAUNCH();
+  return TB_OK;
+}

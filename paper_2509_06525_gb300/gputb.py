@@ -26,6 +26,7 @@ TB_ERR_ELL_OVERFLOW = 5
 TB_ERR_BOUNDS = 6
 TB_ERR_NOT_FINITE = 7
 TB_ERR_TIMEOUT = 8
+TB_ERR_NOT_CONVERGED = 9
 
 F32, F64 = 0, 1
 KERNELS = {"jackson": 0, "lorentz": 1, "none": 2}
@@ -86,6 +87,22 @@ SIGNATURES = {
     "tb_build_hamiltonian": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i64,
                                       _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp,
                                       _c_sz, _c_vp]),
+    "tb_env_edge_inputs": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                                    _c_vp, _c_vp]),
+    "tb_env_forward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp,
+                                _c_vp]),
+    "tb_build_hamiltonian_env": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp,
+                                          _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp]),
+    "tb_env_backward_workspace_size": (_c_sz, [_c_i64, _c_i64]),
+    "tb_env_backward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
+                                 _c_vp, _c_sz, _c_vp]),
+    "tb_bloch_bands": (_c_i32, [_c_i32, _c_i32, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
+                                _c_i32, _c_vp, _c_vp, _c_vp, _c_vp]),
+    "tb_band_loss": (_c_i32, [_c_i64, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]),
+    "tb_band_gradient": (_c_i32, [_c_i32, _c_i32, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp,
+                                  _c_vp, _c_vp, _c_vp]),
+    "tb_adamw_flat": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl,
+                               _c_vp]),
     "tb_spectral_bounds_workspace_size": (_c_sz, [_c_i64, _c_i32]),
     "tb_spectral_bounds": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_i32, _c_u64, _c_vp, _c_vp,
                                     _c_sz, _c_vp]),
@@ -101,7 +118,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 5   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 6   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -602,3 +619,127 @@ def build_hamiltonian(positions, species, box, pbc, rcut, nb: Neighbors, model: 
                                 precision_of(dtype), _ptr(val), _ptr(diag), _ptr(ws), ws.numel(), _stream(stream))
     _check("tb_build_hamiltonian", st)
     return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
+
+
+# ---------------------------------------------------------------- environment network and bands
+
+ENV_NPARAM = 2349    # TB_ENV_NPARAM
+ENV_NFEAT = 20       # TB_ENV_NFEAT
+
+
+class EnvModel:
+    """Device state of the environment-network model: the flat FP32
+    parameter vector (layout of include/gputb.h), its AdamW moments, the
+    species-pair mixing c^{Z_i Z_j} and the reference onsite energies."""
+
+    def __init__(self, params, cmix, eps0, device="cuda"):
+        import numpy as np
+        flat = np.asarray(params, np.float32).reshape(-1)
+        if flat.size != ENV_NPARAM:
+            raise ValueError(f"expected {ENV_NPARAM} parameters, got {flat.size}")
+        c = np.asarray(cmix, np.float32).reshape(3, 3, 8, 8)
+        if not np.array_equal(c, c.transpose(1, 0, 2, 3)):
+            raise ValueError("the environment model needs a mixing symmetric in the species pair")
+        self.p = torch.tensor(flat, device=device)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.cmix = torch.tensor(c.reshape(-1), device=device)
+        self.eps0 = torch.tensor(np.asarray(eps0, np.float32), device=device)
+        self.step = 0
+
+
+def env_edge_inputs(positions, species, box, pbc, rcut, nb: Neighbors, cmix, v, stream=None) -> torch.Tensor:
+    b, p, bptr, pptr = _host_box(box, pbc)
+    feat = torch.zeros((max(nb.total, 1), ENV_NFEAT), dtype=torch.float32, device=positions.device)
+    _check("tb_env_edge_inputs", lib().tb_env_edge_inputs(
+        _ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr), _ptr(nb.col),
+        _ptr(nb.cnt), _ptr(cmix), _ptr(v), _ptr(feat), _stream(stream)))
+    return feat
+
+
+def env_forward(n, slice_ptr, cnt, feat, v, species, model: EnvModel, total: int, dtype=torch.float32,
+                with_diag=True, stream=None):
+    """(val [total], diag [n] or None) of the model from stored bond inputs."""
+    val = torch.zeros(max(total, 1), dtype=dtype, device=feat.device)
+    diag = torch.zeros(n, dtype=dtype, device=feat.device) if with_diag else None
+    _check("tb_env_forward", lib().tb_env_forward(
+        n, _ptr(slice_ptr), _ptr(cnt), _ptr(feat), _ptr(v), _ptr(species), _ptr(model.p), _ptr(model.eps0),
+        precision_of(dtype), _ptr(val), _ptr(diag), _stream(stream)))
+    return val, diag
+
+
+def build_hamiltonian_env(positions, species, box, pbc, rcut, nb: Neighbors, model: EnvModel, v=None,
+                          dtype=torch.float32, with_diag=True, stream=None) -> SellMatrix:
+    """H of the environment-network model straight from positions."""
+    if v is None:
+        v = compute_descriptors(positions, species, box, pbc, rcut, nb, model.cmix, stream)
+    b, p, bptr, pptr = _host_box(box, pbc)
+    val = torch.zeros(max(nb.total, 1), dtype=dtype, device=positions.device)
+    diag = torch.empty(nb.n, dtype=dtype, device=positions.device) if with_diag else None
+    _check("tb_build_hamiltonian_env", lib().tb_build_hamiltonian_env(
+        _ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr), _ptr(nb.col),
+        _ptr(nb.cnt), _ptr(model.cmix), _ptr(v), _ptr(model.p), _ptr(model.eps0), precision_of(dtype), _ptr(val),
+        _ptr(diag), _stream(stream)))
+    return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
+
+
+def env_backward(n, slice_ptr, cnt, total, feat, v, species, model: EnvModel, g_val, g_diag, grad=None,
+                 workspace=None, stream=None) -> torch.Tensor:
+    L = lib()
+    if grad is None:
+        grad = torch.empty(ENV_NPARAM, dtype=torch.float32, device=feat.device)
+    need = L.tb_env_backward_workspace_size(n, total)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, feat.device)
+    _check("tb_env_backward", L.tb_env_backward(
+        n, _ptr(slice_ptr), _ptr(cnt), total, _ptr(feat), _ptr(v), _ptr(species), _ptr(model.p), _ptr(g_val),
+        _ptr(g_diag), _ptr(grad), _ptr(workspace), workspace.numel(), _stream(stream)))
+    return grad
+
+
+def bloch_bands(n_cells, n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, val, diag, kpts, max_sweeps=30,
+                flags=None, stream=None):
+    """(evals [cells, nk, n], evecs [cells, nk, n, n] complex64) of a batch
+    of periodic cells (kpts: device float32 [nk, 3])."""
+    n_k = kpts.shape[0]
+    dev = feat.device
+    evals = torch.empty((n_cells, n_k, n_atoms), dtype=torch.float32, device=dev)
+    evecs = torch.empty((n_cells, n_k, n_atoms, n_atoms), dtype=torch.complex64, device=dev)
+    if flags is None:
+        flags = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check("tb_bloch_bands", lib().tb_bloch_bands(
+        n_cells, n_atoms, rows_per_cell, _ptr(slice_ptr), _ptr(col), _ptr(cnt), _ptr(feat), _ptr(val), _ptr(diag),
+        n_k, _ptr(kpts), max_sweeps, _ptr(evals), _ptr(evecs), _ptr(flags), _stream(stream)))
+    return evals, evecs
+
+
+def band_loss(evals, e_ref, weights, dLdE=None, stats=None, stream=None):
+    """(dL/dE, stats = {S, sum w D^2, L} device float64 [3]) of Eq. 3."""
+    nb = evals.shape[-1]
+    if dLdE is None:
+        dLdE = torch.empty_like(evals)
+    if stats is None:
+        stats = torch.empty(3, dtype=torch.float64, device=evals.device)
+    _check("tb_band_loss", lib().tb_band_loss(evals.numel() // nb, nb, _ptr(evals), _ptr(e_ref), _ptr(weights),
+                                              _ptr(dLdE), _ptr(stats), _stream(stream)))
+    return dLdE, stats
+
+
+def band_gradient(n_cells, n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, kpts, evecs, dLdE, total,
+                  g_val=None, g_diag=None, stream=None):
+    dev = feat.device
+    if g_val is None:
+        g_val = torch.zeros(max(total, 1), dtype=torch.float32, device=dev)
+    if g_diag is None:
+        g_diag = torch.zeros(n_cells * rows_per_cell, dtype=torch.float32, device=dev)
+    _check("tb_band_gradient", lib().tb_band_gradient(
+        n_cells, n_atoms, rows_per_cell, _ptr(slice_ptr), _ptr(col), _ptr(cnt), _ptr(feat), kpts.shape[0],
+        _ptr(kpts), _ptr(evecs), _ptr(dLdE), _ptr(g_val), _ptr(g_diag), _stream(stream)))
+    return g_val, g_diag
+
+
+def adamw_flat(model: EnvModel, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    model.step += 1
+    _check("tb_adamw_flat", lib().tb_adamw_flat(model.p.numel(), _ptr(model.p), _ptr(grad), _ptr(model.m),
+                                                _ptr(model.v), model.step, lr, beta1, beta2, eps, weight_decay,
+                                                _stream(stream)))
