@@ -37,7 +37,17 @@ constexpr int kNF = TB_ENV_NFEAT;  // C[8], u[8], n_z^2, d[3]
 constexpr int kMaxBand = 64;
 constexpr int kMaxCnt = 32;
 
-__device__ __forceinline__ float sig(float z) { return 1.0f / (1.0f + expf(-z)); }
+// onsite block shifted by two floats in shared memory so that every weight
+// row starts on a 16-byte boundary (float4 broadcast loads)
+constexpr int kShift = 2;
+constexpr int sWo1 = oWo1 + kShift, sbo1 = obo1 + kShift, sWo2 = oWo2 + kShift, sbo2 = obo2 + kShift;
+constexpr int kNPs = kNP + kShift;
+static_assert(oWe2 % 4 == 0 && oWh1 % 4 == 0 && oWh2 % 4 == 0 && oWh3 % 4 == 0 && sWo1 % 4 == 0 && sWo2 % 4 == 0,
+              "weight rows 16-byte aligned in shared memory");
+
+// logistic function from the hardware exponential and divide (a few ulp;
+// the argument is clamped so that 1 + e^{-z} stays below 2^126)
+__device__ __forceinline__ float sig(float z) { return __fdividef(1.0f, 1.0f + __expf(-fmaxf(z, -80.0f))); }
 __device__ __forceinline__ float silu(float z) { return z * sig(z); }
 __device__ __forceinline__ float dsilu(float z) {
   const float s = sig(z);
@@ -45,42 +55,49 @@ __device__ __forceinline__ float dsilu(float z) {
 }
 
 __device__ __forceinline__ void stage_params(float *P, const float *__restrict__ params) {
-  for (int k = threadIdx.x; k < kNP; k += blockDim.x) P[k] = params[k];
+  for (int k = threadIdx.x; k < kNP; k += blockDim.x) P[k < oWo1 ? k : k + kShift] = params[k];
+}
+
+__device__ __forceinline__ float dot8(const float *w, const float (&x)[8], float acc) {
+  const float4 a = *reinterpret_cast<const float4 *>(w);
+  const float4 b = *reinterpret_cast<const float4 *>(w + 4);
+  acc = fmaf(a.x, x[0], acc);
+  acc = fmaf(a.y, x[1], acc);
+  acc = fmaf(a.z, x[2], acc);
+  acc = fmaf(a.w, x[3], acc);
+  acc = fmaf(b.x, x[4], acc);
+  acc = fmaf(b.y, x[5], acc);
+  acc = fmaf(b.z, x[6], acc);
+  return fmaf(b.w, x[7], acc);
+}
+
+__device__ __forceinline__ float dot32(const float *w, const float (&x)[32], float acc) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = *reinterpret_cast<const float4 *>(w + 4 * q);
+    acc = fmaf(a.x, x[4 * q], acc);
+    acc = fmaf(a.y, x[4 * q + 1], acc);
+    acc = fmaf(a.z, x[4 * q + 2], acc);
+    acc = fmaf(a.w, x[4 * q + 3], acc);
+  }
+  return acc;
 }
 
 // t_ij from the inputs of one bond (weights P in shared memory)
 __device__ float hop_forward(const float *P, const float (&C)[8], const float (&u)[8], float nz2) {
   float h1[32];
 #pragma unroll
-  for (int o = 0; o < 32; ++o) {
-    float z = P[obe1 + o];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) z = fmaf(P[oWe1 + o * 8 + i], u[i], z);
-    h1[o] = silu(z);
-  }
+  for (int o = 0; o < 32; ++o) h1[o] = silu(dot8(P + oWe1 + o * 8, u, P[obe1 + o]));
   float e[8];
 #pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    float z = P[obe2 + o];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z = fmaf(P[oWe2 + o * 32 + i], h1[i], z);
-    e[o] = C[o] * z;
-  }
+  for (int o = 0; o < 8; ++o) e[o] = C[o] * dot32(P + oWe2 + o * 32, h1, P[obe2 + o]);
   float h2[32];
 #pragma unroll
-  for (int o = 0; o < 32; ++o) {
-    float z = P[obh1 + o];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) z = fmaf(P[oWh1 + o * 8 + i], e[i], z);
-    h2[o] = silu(z);
-  }
+  for (int o = 0; o < 32; ++o) h2[o] = silu(dot8(P + oWh1 + o * 8, e, P[obh1 + o]));
   float y0 = P[obh3], y1 = P[obh3 + 1];
 #pragma unroll 4
   for (int o = 0; o < 32; ++o) {
-    float z = P[obh2 + o];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z = fmaf(P[oWh2 + o * 32 + i], h2[i], z);
-    const float h3 = silu(z);
+    const float h3 = silu(dot32(P + oWh2 + o * 32, h2, P[obh2 + o]));
     y0 = fmaf(P[oWh3 + o], h3, y0);
     y1 = fmaf(P[oWh3 + 32 + o], h3, y1);
   }
@@ -89,14 +106,9 @@ __device__ float hop_forward(const float *P, const float (&C)[8], const float (&
 
 // MLP_alpha(v_i)[Z_i]
 __device__ float onsite_forward(const float *P, const float (&v)[8], int z) {
-  float out = P[obo2 + z];
+  float out = P[sbo2 + z];
 #pragma unroll 4
-  for (int o = 0; o < 32; ++o) {
-    float s = P[obo1 + o];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) s = fmaf(P[oWo1 + o * 8 + i], v[i], s);
-    out = fmaf(P[oWo2 + z * 32 + o], silu(s), out);
-  }
+  for (int o = 0; o < 32; ++o) out = fmaf(P[sWo2 + z * 32 + o], silu(dot8(P + sWo1 + o * 8, v, P[sbo1 + o])), out);
   return out;
 }
 
@@ -114,17 +126,15 @@ __device__ __forceinline__ void bond_inputs(const double *__restrict__ pos, cons
                                             const float *__restrict__ v, int64_t i, int32_t j, float (&C)[8],
                                             float (&u)[8], float &nz2, float3 &d) {
   const int zi = min(max(species[i], 0), 2), zj = min(max(species[j], 0), 2);
-  const float r = bond_length_f32(B, pos, i, j);
-  bond_descriptor(r, rcut, sc + (zi * 3 + zj) * 64, C);
+  d = bond_vector_f32(B, pos, i, j);
+  const float r2 = bond_r2_f32(d);
+  bond_descriptor(sqrtf(r2), rcut, sc + (zi * 3 + zj) * 64, C);
   float vi[8], vj[8];
   load8(v + i * 8, vi);
   load8(v + (int64_t)j * 8, vj);
 #pragma unroll
   for (int k = 0; k < 8; ++k) u[k] = vi[k] + vj[k];
-  const double3 dd = bond_vector(B, pos, i, j);
-  const double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-  nz2 = r2 > 0.0 ? (float)(dd.z * dd.z / r2) : 0.0f;
-  d = make_float3((float)dd.x, (float)dd.y, (float)dd.z);
+  nz2 = r2 > 0.0f ? d.z * d.z / r2 : 0.0f;
 }
 
 __global__ void env_inputs_kernel(const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n,
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(128) env_forward_kernel(
     float rcut, const int32_t *__restrict__ col, const float *__restrict__ cmix, const float *__restrict__ v,
     const float *__restrict__ params, const float *__restrict__ eps0, valT *__restrict__ val,
     valT *__restrict__ diag) {
-  __shared__ float P[kNP];
+  __shared__ __align__(16) float P[kNPs];
   __shared__ float sc[9 * 64];
   stage_params(P, params);
   if (FROM_POS) load_mixing(sc, cmix);
@@ -296,11 +306,9 @@ __device__ void onsite_backward_item(const float *P, float *R, const float (&v)[
 #pragma unroll
   for (int k = 0; k < 8; ++k) R[rV + k] = v[k];
   for (int o = 0; o < 32; ++o) {
-    float s = P[obo1 + o];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) s = fmaf(P[oWo1 + o * 8 + i], v[i], s);
+    const float s = dot8(P + sWo1 + o * 8, v, P[sbo1 + o]);
     R[rH + o] = silu(s);
-    R[rDZ + o] = dsilu(s) * P[oWo2 + z * 32 + o] * g;
+    R[rDZ + o] = dsilu(s) * P[sWo2 + z * 32 + o] * g;
   }
   for (int a = 0; a < 3; ++a) R[rDO + a] = a == z ? g : 0.0f;
 }
@@ -311,9 +319,9 @@ __global__ void __launch_bounds__(kBT) env_backward_kernel(
     const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ v,
     const int32_t *__restrict__ species, const float *__restrict__ params, const float *__restrict__ g_val,
     const float *__restrict__ g_diag, float *__restrict__ partial) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   float *P = smem;
-  float *rows = smem + kNP;
+  float *rows = smem + kNPs;
   stage_params(P, params);
   float *R = rows + threadIdx.x * kRow;
   R[sOne] = 1.0f;
@@ -709,7 +717,7 @@ int backward_grid(int64_t items) {
   const int64_t g = (int64_t)sm_count() * 3;
   return (int)(tiles < g ? (tiles > 0 ? tiles : 1) : g);
 }
-constexpr size_t kBackSmem = (size_t)(kNP + kBT * kRow) * sizeof(float);
+constexpr size_t kBackSmem = (size_t)(kNPs + kBT * kRow) * sizeof(float);
 
 tb_status check_sell(int64_t n, const int64_t *slice_ptr, const int32_t *cnt) {
   TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "bad row count");
@@ -744,8 +752,11 @@ tb_status launch_env_forward(int64_t n, const int64_t *slice_ptr, const int32_t 
                              const double *pos, const int32_t *species, const Box &B, float rcut,
                              const int32_t *col, const float *cmix, const float *v, const float *params,
                              const float *eps0, void *val, void *diag, cudaStream_t st) {
+  // one wave: the resident CTAs of every SM, each striding over the rows
+  int occ = 0;
+  TB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_forward_kernel<valT, FROM_POS>, 128, 0));
   const int64_t want = (n + 127) / 128;
-  const int64_t cap = (int64_t)sm_count() * 16;
+  const int64_t cap = (int64_t)sm_count() * (occ > 0 ? occ : 1);
   const unsigned grid = (unsigned)(want < cap ? want : cap);
   env_forward_kernel<valT, FROM_POS><<<grid, 128, 0, st>>>(n, slice_ptr, cnt, feat, pos, species, B, rcut, col,
                                                           cmix, v, params, eps0, static_cast<valT *>(val),

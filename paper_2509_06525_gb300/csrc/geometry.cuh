@@ -90,13 +90,13 @@ __device__ __forceinline__ double bond_r2(const Box &B, const double *__restrict
   return sq_norm(make_double3(dx, dy, dz));
 }
 
-// |r_j - r_i| (minimum image) in FP32 for the learned-H features: the
+// r_j - r_i (minimum image) in FP32 for the learned-H features: the
 // coordinate differences in FP64 (exact for nearby atoms), the image shift
 // decided from their FP32 values and applied in FP64 only when it is not
-// zero (a periodic seam), then FP32 for the length.  The shift agrees with
-// min_image for every pair closer than half a periodic width.
-__device__ __forceinline__ float bond_length_f32(const Box &B, const double *__restrict__ pos, int64_t i,
-                                                 int64_t j) {
+// zero (a periodic seam), then FP32.  The shift agrees with min_image for
+// every pair closer than half a periodic width.
+__device__ __forceinline__ float3 bond_vector_f32(const Box &B, const double *__restrict__ pos, int64_t i,
+                                                  int64_t j) {
   double dx = __ldg(pos + 3 * j) - __ldg(pos + 3 * i);
   double dy = __ldg(pos + 3 * j + 1) - __ldg(pos + 3 * i + 1);
   double dz = __ldg(pos + 3 * j + 2) - __ldg(pos + 3 * i + 2);
@@ -119,8 +119,15 @@ __device__ __forceinline__ float bond_length_f32(const Box &B, const double *__r
     const float n1 = rintf((float)dx * (float)B.iax);
     if (n1 != 0.0f) dx -= (double)n1 * B.ax;
   }
-  const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-  return sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
+  return make_float3((float)dx, (float)dy, (float)dz);
+}
+
+// |r|^2 and |r| of an FP32 bond vector (the length of the learned features)
+__device__ __forceinline__ float bond_r2_f32(float3 d) { return fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)); }
+
+__device__ __forceinline__ float bond_length_f32(const Box &B, const double *__restrict__ pos, int64_t i,
+                                                 int64_t j) {
+  return sqrtf(bond_r2_f32(bond_vector_f32(B, pos, i, j)));
 }
 
 }  // namespace gputb
