@@ -602,7 +602,8 @@ TB_API tb_status tb_bloch_bands(int32_t n_cells, int32_t n_atoms, int32_t rows_p
  * [n_spectra][n_bands]) with band weights w (device float [n_bands]):
  *   D = E - E_ref, S = sum w_b |D|, L = S^2 + sum w_b D^2,
  *   dLdE = 2 S w_b sign(D) + 2 w_b D  (sign(0) = 0);
- * stats (device double [3]) = {S, sum w_b D^2, L}, sums in FP64. */
+ * stats (device double [3]) = {S, sum w_b D^2, L}: terms in FP32, sums in
+ * FP64. */
 TB_API tb_status tb_band_loss(int64_t n_spectra, int32_t n_bands, const float *evals, const float *e_ref,
                               const float *weights, float *dLdE, double *stats, void *stream);
 

@@ -388,26 +388,91 @@ __global__ void __launch_bounds__(kBT) env_backward_kernel(
   }
 }
 
-__global__ void partial_sum_kernel(const float *__restrict__ partial, int nblocks, float *__restrict__ grad) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= kNP) return;
+// grad[p] = sum over the partial rows in a fixed order: warp w of a CTA adds
+// rows w, w + 8, ... for 32 parameters, then the 8 warp sums in order
+__global__ void __launch_bounds__(256) partial_sum_kernel(const float *__restrict__ partial, int nblocks,
+                                                          float *__restrict__ grad) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += (double)partial[(int64_t)b * kNP + p];
-  grad[p] = (float)s;
+  if (p < kNP)
+    for (int b = w; b < nblocks; b += 8) s += (double)partial[(int64_t)b * kNP + p];
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && p < kNP) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += part[k][lane];
+    grad[p] = (float)t;
+  }
 }
 
 // ------------------------------------------------------------------ Bloch bands
 
-// H(k) of cell c into A (row stride ld); error bits: 1 = a neighbour outside
-// the cell's rows, 4 = a row with more than kMaxCnt neighbours
-__device__ int build_bloch(float2 *A, int ld, int n, int c, int rows_per_cell, const int64_t *__restrict__ slice_ptr,
+// butterfly sums: every lane ends with the same two totals, bit for bit
+__device__ __forceinline__ void warp_sum2(float &a, float &b) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+
+// The CTA that solves one Bloch matrix (n up to 64).
+struct CtaGroup {
+  float *red;  // [16] shared scratch for the reductions
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sum2(float &a, float &b) const {
+    warp_sum2(a, b);
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = a;
+      red[8 + (threadIdx.x >> 5)] = b;
+    }
+    __syncthreads();
+    a = 0.0f;
+    b = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[w];
+      b += red[8 + w];
+    }
+    __syncthreads();
+  }
+};
+
+// players a < b of pair pp in round `round` of the circle method over m
+// players (player 0 fixed, the others rotating)
+__device__ __forceinline__ void round_pair(int pp, int round, int m, int &a, int &b) {
+  a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
+  b = 1 + (m - 2 - pp + round) % (m - 1);
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// H(k) of cell c, cyclic Jacobi, ascending eigenvalues and their vectors
+// written out.  Shared memory: A and V [n][n+1], rot and nd [n/2 + 1].
+// Returns error bits: 1 = a neighbour outside the cell's rows, 2 = not
+// converged in max_sweeps, 4 = a row with more than kMaxCnt neighbours.
+template <class G>
+__device__ int bloch_solve(const G &g, float2 *A, float2 *V, float4 *rot, float2 *nd, int n, int c, int q,
+                           int rows_per_cell, const int64_t *__restrict__ slice_ptr,
                            const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
                            const float *__restrict__ feat, const float *__restrict__ val,
-                           const float *__restrict__ diag, float3 k) {
+                           const float *__restrict__ diag, int n_k, const float *__restrict__ kpts, int max_sweeps,
+                           float *__restrict__ evals, float2 *__restrict__ evecs) {
+  const int ld = n + 1, tid = g.rank(), gs = g.size();
+  const float3 k = make_float3(kpts[3 * q], kpts[3 * q + 1], kpts[3 * q + 2]);
   int err = 0;
-  for (int idx = threadIdx.x; idx < n * ld; idx += blockDim.x) A[idx] = make_float2(0.0f, 0.0f);
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int idx = tid; idx < n * ld; idx += gs) {
+    A[idx] = make_float2(0.0f, 0.0f);
+    V[idx] = make_float2(idx / ld == idx % ld ? 1.0f : 0.0f, 0.0f);
+  }
+  g.sync();
+  // Bloch sum: every stored neighbour adds t e^{i k.d}; one thread per row
+  for (int i = tid; i < n; i += gs) {
     const int64_t row = (int64_t)c * rows_per_cell + i;
     const int64_t e0 = slice_ptr[row >> 5] + (row & 31);
     const int m = cnt[row];
@@ -427,48 +492,19 @@ __device__ int build_bloch(float2 *A, int ld, int n, int c, int rows_per_cell, c
       a.x = fmaf(t, cs, a.x);
       a.y = fmaf(t, sn, a.y);
     }
-    if (diag) A[i * ld + i].x += diag[row];
+    // the diagonal of a Hermitian matrix is real
+    A[i * ld + i] = make_float2(A[i * ld + i].x + (diag ? diag[row] : 0.0f), 0.0f);
   }
-  __syncthreads();
-  return err;
-}
-
-// one CTA per (k-point, cell): Bloch matrix, cyclic Jacobi, sorted output
-__global__ void __launch_bounds__(256) bloch_eigh_kernel(
-    int n, int rows_per_cell, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
-    const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ val,
-    const float *__restrict__ diag, int n_k, const float *__restrict__ kpts, int max_sweeps,
-    float *__restrict__ evals, float2 *__restrict__ evecs, int *__restrict__ flags) {
-  extern __shared__ float2 sh[];
-  const int ld = n + 1;
-  float2 *A = sh;
-  float2 *V = A + n * ld;
-  float4 *rot = reinterpret_cast<float4 *>(V + n * ld);  // c, s, cos(phi), sin(phi) per pair
-  float2 *newdiag = reinterpret_cast<float2 *>(rot + kMaxBand / 2);
-  float *red = reinterpret_cast<float *>(newdiag + kMaxBand / 2);  // [2][8]
-  const int q = blockIdx.x, c = blockIdx.y;
-  const float3 k = make_float3(kpts[3 * q], kpts[3 * q + 1], kpts[3 * q + 2]);
-  const int err = build_bloch(A, ld, n, c, rows_per_cell, slice_ptr, col, cnt, feat, val, diag, k);
-  if (err) atomicOr(flags, err);
-  for (int idx = threadIdx.x; idx < n * ld; idx += blockDim.x) {
-    const int i = idx / ld, j = idx % ld;
-    V[idx] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
-  }
-  // the diagonal of a Hermitian matrix is real
-  for (int i = threadIdx.x; i < n; i += blockDim.x) A[i * ld + i].y = 0.0f;
-  __syncthreads();
+  g.sync();
 
   const int m = (n + 1) & ~1;  // players, with one idle slot when n is odd
   const int half = m / 2;
   bool converged = false;
   for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
     for (int round = 0; round < m - 1; ++round) {
-      // pair p of this round: positions p and m-1-p of the rotated circle
-      if (threadIdx.x < half) {
-        const int pp = threadIdx.x;
-        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
-        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
+      for (int pp = tid; pp < half; pp += gs) {
+        int a, b;
+        round_pair(pp, round, m, a, b);
         float4 r = make_float4(1.0f, 0.0f, 1.0f, 0.0f);
         float2 dg = make_float2(0.0f, 0.0f);
         if (b < n) {
@@ -488,88 +524,68 @@ __global__ void __launch_bounds__(256) bloch_eigh_kernel(
           }
         }
         rot[pp] = r;
-        newdiag[pp] = dg;
+        nd[pp] = dg;
       }
-      __syncthreads();
+      g.sync();
       // rows: A <- U^H A  (new_p = c A_p - s e^{i phi} A_q, new_q = s A_p + c e^{i phi} A_q)
-      for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
+      for (int idx = tid; idx < half * n; idx += gs) {
         const int pp = idx / n, j = idx % n;
-        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
-        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
+        int a, b;
+        round_pair(pp, round, m, a, b);
         if (b >= n) continue;
         const float4 r = rot[pp];
         const float2 x = A[a * ld + j], y = A[b * ld + j];
-        // e^{i phi} y
         const float2 ey = make_float2(r.z * y.x - r.w * y.y, r.z * y.y + r.w * y.x);
         A[a * ld + j] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
         A[b * ld + j] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
       }
-      __syncthreads();
+      g.sync();
       // columns: A <- A U and V <- V U  (new col p = c A_p - s e^{-i phi} A_q,
       // new col q = s A_p + c e^{-i phi} A_q)
-      for (int idx = threadIdx.x; idx < 2 * half * n; idx += blockDim.x) {
+      for (int idx = tid; idx < 2 * half * n; idx += gs) {
         const int which = idx / (half * n);
         const int rem = idx % (half * n);
         const int pp = rem / n, i = rem % n;
-        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
-        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
+        int a, b;
+        round_pair(pp, round, m, a, b);
         if (b >= n) continue;
         const float4 r = rot[pp];
         float2 *M = which ? V : A;
         const float2 x = M[i * ld + a], y = M[i * ld + b];
-        // e^{-i phi} y
         const float2 ey = make_float2(r.z * y.x + r.w * y.y, r.z * y.y - r.w * y.x);
         M[i * ld + a] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
         M[i * ld + b] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
       }
-      __syncthreads();
-      // the rotated 2 x 2 block is diagonal and real up to rounding
-      if (threadIdx.x < half) {
-        const int pp = threadIdx.x;
-        int a = pp == 0 ? 0 : 1 + (pp - 1 + round) % (m - 1);
-        int b = 1 + (m - 1 - 1 - pp + round) % (m - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
+      g.sync();
+      // the rotated 2 x 2 block: zero off-diagonal, closed-form diagonal
+      for (int pp = tid; pp < half; pp += gs) {
+        int a, b;
+        round_pair(pp, round, m, a, b);
         if (b < n && rot[pp].y != 0.0f) {
           A[a * ld + b] = make_float2(0.0f, 0.0f);
           A[b * ld + a] = make_float2(0.0f, 0.0f);
-          A[a * ld + a] = make_float2(newdiag[pp].x, 0.0f);
-          A[b * ld + b] = make_float2(newdiag[pp].y, 0.0f);
+          A[a * ld + a] = make_float2(nd[pp].x, 0.0f);
+          A[b * ld + b] = make_float2(nd[pp].y, 0.0f);
         }
       }
-      __syncthreads();
+      g.sync();
     }
     // off-diagonal mass against the total
     float off = 0.0f, tot = 0.0f;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = tid; idx < n * n; idx += gs) {
       const int i = idx / n, j = idx % n;
       const float2 a = A[i * ld + j];
       const float s = a.x * a.x + a.y * a.y;
       tot += s;
       if (i != j) off += s;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = off;
-      red[8 + (threadIdx.x >> 5)] = tot;
-    }
-    __syncthreads();
-    float so = 0.0f, st = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      so += red[w];
-      st += red[8 + w];
-    }
-    converged = so <= 1e-13f * st;
-    __syncthreads();
+    g.sum2(off, tot);
+    converged = off <= 1e-13f * tot;
   }
-  if (!converged && threadIdx.x == 0) atomicOr(flags, 2);
+  if (!converged) err |= 2;
   // ascending order: rank of each diagonal entry (ties by index)
   const int64_t base = ((int64_t)c * n_k + q) * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = tid; i < n; i += gs) {
     const float li = A[i * ld + i].x;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
@@ -579,21 +595,210 @@ __global__ void __launch_bounds__(256) bloch_eigh_kernel(
     evals[base + rank] = li;
     for (int a = 0; a < n; ++a) evecs[(base + a) * n + rank] = V[a * ld + i];
   }
+  return err;
 }
 
-// Eq. 3 over all (cell, k, band) items: stats = {S, sum w D^2, L}
-__global__ void __launch_bounds__(1024) band_loss_kernel(int64_t items, int nb, const float *__restrict__ E,
+// one CTA per (k-point, cell), n up to 64
+__global__ void __launch_bounds__(256) bloch_eigh_kernel(
+    int n, int rows_per_cell, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ val,
+    const float *__restrict__ diag, int n_k, const float *__restrict__ kpts, int max_sweeps,
+    float *__restrict__ evals, float2 *__restrict__ evecs, int *__restrict__ flags) {
+  extern __shared__ __align__(16) float2 sh[];
+  float2 *A = sh;
+  float2 *V = A + n * (n + 1);
+  float4 *rot = reinterpret_cast<float4 *>(V + n * (n + 1));
+  float2 *nd = reinterpret_cast<float2 *>(rot + kMaxBand / 2);
+  float *red = reinterpret_cast<float *>(nd + kMaxBand / 2);
+  const int err = bloch_solve(CtaGroup{red}, A, V, rot, nd, n, blockIdx.y, blockIdx.x, rows_per_cell, slice_ptr,
+                              col, cnt, feat, val, diag, n_k, kpts, max_sweeps, evals, evecs);
+  if (err) atomicOr(flags, err);
+}
+
+// One warp per (cell, k-point) for n up to 32: lane j owns column j in the
+// row updates and row j in the column updates, so a round is a loop over
+// the n/2 pairs with no index arithmetic and only warp-level
+// synchronisation; kWarpsEigh matrices per CTA.
+constexpr int kWarpsEigh = 4;
+__host__ __device__ constexpr size_t eigh_warp_bytes(int n) {
+  return ((size_t)2 * n * (n + 1) * sizeof(float2) + 16 * (sizeof(float4) + sizeof(float2) + 2 * sizeof(int)) + 15) /
+         16 * 16;
+}
+
+__device__ int bloch_solve_warp(float2 *A, float2 *V, float4 *rot, float2 *nd, int *pa, int *pb, int n, int c, int q,
+                                int rows_per_cell, const int64_t *__restrict__ slice_ptr,
+                                const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
+                                const float *__restrict__ feat, const float *__restrict__ val,
+                                const float *__restrict__ diag, int n_k, const float *__restrict__ kpts,
+                                int max_sweeps, float *__restrict__ evals, float2 *__restrict__ evecs) {
+  const int lane = threadIdx.x & 31, ld = n + 1;
+  const float3 k = make_float3(kpts[3 * q], kpts[3 * q + 1], kpts[3 * q + 2]);
+  int err = 0;
+  if (lane < n) {
+    for (int j = 0; j < n; ++j) {
+      A[lane * ld + j] = make_float2(0.0f, 0.0f);
+      V[lane * ld + j] = make_float2(lane == j ? 1.0f : 0.0f, 0.0f);
+    }
+    // Bloch sum of row `lane`: every stored neighbour adds t e^{i k.d}
+    const int64_t row = (int64_t)c * rows_per_cell + lane;
+    const int64_t e0 = slice_ptr[row >> 5] + (row & 31);
+    const int m = cnt[row];
+    if (m > kMaxCnt) err |= 4;
+    for (int s = 0; s < m; ++s) {
+      const int64_t e = e0 + 32 * s;
+      const int64_t j = (int64_t)col[e] - (int64_t)c * rows_per_cell;
+      if (j < 0 || j >= n) {
+        err |= 1;
+        continue;
+      }
+      const float *f = feat + e * kNF;
+      float sn, cs;
+      sincosf(k.x * f[17] + k.y * f[18] + k.z * f[19], &sn, &cs);
+      const float t = val[e];
+      float2 &a = A[lane * ld + j];
+      a.x = fmaf(t, cs, a.x);
+      a.y = fmaf(t, sn, a.y);
+    }
+    A[lane * ld + lane] = make_float2(A[lane * ld + lane].x + (diag ? diag[row] : 0.0f), 0.0f);
+  }
+  __syncwarp();
+
+  const int m = (n + 1) & ~1;
+  const int half = m / 2;
+  bool converged = false;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    for (int round = 0; round < m - 1; ++round) {
+      if (lane < half) {
+        int a, b;
+        round_pair(lane, round, m, a, b);
+        float4 r = make_float4(1.0f, 0.0f, 1.0f, 0.0f);
+        float2 dg = make_float2(0.0f, 0.0f);
+        if (b < n) {
+          const float2 h = A[a * ld + b];
+          const float ah = hypotf(h.x, h.y);
+          const float app = A[a * ld + a].x, aqq = A[b * ld + b].x;
+          dg = make_float2(app, aqq);
+          if (ah > 0.0f) {
+            const float tau = (aqq - app) / (2.0f * ah);
+            const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            const float cth = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+            r = make_float4(cth, t * cth, h.x / ah, h.y / ah);
+            dg = make_float2(app - t * ah, aqq + t * ah);
+          }
+        } else {
+          b = -1;  // idle pair (odd n)
+        }
+        pa[lane] = a;
+        pb[lane] = b;
+        rot[lane] = r;
+        nd[lane] = dg;
+      }
+      __syncwarp();
+      if (lane < n) {
+        // rows a, b at column `lane`: A <- U^H A
+        for (int pp = 0; pp < half; ++pp) {
+          const int a = pa[pp], b = pb[pp];
+          if (b < 0) continue;
+          const float4 r = rot[pp];
+          const float2 x = A[a * ld + lane], y = A[b * ld + lane];
+          const float2 ey = make_float2(r.z * y.x - r.w * y.y, r.z * y.y + r.w * y.x);
+          A[a * ld + lane] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
+          A[b * ld + lane] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
+        }
+      }
+      __syncwarp();
+      if (lane < n) {
+        // columns a, b at row `lane`: A <- A U, V <- V U
+        for (int pp = 0; pp < half; ++pp) {
+          const int a = pa[pp], b = pb[pp];
+          if (b < 0) continue;
+          const float4 r = rot[pp];
+          float2 x = A[lane * ld + a], y = A[lane * ld + b];
+          float2 ey = make_float2(r.z * y.x + r.w * y.y, r.z * y.y - r.w * y.x);
+          A[lane * ld + a] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
+          A[lane * ld + b] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
+          x = V[lane * ld + a];
+          y = V[lane * ld + b];
+          ey = make_float2(r.z * y.x + r.w * y.y, r.z * y.y - r.w * y.x);
+          V[lane * ld + a] = make_float2(r.x * x.x - r.y * ey.x, r.x * x.y - r.y * ey.y);
+          V[lane * ld + b] = make_float2(r.y * x.x + r.x * ey.x, r.y * x.y + r.x * ey.y);
+        }
+      }
+      __syncwarp();
+      if (lane < half) {
+        const int a = pa[lane], b = pb[lane];
+        if (b >= 0 && rot[lane].y != 0.0f) {
+          A[a * ld + b] = make_float2(0.0f, 0.0f);
+          A[b * ld + a] = make_float2(0.0f, 0.0f);
+          A[a * ld + a] = make_float2(nd[lane].x, 0.0f);
+          A[b * ld + b] = make_float2(nd[lane].y, 0.0f);
+        }
+      }
+      __syncwarp();
+    }
+    float off = 0.0f, tot = 0.0f;
+    if (lane < n) {
+      for (int j = 0; j < n; ++j) {
+        const float2 a = A[lane * ld + j];
+        const float s = a.x * a.x + a.y * a.y;
+        tot += s;
+        if (j != lane) off += s;
+      }
+    }
+    warp_sum2(off, tot);
+    converged = off <= 1e-13f * tot;
+  }
+  if (!converged) err |= 2;
+  const int64_t base = ((int64_t)c * n_k + q) * n;
+  if (lane < n) {
+    const float li = A[lane * ld + lane].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float lj = A[j * ld + j].x;
+      rank += (lj < li) || (lj == li && j < lane);
+    }
+    evals[base + rank] = li;
+    for (int a = 0; a < n; ++a) evecs[(base + a) * n + rank] = V[a * ld + lane];
+  }
+  return err;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsEigh) bloch_eigh_warp_kernel(
+    int n, int rows_per_cell, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const int32_t *__restrict__ cnt, const float *__restrict__ feat, const float *__restrict__ val,
+    const float *__restrict__ diag, int n_cells, int n_k, const float *__restrict__ kpts, int max_sweeps,
+    float *__restrict__ evals, float2 *__restrict__ evecs, int *__restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char shb[];
+  const int w = threadIdx.x >> 5;
+  const int64_t mi = (int64_t)blockIdx.x * kWarpsEigh + w;
+  if (mi >= (int64_t)n_cells * n_k) return;  // whole warp: no block barrier follows
+  unsigned char *base = shb + (size_t)w * eigh_warp_bytes(n);
+  float2 *A = reinterpret_cast<float2 *>(base);
+  float2 *V = A + n * (n + 1);
+  float4 *rot = reinterpret_cast<float4 *>(base + (size_t)2 * n * (n + 1) * sizeof(float2));
+  float2 *nd = reinterpret_cast<float2 *>(rot + 16);
+  int *pa = reinterpret_cast<int *>(nd + 16);
+  int *pb = pa + 16;
+  const int c = (int)(mi / n_k), q = (int)(mi % n_k);
+  const int err = bloch_solve_warp(A, V, rot, nd, pa, pb, n, c, q, rows_per_cell, slice_ptr, col, cnt, feat, val,
+                                   diag, n_k, kpts, max_sweeps, evals, evecs);
+  if (err) atomicOr(flags, err);
+}
+
+// Eq. 3 over all (cell, k, band) items: stats = {S, sum w D^2, L}; the
+// terms in FP32, their sums in FP64
+__global__ void __launch_bounds__(1024) band_loss_kernel(int items, int nb, const float *__restrict__ E,
                                                          const float *__restrict__ Eref,
                                                          const float *__restrict__ w, float *__restrict__ dLdE,
                                                          double *__restrict__ stats) {
   __shared__ double red[2][32];
-  __shared__ double S_all;
+  __shared__ float S_all;
   double s1 = 0.0, s2 = 0.0;
-  for (int64_t x = threadIdx.x; x < items; x += blockDim.x) {
-    const double d = (double)E[x] - (double)Eref[x];
-    const double wb = (double)w[x % nb];
-    s1 += wb * fabs(d);
-    s2 += wb * d * d;
+  for (int x = threadIdx.x; x < items; x += blockDim.x) {
+    const float d = E[x] - Eref[x];
+    const float wb = w[x % nb];
+    s1 += (double)(wb * fabsf(d));
+    s2 += (double)(wb * d * d);
   }
   for (int o = 16; o > 0; o >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -610,18 +815,18 @@ __global__ void __launch_bounds__(1024) band_loss_kernel(int64_t items, int nb, 
       a += red[0][k];
       b += red[1][k];
     }
-    S_all = a;
+    S_all = (float)a;
     stats[0] = a;
     stats[1] = b;
     stats[2] = a * a + b;
   }
   __syncthreads();
-  const double S = S_all;
-  for (int64_t x = threadIdx.x; x < items; x += blockDim.x) {
-    const double d = (double)E[x] - (double)Eref[x];
-    const double wb = (double)w[x % nb];
-    const double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
-    dLdE[x] = (float)(2.0 * S * wb * sg + 2.0 * wb * d);
+  const float S2 = 2.0f * S_all;
+  for (int x = threadIdx.x; x < items; x += blockDim.x) {
+    const float d = E[x] - Eref[x];
+    const float wb = w[x % nb];
+    const float sg = d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f);
+    dLdE[x] = wb * fmaf(S2, sg, 2.0f * d);
   }
 }
 
@@ -835,7 +1040,7 @@ extern "C" tb_status tb_env_backward(int64_t n, const int64_t *slice_ptr, const 
                                                         species, params, g_val, g_diag,
                                                         partial + (int64_t)ge * kNP);
   TB_CHECK_LAUNCH();
-  partial_sum_kernel<<<(kNP + 255) / 256, 256, 0, st>>>(partial, ge + gr, grad);
+  partial_sum_kernel<<<(kNP + 31) / 32, 256, 0, st>>>(partial, ge + gr, grad);
   TB_CHECK_LAUNCH();
   return TB_OK;
 }
@@ -852,12 +1057,21 @@ extern "C" tb_status tb_bloch_bands(int32_t n_cells, int32_t n_atoms, int32_t ro
   TB_REQUIRE(slice_ptr && col && cnt && feat && val && kpts && evals && evecs && flags,
              "tb_bloch_bands: null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = eigh_smem(n_atoms);
-  TB_CUDA(cudaFuncSetAttribute(bloch_eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t), st));
-  bloch_eigh_kernel<<<dim3(n_k, n_cells), 256, smem, st>>>(n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, val,
-                                                          diag, n_k, kpts, max_sweeps, evals,
-                                                          static_cast<float2 *>(evecs), flags);
+  if (n_atoms <= 32) {
+    const size_t smem = kWarpsEigh * eigh_warp_bytes(n_atoms);
+    TB_CUDA(cudaFuncSetAttribute(bloch_eigh_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t mats = (int64_t)n_cells * n_k;
+    bloch_eigh_warp_kernel<<<(unsigned)((mats + kWarpsEigh - 1) / kWarpsEigh), 32 * kWarpsEigh, smem, st>>>(
+        n_atoms, rows_per_cell, slice_ptr, col, cnt, feat, val, diag, n_cells, n_k, kpts, max_sweeps, evals,
+        static_cast<float2 *>(evecs), flags);
+  } else {
+    const size_t smem = eigh_smem(n_atoms);
+    TB_CUDA(cudaFuncSetAttribute(bloch_eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bloch_eigh_kernel<<<dim3(n_k, n_cells), 256, smem, st>>>(n_atoms, rows_per_cell, slice_ptr, col, cnt, feat,
+                                                            val, diag, n_k, kpts, max_sweeps, evals,
+                                                            static_cast<float2 *>(evecs), flags);
+  }
   TB_CHECK_LAUNCH();
   int32_t h = 0;
   TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -872,8 +1086,9 @@ extern "C" tb_status tb_band_loss(int64_t n_spectra, int32_t n_bands, const floa
                                   const float *weights, float *dLdE, double *stats, void *stream) {
   TB_REQUIRE(n_spectra >= 1 && n_bands >= 1 && evals && e_ref && weights && dLdE && stats,
              "tb_band_loss: bad argument");
-  band_loss_kernel<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(n_spectra * n_bands, n_bands, evals, e_ref,
-                                                                     weights, dLdE, stats);
+  TB_REQUIRE(n_spectra * (int64_t)n_bands < (int64_t(1) << 31), "tb_band_loss: more than 2^31 - 1 band energies");
+  band_loss_kernel<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>((int)(n_spectra * n_bands), n_bands, evals,
+                                                                     e_ref, weights, dLdE, stats);
   TB_CHECK_LAUNCH();
   return TB_OK;
 }
