@@ -11,7 +11,7 @@ Modules and the passages they follow (arXiv 2509.06525):
 
 * neighbors    -- N(i) of Eq. 1: all periodic images within r_cut.
 * teacher      -- the analytic environment-dependent pz teacher model that
-                  replaces the DFT labels (Sec. 2.3) for this build.
+                  replaces the DFT labels (Sec. 2.3) here.
 * descriptors  -- Chebyshev radial functions f_k, the species-mixed C_n and
                   the node feature v_i of Eq. 2.
 * mlp          -- the SiLU MLP of Sec. 3 (forward, backward), the loss of

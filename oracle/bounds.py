@@ -10,7 +10,7 @@ The Chebyshev expansion of the LSQT method needs the spectrum of H inside
   tridiagonal T_k whose extreme eigenvalues (Ritz values theta_min,
   theta_max) are found by Sturm-sequence bisection.
 
-Combination used by this build:
+Combination used here:
   delta = 0.01 (theta_max - theta_min)
   E_max = min(G_max, theta_max + delta),  E_min = max(G_min, theta_min - delta)
   a = (E_max - E_min) / (2 - eps),  b = (E_max + E_min) / 2,  eps = 0.01.

@@ -4,7 +4,7 @@
     C_n(r)  = sum_k c^{Z_i Z_j}_{nk} f_k(r)
     v_i     = sum_{j in N(i)} C_n(r_ij)                     (node feature)
 
-The per-edge MLP input used by this build (the reduced form of e_ij in Eq. 2,
+The per-edge input of the per-pair MLP (the reduced form of e_ij in Eq. 2,
 with the environment network taken as the identity) is the 32-vector
 
     x_ij = [ C(r_ij), v_i, v_j, C(r_ij) * (v_i + v_j) ]

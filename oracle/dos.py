@@ -1,6 +1,6 @@
 """KPM density of states, Eq. 4.  TEST INFRASTRUCTURE ONLY.
 
-Eq. 4 defines rho(E) = (2 / Omega) Tr[delta(E - H)].  This build returns the
+Eq. 4 defines rho(E) = (2 / Omega) Tr[delta(E - H)].  The library returns the
 density per orbital and per eV, (1/N) Tr[delta(E - H)], which integrates to 1;
 multiplying by 2 (spin) and by N / Omega gives Eq. 4.
 

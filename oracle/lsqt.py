@@ -6,7 +6,7 @@ Eq. 3 (sigma) gives the conductivity at energy E and correlation time t as
     sigma(E, t) = (2 e^2 / Omega) int_0^t Tr[ delta(E - H) Re(V V(tau)) ] dtau,
     V(tau) = exp(i H tau / hbar) V exp(-i H tau / hbar),
 
-with the states propagated in steps of 0.1 fs (Sec. 2.4).  This build
+with the states propagated in steps of 0.1 fs (Sec. 2.4).  The library
 returns the per-orbital quantities
 
     C(E, tau)   = (1/N) Re Tr[ delta(E - H) V V(tau) ]        (A^2 / fs^2 / eV)
