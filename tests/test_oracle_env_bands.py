@@ -196,3 +196,48 @@ def test_training_gradient_finite_difference():
     Lm = oe.cell_loss_and_grad(flat - h * direction, cells, kpts, E_ref, w, eps0)[0]
     fd = (Lp - Lm) / (2 * h)
     assert abs(fd - g @ direction) <= 1e-5 * max(1.0, abs(fd))
+
+
+def test_hand_wired_network():
+    """A network with single nonzero paths, evaluated by hand with the
+    exponential: pins which index is output and input in every layer, the
+    product C * m of Eq. 2, the sigma/pi assignment of the SK factors and the
+    species pick of the onsite network."""
+    import math
+
+    def silu(x):
+        return x / (1.0 + math.exp(-x))
+
+    p = {name: np.zeros(shape) for name, shape in oe.ENV_LAYOUT}
+    p["We1"][0, 1] = 1.0          # z1[0] = u[1]
+    p["We2"][2, 0] = 1.0          # m[2] = h1[0]
+    p["be2"][2] = 0.25
+    p["Wh1"][3, 2] = 1.0          # z2[3] = e[2] = C[2] m[2]
+    p["Wh2"][4, 3] = 1.0          # z3[4] = h2[3]
+    p["Wh3"][0, 4] = 2.0          # y_sigma = 2 h3[4] + 0.5
+    p["Wh3"][1, 4] = 3.0          # y_pi = 3 h3[4] - 1
+    p["bh3"][:] = (0.5, -1.0)
+    p["Wo1"][5, 6] = 1.0          # z[5] = v[6]
+    p["Wo2"][1, 5] = 2.0          # out[1] = 2 h[5] + 0.1
+    p["bo2"][1] = 0.1
+    flat = oe.pack(p)
+    C = np.zeros((1, 8))
+    C[0, 2] = 1.5
+    u = np.zeros((1, 8))
+    u[0, 1] = 2.0
+    nz2 = np.array([0.25])
+    t, _ = oe.hopping_forward(flat, C, u, nz2)
+    # every other unit has a zero pre-activation and silu(0) = 0
+    h1_0 = silu(2.0)
+    m_2 = h1_0 + 0.25
+    e_2 = 1.5 * m_2
+    h2_3 = silu(e_2)
+    h3_4 = silu(h2_3)
+    y_sigma = 2.0 * h3_4 + 0.5
+    y_pi = 3.0 * h3_4 - 1.0
+    assert t[0] == pytest.approx(0.25 * y_sigma + 0.75 * y_pi, rel=1e-14)
+    v = np.zeros((2, 8))
+    v[:, 6] = 1.5
+    eps, _ = oe.onsite_forward(flat, v, np.array([1, 0]), np.array([0.0, -0.3, 0.0]))
+    assert eps[0] == pytest.approx(-0.3 + 0.1 + 2.0 * silu(1.5), rel=1e-14)
+    assert eps[1] == 0.0          # species 0 reads out[0] = 0
