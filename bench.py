@@ -486,6 +486,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "per_vector": {"value": value * R, "unit": "atom*moments*vectors/s",
+                       "note": "N M R / t: the same step counted per random vector"},
         "config": {"workload": args.workload + ("" if (args.M is None and args.R is None) else "-override"),
                    "atoms": n_atoms, "moments": M, "random_vectors": R,
                    "hamiltonian": args.hamiltonian, "kpm_precision": "complex FP32, FP64 moment sums",
