@@ -102,9 +102,16 @@ def band_weights(n_bands: int, active: Tuple[int, int], n_spectra: int) -> torch
 
 
 class BandTrainer:
-    """One training step = model H -> bands -> Eq. 3 -> gradient -> AdamW."""
+    """One training step = model H -> bands -> Eq. 3 -> gradient -> AdamW.
 
-    def __init__(self, model: g.EnvModel, batch: CellBatch, max_sweeps: int = 30):
+    With a process group of several ranks and n_cells_total given, `batch`
+    holds this rank's block of the cells (distributed.block_shard order) and
+    each step exchanges the band energies and the gradients
+    (distributed.band_step); the weights then count the residuals of the
+    whole batch."""
+
+    def __init__(self, model: g.EnvModel, batch: CellBatch, max_sweeps: int = 30, group=None,
+                 n_cells_total: Optional[int] = None):
         self.model, self.batch, self.max_sweeps = model, batch, max_sweeps
         dev = batch.feat.device
         self.grad = torch.empty(g.ENV_NPARAM, dtype=torch.float32, device=dev)
@@ -113,8 +120,41 @@ class BandTrainer:
         self.g_val = torch.zeros(max(batch.total, 1), dtype=torch.float32, device=dev)
         self.g_diag = torch.zeros(batch.n_rows, dtype=torch.float32, device=dev)
         self.stats = torch.zeros(3, dtype=torch.float64, device=dev)
+        self.group = group
+        self.n_cells_total = batch.n_cells if n_cells_total is None else int(n_cells_total)
+        self.sharded = False
+        if n_cells_total is not None:
+            import torch.distributed as dist
+            self.sharded = dist.is_initialized() and dist.get_world_size(group) > 1
+        if self.sharded:
+            from .distributed import gather_blocks
+            self.e_ref_all = gather_blocks(batch.e_ref, self.n_cells_total, group)
+
+    def _loss_and_grad_sharded(self, weights: torch.Tensor):
+        from .distributed import band_step
+        b, m = self.batch, self.model
+
+        def forward_local():
+            val, diag = g.env_forward(b.n_rows, b.slice_ptr, b.cnt, b.feat, b.v, b.species, m, b.total)
+            return bands_of(b, val, diag, self.max_sweeps)
+
+        def loss_all(e_all, e_ref_all):
+            dLdE, _ = g.band_loss(e_all, e_ref_all, weights, stats=self.stats)
+            return dLdE, self.stats
+
+        def backward_local(evecs, dLdE):
+            g.band_gradient(b.n_cells, b.n_atoms, b.rows_per_cell, b.slice_ptr, b.col, b.cnt, b.feat, b.kpts, evecs,
+                            dLdE, b.total, g_val=self.g_val, g_diag=self.g_diag)
+            return g.env_backward(b.n_rows, b.slice_ptr, b.cnt, b.total, b.feat, b.v, b.species, m, self.g_val,
+                                  self.g_diag, grad=self.grad, workspace=self.ws)
+
+        stats, grad = band_step(forward_local, loss_all, backward_local, self.e_ref_all, self.n_cells_total,
+                                self.group)
+        return stats, grad, None
 
     def loss_and_grad(self, weights: torch.Tensor):
+        if self.sharded:
+            return self._loss_and_grad_sharded(weights)
         b, m = self.batch, self.model
         val, diag = g.env_forward(b.n_rows, b.slice_ptr, b.cnt, b.feat, b.v, b.species, m, b.total)
         evals, evecs = bands_of(b, val, diag, self.max_sweeps)
@@ -132,12 +172,14 @@ class BandTrainer:
 
 
 def train_bands(model: g.EnvModel, batch: CellBatch, schedule: List[Tuple[int, Tuple[int, int]]],
-                lr: float = 3e-3, lr_min: float = 3e-4, log_every: int = 25):
+                lr: float = 3e-3, lr_min: float = 3e-4, log_every: int = 25, group=None,
+                n_cells_total: Optional[int] = None):
     """Band-expansion schedule: a list of (steps, (lo, hi)) stages, each
     fitting bands lo..hi-1 with a cosine-decayed learning rate.  Returns the
-    loss history [(step, band window, L)]."""
-    tr = BandTrainer(model, batch)
-    n_spec = batch.n_cells * batch.kpts.shape[0]
+    loss history [(step, band window, L)].  group / n_cells_total: cells
+    sharded over ranks (BandTrainer)."""
+    tr = BandTrainer(model, batch, group=group, n_cells_total=n_cells_total)
+    n_spec = tr.n_cells_total * batch.kpts.shape[0]
     hist = []
     k = 0
     for steps, window in schedule:

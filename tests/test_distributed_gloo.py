@@ -93,3 +93,86 @@ def test_two_gloo_ranks_reproduce_the_single_rank_ensemble(tmp_path, r_total):
     np.testing.assert_allclose(mu_all, mu_ref, rtol=0, atol=1e-14)
     with open(out + ".t") as f:
         assert float(f.read()) == 2.5
+
+
+# ---------------------------------------------------------------- band-energy training
+
+def _band_cells(n_cells):
+    from oracle import env_bands as oe
+    from oracle import neighbors as onb
+    from paper_2509_06525_gb300 import synth
+    cm = synth.descriptor_mixing("identity").astype(float)
+    cells = []
+    for s in synth.band_training_cells(n_cells, 900):
+        indptr, idx, d = onb.neighbors(s.positions, s.box, s.pbc, 3.0)
+        C, u, nz2, v = oe.edge_inputs(s.species, indptr, idx, d, cm, 3.0)
+        cells.append(dict(n=s.n, species=s.species, indptr=indptr, indices=idx, dvec=d, C=C, u=u, nz2=nz2, v=v))
+    return cells
+
+
+def _band_problem(n_cells):
+    from paper_2509_06525_gb300 import synth
+    cells = _band_cells(n_cells)
+    kpts = synth.band_kgrid(synth.graphene_rect(2, 3).box, 2, 1)
+    rng = np.random.default_rng(5)
+    e_ref = rng.normal(0.0, 1.0, (n_cells, len(kpts), cells[0]["n"]))
+    w = np.linspace(1.0, 0.5, cells[0]["n"]) / (n_cells * len(kpts))
+    flat = synth.init_env_mlp(7, -1.0).astype(float)
+    return cells, kpts, e_ref, w, flat
+
+
+def _band_worker(rank, world, port, n_cells, out_path):
+    """Each rank computes the model and bands of its cells with the oracle;
+    band_step exchanges the band energies and the gradients."""
+    from oracle import env_bands as oe
+    from paper_2509_06525_gb300.distributed import band_step, block_shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        cells, kpts, e_ref, w, flat = _band_problem(n_cells)
+        first, count = block_shard(n_cells, rank, world)
+        mine = cells[first:first + count]
+
+        def forward_local():
+            E, ctx = [], []
+            for c in mine:
+                t, hc = oe.hopping_forward(flat, c["C"], c["u"], c["nz2"])
+                e, oc = oe.onsite_forward(flat, c["v"], c["species"], np.zeros(3))
+                Ec, psi = oe.bands(c["n"], c["indptr"], c["indices"], c["dvec"], t, e, kpts)
+                E.append(Ec)
+                ctx.append((hc, oc, psi))
+            return torch.tensor(np.stack(E)), ctx
+
+        def loss_all(E_all, E_ref_all):
+            L, dLdE = oe.band_loss(E_all.numpy(), E_ref_all.numpy(), w)
+            return torch.tensor(dLdE), torch.tensor([L], dtype=torch.float64)
+
+        def backward_local(ctx, dLdE):
+            g = np.zeros(oe.ENV_NPARAM)
+            for c, (hc, oc, psi), d in zip(mine, ctx, dLdE.numpy()):
+                gt, ge = oe.band_gradient(c["indptr"], c["indices"], c["dvec"], kpts, psi, d)
+                g += oe.hopping_backward(flat, hc, gt) + oe.onsite_backward(flat, oc, ge)
+            return torch.tensor(g)
+
+        stats, grad = band_step(forward_local, loss_all, backward_local, torch.tensor(e_ref), n_cells)
+        if rank == 0:
+            np.save(out_path, np.concatenate([stats.numpy(), grad.numpy()]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("n_cells,world", [(4, 2), (5, 2), (5, 3)])
+def test_gloo_ranks_reproduce_the_single_process_band_step(tmp_path, n_cells, world):
+    """Cells sharded over 2 or 3 gloo ranks (even and uneven shards): the
+    loss of Eq. 3 and its parameter gradient equal one oracle evaluation
+    over the whole batch."""
+    from oracle import env_bands as oe
+    out = str(tmp_path / "band.npy")
+    mp.start_processes(_band_worker, args=(world, _free_port(), n_cells, out), nprocs=world, join=True,
+                       start_method="spawn")
+    got = np.load(out)
+    cells, kpts, e_ref, w, flat = _band_problem(n_cells)
+    L, grad, _ = oe.cell_loss_and_grad(flat, cells, kpts, e_ref, w, np.zeros(3))
+    assert got[0] == pytest.approx(L, rel=1e-12)
+    np.testing.assert_allclose(got[1:], grad, rtol=1e-10, atol=1e-12 * np.max(np.abs(grad)))
