@@ -1021,7 +1021,7 @@ extern "C" tb_status tb_env_backward(int64_t n, const int64_t *slice_ptr, const 
                                      size_t workspace_bytes, void *stream) {
   tb_status s = check_sell(n, slice_ptr, cnt);
   if (s != TB_OK) return s;
-  TB_REQUIRE(total_elements >= 1 && feat && v && species && params && g_val && g_diag && grad && workspace,
+  TB_REQUIRE(total_elements >= 0 && feat && v && species && params && g_val && g_diag && grad && workspace,
              "tb_env_backward: bad argument");
   if (workspace_bytes < tb_env_backward_workspace_size(n, total_elements))
     return fail(TB_ERR_WORKSPACE, "tb_env_backward: workspace too small");
