@@ -456,6 +456,16 @@ def run_ours(args):
     kind = args.hamiltonian
     lib = g.lib()
 
+    # autotune the Chebyshev step on this workload's own matrix (untimed),
+    # then the warm-up steps with the chosen shape
+    pipe.step(pipe.pos, pipe.spc, kind, torch.float32, record=False)
+    H0, bd0 = pipe.last["H"], pipe.last["bd"]
+    best, shape_ms = g.kpm_autotune(H0, bd0.a, bd0.b, w["R"], doubling=pipe.doubling, reps=20)
+    autotune = {"shape": best, "shape_desc": g.kpm_shape_info(w["R"], torch.float32, best),
+                "ms_per_step": shape_ms, "default_shape_ms": shape_ms[0],
+                "shapes": [g.kpm_shape_info(w["R"], torch.float32, k) for k in range(len(shape_ms))]}
+    del H0, bd0
+
     # device-resident timed region
     sampler = ClockSampler(local)
     pipe.kpm_ms.clear()
@@ -503,6 +513,7 @@ def run_ours(args):
                      "kpm_share_of_step": kpm_frac_of_step},
         "gpu_launches": launches,
         "clocks": clocks,
+        "autotune": autotune,
     }
 
     if training is not None:

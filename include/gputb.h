@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 6
+#define GPUTB_ABI_VERSION 7
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -134,16 +134,67 @@ TB_API int64_t tb_launch_count(void);
  * ------------------------------------------------------------------- */
 TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_t precision);
 
-/* Tuning hook for the Chebyshev-step kernel used by kpm_moments and
- * kpm_moments_noalloc: 0 = automatic (the bulk-copy pipeline where several
- * threads share a row and its tile geometry fits, else direct loads),
- * 1 = direct loads, 2 = pipeline where it fits, 3 = two Chebyshev steps per
- * cooperative launch with the matrix read once (temporal blocking; doubling
- * mode of kpm_moments only, other calls use single steps).  Process-wide;
- * every variant computes the same moments up to the order of the partial
- * sums (each variant is bitwise reproducible).  Query workspace sizes after
- * setting it. */
-TB_API tb_status tb_kpm_set_variant(int32_t variant);
+/* ---------------------------------------------------------------------
+ * Step shapes and their autotuner (no counterpart in the paper: launch
+ * configuration of this library's Chebyshev-step kernel).
+ *
+ * For each (R, precision) the library carries a fixed list of compiled
+ * launch shapes of the Chebyshev step; entry 0 is the default.  A shape is
+ * the kernel family (direct loads, or a bulk-copy ring of `stages` tiles in
+ * shared memory), the complex numbers each thread moves (R divided by it =
+ * threads per row), the resident CTAs per SM its register budget is sized
+ * for, and the rows one CTA processes per tile.  Every shape computes the
+ * same moments up to the grouping of the FP64 partial sums (differences of
+ * a few ulps), and each shape on its own is bitwise reproducible.
+ *
+ * kpm_moments, kpm_moments_noalloc, kpm_moments_batched and lsqt_vac use,
+ * for (precision, R, mode, n): the shape forced for every size (n = 0 entry)
+ * if one is set, else the entry of n's size class floor(log2 n), else 0.
+ * The table is process-wide and guarded by a mutex; workspace sizes cover
+ * every shape, so a workspace queried once stays valid when the table
+ * changes.
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int32_t pipelined;            /* 1: bulk-copy ring, 0: direct loads         */
+  int32_t complex_per_thread;   /* complex numbers per thread (R / threads per row) */
+  int32_t stages;               /* ring depth (0 for direct loads)           */
+  int32_t min_blocks;           /* resident CTAs per SM of the register budget */
+  int32_t rows_per_tile;        /* rows a CTA processes per tile             */
+} tb_step_shape;
+
+/* Number of shapes for (R, precision); 0 if R is unsupported. */
+TB_API int32_t tb_kpm_shape_count(int32_t R, int32_t precision);
+/* Description of shape `shape`; TB_ERR_INVALID_ARG if out of range. */
+TB_API tb_status tb_kpm_shape_info(int32_t R, int32_t precision, int32_t shape, tb_step_shape *out);
+/* Set the table entry of n's size class (n > 0) or the forced entry (n = 0)
+ * for mode TB_KPM_DIRECT, TB_KPM_DOUBLING or both (mode = -1); shape = -1
+ * removes the entry. */
+TB_API tb_status tb_kpm_set_shape(int64_t n, int32_t R, int32_t precision, int32_t mode, int32_t shape);
+/* Remove every entry (all calls use shape 0 again). */
+TB_API tb_status tb_kpm_clear_shapes(void);
+/* The shape a call with these arguments would use; -1 if unsupported. */
+TB_API int32_t tb_kpm_get_shape(int64_t n, int32_t R, int32_t precision, int32_t mode);
+/* CTAs of one Chebyshev-step launch of `shape` over n rows in `mode` (the
+ * occupancy-limited grid: min(tiles, resident CTAs per SM x SMs)); each CTA
+ * processes ceil(tiles / grid) or fewer tiles of rows_per_tile rows.  Queries
+ * the current device; -1 on bad arguments or a failed query. */
+TB_API int32_t tb_kpm_shape_grid(int64_t n, int32_t R, int32_t precision, int32_t mode, int32_t shape);
+
+/* Autotuner: on the caller's matrix (arguments as kpm_moments), draws the
+ * random phases, forms v1 with shape 0, then for every shape of
+ * (R, precision) runs 2 warm-up and `reps` timed steps of the recursion in
+ * `mode` (the same kernels, operands and in-place update as kpm_moments;
+ * CUDA events on `stream`).  ms_per_step (host float [ms_capacity] or NULL)
+ * receives the mean time per step of each shape; *best_shape the fastest,
+ * which is also stored as the table entry of n's size class for this mode.
+ *   reps        1 .. 10000
+ *   workspace   >= kpm_moments_workspace_size(n, 2, R, precision) bytes
+ * Synchronises `stream`; TB_ERR_TIMEOUT if a pipeline wait gave up. */
+TB_API tb_status tb_kpm_autotune(int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                                 const void *val, const void *diag, int32_t precision, double a,
+                                 double b, int32_t R, int32_t mode, int32_t reps, void *workspace,
+                                 size_t workspace_bytes, void *stream, int32_t *best_shape,
+                                 float *ms_per_step, int32_t ms_capacity);
 
 TB_API tb_status kpm_moments(int64_t n, const int64_t *slice_ptr, const int32_t *col,
                       const void *val, const void *diag, int32_t precision,
@@ -227,14 +278,13 @@ TB_API tb_status kpm_dos(const double *mu_r, int32_t R, int32_t M, int32_t kerne
 
 
 /* Test hook (no counterpart in the paper): runs the bounded wait of the
- * two-step kernel (which = 0: stage-1 flags) or of the pipelined step
- * (which = 1: an mbarrier phase) on flags / a phase that nothing completes,
- * with a limit of `polls` polls.  Returns TB_ERR_TIMEOUT when the wait gave
- * up (the expected outcome; the context stays usable), TB_OK if it completed.
- *   workspace   device, >= 512 bytes (zeroed by the call)
+ * pipelined step (an mbarrier phase) on a phase that nothing completes, with
+ * a limit of `polls` polls.  Returns TB_ERR_TIMEOUT when the wait gave up
+ * (the expected outcome; the context stays usable), TB_OK if it completed.
+ *   workspace   device, >= 256 bytes (zeroed by the call)
  * Synchronises `stream`. */
-TB_API tb_status tb_debug_wait_timeout(int32_t which, int64_t polls, void *workspace,
-                                       size_t workspace_bytes, void *stream);
+TB_API tb_status tb_debug_wait_timeout(int64_t polls, void *workspace, size_t workspace_bytes,
+                                       void *stream);
 
 /* ---------------------------------------------------------------------
  * Velocity-autocorrelation conductivity, Eq. 3 (sigma) of Sec. 2.4:

@@ -1,18 +1,24 @@
-// Chebyshev-step machinery shared by the KPM moments (kpm.cu) and the VAC
+// Chebyshev-step machinery shared by the KPM moments (kpm_*.cu) and the VAC
 // conductivity (lsqt.cu): the direct-load and bulk-copy-pipeline step
-// kernels, their launch geometry, the moment partial flush and the
-// fixed-order moment reduction.  Everything below has internal linkage in
-// each translation unit that includes it.
+// kernels, templated on their launch shape; the table of candidate shapes
+// per (precision, R) that the autotuner chooses from; the moment partial
+// flush and the fixed-order moment reduction.  Everything below the kpmdev
+// declarations has internal linkage in each translation unit that includes
+// it.
 #pragma once
+
+#include <algorithm>
+#include <type_traits>
+#include <utility>
 
 #include "kpm_common.cuh"
 
 namespace gputb {
 namespace kpmdev {
-// kernel variant for the Chebyshev step: 0 = choose automatically,
-// 1 = direct loads, 2 = bulk-copy pipeline, 3 = two steps per launch
-// (doubling mode; set with tb_kpm_set_variant); defined in kpm.cu
-extern int g_kpm_variant;
+// Shape of the Chebyshev step chosen for a call (see kpm_shapes.cu): an
+// explicitly forced shape, else the autotuned one for the size class of n,
+// else 0 (the default shape of every candidate list).
+int chosen_shape(int precision, int R, int mode, int64_t n);
 }  // namespace kpmdev
 
 namespace {
@@ -41,25 +47,6 @@ constexpr int kBatchTile = 256;
 // with the row's own v_{n-1} and v0 loads hoisted above them; wider rows take
 // a plain loop.
 constexpr int kFastW = 16;
-
-// Resident CTAs per SM that the register budget is sized for (minimum
-// blocks of __launch_bounds__), chosen by timing on GB300: the kernels are
-// latency bound, so more resident warps pay where the tighter budget costs
-// no spills.  FP32 with one vector (1e8-atom workload): 4 CTAs (64
-// registers), 15% faster than 3; FP32 pipeline with two complex numbers per
-// thread and R >= 8: 4 CTAs, 5% faster than the compiler's own choice.
-// FP64 vectors keep 2 CTAs (no spills).
-template <typename real, int R, int CPT>
-constexpr int direct_min_blocks() {
-  return sizeof(real) == 8 ? 2 : (R == 1 ? 4 : (CPT >= 4 ? 2 : 3));
-}
-template <typename real, int R, int CPT>
-constexpr int bulk_min_blocks() {
-#ifndef TB_BULK_MINB_R8
-#define TB_BULK_MINB_R8 4
-#endif
-  return (sizeof(real) == 4 && CPT == 2 && R >= 8) ? TB_BULK_MINB_R8 : 1;
-}
 
 // Write the CTA's partial sums as entry `idx` of the moment slot (and of the
 // next slot for the doubling pair), then restart the accumulators.  Every
@@ -103,8 +90,72 @@ __device__ __forceinline__ void segment_boundary(DotAcc<real> (&acc)[CPT], DotAc
   }
 }
 
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) cheb_step_kernel(
+// The row's product y = sum_s h_s x[j_s] (CPT complex numbers of the
+// thread's share of the R vectors) with the slot loads issued first.
+template <typename real, typename valT, int R, int CPT>
+__device__ __forceinline__ void row_product_direct(const int32_t *__restrict__ col, const valT *__restrict__ val,
+                                                   const real *__restrict__ x, int64_t e0, int w, int part,
+                                                   real (&y)[2 * CPT]) {
+  if (w <= kFastW) {
+    int32_t j[kFastW];
+    real h[kFastW];
+#pragma unroll
+    for (int s = 0; s < kFastW; ++s) {
+      if (s < w) {
+        j[s] = __ldcs(col + e0 + 32 * s);
+        h[s] = static_cast<real>(__ldcs(val + e0 + 32 * s));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kFastW; ++s) {
+      if (s < w) {
+        real xv[2 * CPT];
+        ld_gather<real, CPT>(x + ((int64_t)j[s] * R + part * CPT) * 2, xv);
+#pragma unroll
+        for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h[s], xv[c], y[c]);
+      }
+    }
+  } else {
+    int64_t e = e0;
+    for (int s = 0; s < w; ++s, e += 32) {
+      const int32_t jj = __ldcs(col + e);
+      const real hh = static_cast<real>(__ldcs(val + e));
+      real xv[2 * CPT];
+      ld_gather<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
+#pragma unroll
+      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
+    }
+  }
+}
+
+// The row's tail shared by both kernels: the diagonal term, the output
+// (stored with evict-first) and the dot accumulation.
+template <typename real, int CPT, bool FIRST, bool DBL>
+__device__ __forceinline__ void row_finish(real (&y)[2 * CPT], const real (&xi)[2 * CPT], const real (&p)[2 * CPT],
+                                           const real (&z)[2 * CPT], real d, real alpha, real *out,
+                                           DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT]) {
+#pragma unroll
+  for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
+  real o[2 * CPT];
+#pragma unroll
+  for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
+  st_stream<real, CPT>(out, o);
+  if (DBL) {
+    // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
+      acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
+    }
+  } else {
+    // Re(conj(v0) * o) = z.re o.re + z.im o.im
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
+  }
+}
+
+template <typename real, typename valT, int R, int CPT, int MINB, bool FIRST, bool DBL, bool SEG>
+__global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x,
     const real *prev, const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha,
@@ -131,60 +182,13 @@ __global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) che
       const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
       const int64_t sb = __ldg(slice_ptr + (i >> 5));
       const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
-      const int64_t e0 = sb + (i & 31);
       real y[2 * CPT];
 #pragma unroll
       for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
-      if (w <= kFastW) {
-        int32_t j[kFastW];
-        real h[kFastW];
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            j[s] = __ldcs(col + e0 + 32 * s);
-            h[s] = static_cast<real>(__ldcs(val + e0 + 32 * s));
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            real xv[2 * CPT];
-            ld_gather<real, CPT>(x + ((int64_t)j[s] * R + part * CPT) * 2, xv);
-#pragma unroll
-            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h[s], xv[c], y[c]);
-          }
-        }
-      } else {
-        int64_t e = e0;
-        for (int s = 0; s < w; ++s, e += 32) {
-          const int32_t jj = __ldcs(col + e);
-          const real hh = static_cast<real>(__ldcs(val + e));
-          real xv[2 * CPT];
-          ld_gather<real, CPT>(x + ((int64_t)jj * R + part * CPT) * 2, xv);
-#pragma unroll
-          for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(hh, xv[c], y[c]);
-        }
-      }
+      row_product_direct<real, valT, R, CPT>(col, val, x, sb + (i & 31), w, part, y);
       real xi[2 * CPT];
       ld_gather<real, CPT>(x + off, xi);
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
-      real o[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
-      st_stream<real, CPT>(out + off, o);
-      if (DBL) {
-        // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
-          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
-        }
-      } else {
-        // Re(conj(v0) * o) = z.re o.re + z.im o.im
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
-      }
+      row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
     if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head);
   }
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) che
 // ---------------------------------------------------------------------------
 // Pipelined variant: the streamed operands of a tile of TR rows -- the tile's
 // SELL slices of col and val (contiguous), and its rows of v_{n-1} and v0 --
-// are moved by one elected thread with cp.async.bulk into a kStages-deep
+// are moved by one elected thread with cp.async.bulk into a STAGES-deep
 // shared-memory ring whose stages complete on mbarriers (transaction
 // counts).  All warps compute on one stage while the next ones are in
 // flight, and the neighbour gathers take their indices from shared memory,
@@ -203,13 +207,6 @@ __global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) che
 // and val.  Every wait is bounded: on timeout the CTA drains its own copies
 // (bounded again), raises flags[0] |= 4 and returns.
 // ---------------------------------------------------------------------------
-#ifndef TB_KPM_STAGES
-#define TB_KPM_STAGES 3
-#endif
-// pipeline depth (tuning macro): measured on GB300 at 10M atoms, R = 8, doubling
-// mode: 3 stages 375 ms, 4 stages 392 ms (the extra shared memory costs
-// resident CTAs)
-constexpr int kStages = TB_KPM_STAGES;
 constexpr long long kWaitPolls = 1ll << 21;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -244,7 +241,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode)
-template <typename real, typename valT, int R, int CPT, int NV = 2>
+template <typename real, typename valT, int R, int CPT, int STAGES, int NV = 2>
 struct BulkGeom {
   static constexpr int TPR = R / CPT;
   static constexpr int TR = kBlock / TPR;                       // rows per tile
@@ -253,17 +250,17 @@ struct BulkGeom {
   static constexpr size_t kValBytes = kEl * sizeof(valT);
   static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
   static constexpr size_t kStageBytes = kColBytes + kValBytes + NV * kVecBytes;
-  static constexpr size_t kSmem = 128 + kStages * kStageBytes;  // mbarriers first
-  static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024;
+  static constexpr size_t kSmem = 128 + STAGES * kStageBytes;  // mbarriers first
+  static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024 && STAGES >= 2 && STAGES <= 8;
 };
 
-template <typename real, typename valT, int R, int CPT, bool FIRST, bool DBL, bool SEG>
-__global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_step_bulk_kernel(
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, bool FIRST, bool DBL, bool SEG>
+__global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
     int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
-  using G = BulkGeom<real, valT, R, CPT, DBL ? 1 : 2>;
+  using G = BulkGeom<real, valT, R, CPT, STAGES, DBL ? 1 : 2>;
   constexpr int TPR = G::TPR, TR = G::TR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -285,7 +282,7 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
   auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
 
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(full + st, 1);
+    for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -293,7 +290,7 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
   // producer: stream the operands of local tile number kk into its stage
   auto issue = [&](int64_t kk) {
     const int64_t tile = tile_of(kk);
-    const int st = static_cast<int>(kk % kStages);
+    const int st = static_cast<int>(kk % STAGES);
     const int64_t r0 = tile * TR;
     const int64_t k0 = r0 >> 5;
     const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
@@ -318,14 +315,14 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
   int64_t run_head = t_begin;
   int64_t issued = 0;
   if (threadIdx.x == 0)
-    for (; issued < my_tiles && issued < kStages; ++issued) issue(issued);
+    for (; issued < my_tiles && issued < STAGES; ++issued) issue(issued);
 
   DotAcc<real> acc[CPT], acc2[CPT];
   bool ok = true;
   int64_t kk = 0;
   for (; kk < my_tiles; ++kk) {
-    const int st = static_cast<int>(kk % kStages);
-    const uint32_t parity = static_cast<uint32_t>((kk / kStages) & 1);
+    const int st = static_cast<int>(kk % STAGES);
+    const uint32_t parity = static_cast<uint32_t>((kk / STAGES) & 1);
     ok = __syncthreads_and(mbar_wait_bounded(full + st, parity)) != 0;
     if (!ok) break;
     const int64_t tile = tile_of(kk);
@@ -373,24 +370,7 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
       const int64_t off = (i * R + part * CPT) * 2;
       real xi[2 * CPT];
       ld_gather<real, CPT>(x + off, xi);
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
-      real o[2 * CPT];
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) o[c] = FIRST ? alpha * y[c] : fma(alpha, y[c], -p[c]);
-      st_stream<real, CPT>(out + off, o);
-      if (DBL) {
-        // <v_n|v_n> and Re <v_n|v_{n+1}> for the doubling identities
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          acc[c].add(xi[2 * c], xi[2 * c + 1], xi[2 * c], xi[2 * c + 1]);
-          acc2[c].add(xi[2 * c], xi[2 * c + 1], o[2 * c], o[2 * c + 1]);
-        }
-      } else {
-        // Re(conj(v0) * o) = z.re o.re + z.im o.im
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c].add(z[2 * c], z[2 * c + 1], o[2 * c], o[2 * c + 1]);
-      }
+      row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
     if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
     __syncthreads();  // every thread is done with this stage
@@ -401,7 +381,7 @@ __global__ void __launch_bounds__(kBlock, bulk_min_blocks<real, R, CPT>()) cheb_
     if (threadIdx.x == 0) {
       atomicOr(flags, 4);
       for (int64_t q = kk; q < issued; ++q)
-        mbar_wait_bounded(full + q % kStages, static_cast<uint32_t>((q / kStages) & 1));
+        mbar_wait_bounded(full + q % STAGES, static_cast<uint32_t>((q / STAGES) & 1));
     }
     __syncthreads();
 #pragma unroll
@@ -434,104 +414,208 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
   else if (bound > 0.0 && fabs(mu) > bound) atomicOr(flags, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Launch shapes.  A shape fixes the kernel family (direct loads or the
+// bulk-copy ring), the complex numbers per thread CPT (so TPR = R / CPT
+// threads share a row), the ring depth and the resident CTAs per SM that the
+// register budget is sized for (the minimum blocks of __launch_bounds__).
+// Entry 0 of every list is the default; the autotuner (tb_kpm_autotune)
+// times the whole list on the caller's matrix.  Every shape computes the
+// same moments up to the grouping of the partial sums, and each is bitwise
+// reproducible.
+// ---------------------------------------------------------------------------
+struct StepShape {
+  int pipelined;   // 1: bulk-copy ring, 0: direct loads
+  int cpt;         // complex numbers per thread
+  int stages;      // ring depth (pipelined only)
+  int minb;        // resident CTAs per SM of the register budget
+};
 
-template <typename real, typename valT, int R>
-struct StepKit {
-  // complex numbers per thread, chosen by measurement on GB300 (10M-atom
-  // graphene): FP32 R = 4 -> 4 (two 16-byte accesses), other R >= 2 -> 2
-  // (one 16-byte access), R = 1 -> 1; FP64 2 when R >= 2, else 1
-  static constexpr int CPT = sizeof(real) == 4 ? (R == 4 ? 4 : (R >= 2 ? 2 : 1)) : (R >= 2 ? 2 : 1);
+template <typename real, int R> struct Shapes;
+// FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
+// one thread per row for R <= 4 (R = 1 with 4 CTAs of 64 registers was 15%
+// faster than 3), the 3-stage ring with 16-byte accesses (CPT = 2) and 4 CTAs
+// where four or more threads share a row.
+template <> struct Shapes<float, 1> {
+  static constexpr StepShape at[] = {{0, 1, 0, 4}, {0, 1, 0, 3}, {0, 1, 0, 5}};
+};
+template <> struct Shapes<float, 2> {
+  static constexpr StepShape at[] = {{0, 2, 0, 3}, {0, 1, 0, 4}};
+};
+template <> struct Shapes<float, 4> {
+  static constexpr StepShape at[] = {{0, 4, 0, 2}, {0, 2, 0, 3}, {1, 2, 3, 2}};
+};
+template <> struct Shapes<float, 8> {
+  static constexpr StepShape at[] = {{1, 2, 3, 4}, {1, 2, 2, 4}, {1, 2, 4, 4}, {1, 1, 3, 4},
+                                     {0, 2, 0, 3}, {0, 1, 0, 4}, {1, 4, 3, 2}};
+};
+template <> struct Shapes<float, 16> {
+  static constexpr StepShape at[] = {{1, 2, 3, 4}, {1, 2, 2, 4}, {1, 4, 3, 2}, {0, 2, 0, 3}};
+};
+template <> struct Shapes<float, 32> {
+  static constexpr StepShape at[] = {{0, 2, 0, 3}, {1, 4, 3, 2}, {0, 4, 0, 2}};
+};
+// FP64 vectors (the FP64 pipe, not HBM, limits these on GB300).
+template <> struct Shapes<double, 1> {
+  static constexpr StepShape at[] = {{0, 1, 0, 2}, {0, 1, 0, 3}};
+};
+template <> struct Shapes<double, 2> {
+  static constexpr StepShape at[] = {{0, 2, 0, 2}};
+};
+template <> struct Shapes<double, 4> {
+  static constexpr StepShape at[] = {{0, 2, 0, 2}, {1, 2, 3, 1}};
+};
+template <> struct Shapes<double, 8> {
+  static constexpr StepShape at[] = {{1, 2, 3, 1}, {1, 2, 3, 2}, {0, 2, 0, 2}};
+};
+template <> struct Shapes<double, 16> {
+  static constexpr StepShape at[] = {{1, 2, 3, 1}, {0, 2, 0, 2}};
+};
+template <> struct Shapes<double, 32> {
+  static constexpr StepShape at[] = {{0, 2, 0, 2}};
+};
+
+template <typename real, int R>
+constexpr int shape_count() {
+  return static_cast<int>(sizeof(Shapes<real, R>::at) / sizeof(StepShape));
+}
+
+// Everything that depends on one shape: occupancy-derived grid, shared
+// memory opt-in and the launches.
+template <typename real, typename valT, int R, int CPT, int PIPE, int STAGES, int MINB>
+struct ShapeKit {
   static constexpr int TPR = R / CPT;
-  static constexpr int RPB = kBlock / TPR;
-  using G = BulkGeom<real, valT, R, CPT>;
+  static constexpr int RPB = kBlock / TPR;   // rows per tile (both kernels)
   template <bool DBL>
-  using GB = BulkGeom<real, valT, R, CPT, DBL ? 1 : 2>;   // the stage size of each mode
-  static constexpr int64_t kRowPad = 256;   // vector blocks hold whole tiles
+  using GB = BulkGeom<real, valT, R, CPT, PIPE ? STAGES : 2, DBL ? 1 : 2>;
+  static_assert(R % CPT == 0 && TPR <= 32, "bad shape");
+  static_assert(!PIPE || (GB<true>::kOk && GB<false>::kOk), "pipelined shape does not fit");
 
-  // the pipeline wins where several threads share a row (R >= 8 in FP32 on
-  // GB300, measured); with one thread per row the direct kernel is faster
-  static bool use_bulk() {
-    if (!G::kOk || g_kpm_variant == 1) return false;
-    return g_kpm_variant == 2 || TPR >= 4;
+  template <bool FIRST, bool DBL, bool SEG>
+  static void opt_in() {
+    if (PIPE)
+      cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, FIRST, DBL, SEG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<DBL>::kSmem);
   }
-
-  // resident CTAs x SMs (doubling mode streams one vector less per stage,
-  // so its pipelined kernel may fit more CTAs)
-  static int grid_for(int64_t n, bool dbl = false) {
-    static int per_sm_direct = 0, per_sm_bulk[2] = {0, 0};
-    if (use_bulk()) {
-      int &pb = per_sm_bulk[dbl ? 1 : 0];
-      if (pb == 0) {
-        int b = 0;
-        cudaError_t e;
-        if (dbl) {
-          cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<true>::kSmem);
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &b, cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>, kBlock, GB<true>::kSmem);
-        } else {
-          cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<false>::kSmem);
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &b, cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>, kBlock, GB<false>::kSmem);
-        }
-        pb = (e != cudaSuccess || b <= 0) ? 1 : b;
-      }
-      const int64_t need = (n + G::TR - 1) / G::TR;
-      const int64_t cap = (int64_t)pb * sm_count();
-      return static_cast<int>(need < cap ? need : cap);
-    }
-    if (per_sm_direct == 0) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cheb_step_kernel<real, valT, R, CPT, false, false, false>, kBlock, 0) !=
-              cudaSuccess ||
-          b <= 0)
-        b = 4;
-      per_sm_direct = b;
-    }
-    const int64_t need = (n + RPB - 1) / RPB;
-    const int64_t cap = (int64_t)per_sm_direct * sm_count();
-    return static_cast<int>(need < cap ? need : cap);
-  }
-
   // opt every pipelined instantiation into its shared-memory size (before any
   // stream capture)
   static void prepare() {
-    if (!use_bulk()) return;
-    const int s1 = (int)GB<true>::kSmem, s2 = (int)GB<false>::kSmem;
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, true, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, false, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, false, true, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+    static bool done = false;
+    if (done) return;
+    opt_in<true, false, false>();
+    opt_in<true, true, false>();
+    opt_in<false, false, false>();
+    opt_in<false, true, false>();
+    opt_in<true, false, true>();
+    opt_in<true, true, true>();
+    opt_in<false, false, true>();
+    opt_in<false, true, true>();
+    done = true;
   }
-
+  // resident CTAs per SM (doubling mode streams one vector less per stage, so
+  // its pipelined kernel may fit more CTAs)
+  static int per_sm(bool dbl) {
+    static int cache[2] = {0, 0};
+    int &c = cache[dbl ? 1 : 0];
+    if (c == 0) {
+      int b = 0;
+      cudaError_t e;
+      prepare();
+      if (PIPE && dbl)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, false, true, false>, kBlock,
+            GB<true>::kSmem);
+      else if (PIPE)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, false, false, false>, kBlock,
+            GB<false>::kSmem);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, cheb_step_kernel<real, valT, R, CPT, MINB, false, false, false>, kBlock, 0);
+      c = (e != cudaSuccess || b <= 0) ? MINB : b;
+    }
+    return c;
+  }
+  static int grid(int64_t n, bool dbl) {
+    const int64_t need = (n + RPB - 1) / RPB;
+    const int64_t cap = (int64_t)per_sm(dbl) * sm_count();
+    return static_cast<int>(need < cap ? need : cap);
+  }
   template <bool FIRST, bool DBL, bool SEG>
   static tb_status step(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                         const valT *diag, const real *x, const real *prev, const real *v0, real *out,
                         double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
                         const BatchTables &bt, cudaStream_t st) {
-    if (use_bulk())
-      cheb_step_bulk_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, GB<DBL>::kSmem, st>>>(
-          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt);
+    if (PIPE)
+      cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, FIRST, DBL, SEG>
+          <<<grid, kBlock, GB<DBL>::kSmem, st>>>(n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha,
+                                                 shift, flags, slot_stride, bt);
     else
-      cheb_step_kernel<real, valT, R, CPT, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
+      cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
     TB_CHECK_LAUNCH();
     return TB_OK;
   }
+};
 
+template <typename real, typename valT, int R, int I>
+using KitOf = ShapeKit<real, valT, R, Shapes<real, R>::at[I].cpt, Shapes<real, R>::at[I].pipelined,
+                       Shapes<real, R>::at[I].stages, Shapes<real, R>::at[I].minb>;
+
+// Call f(KitOf<..., I>{}) for the runtime shape index `id`.
+template <typename real, typename valT, int R, int I = 0, typename F>
+auto visit_shape(int id, F &&f) -> decltype(f(KitOf<real, valT, R, 0>{})) {
+  if constexpr (I + 1 < shape_count<real, R>()) {
+    if (id != I) return visit_shape<real, valT, R, I + 1>(id, std::forward<F>(f));
+  }
+  return f(KitOf<real, valT, R, I>{});
+}
+
+// The step interface used by the KPM and conductivity runners: every call
+// names its shape (an index into Shapes<real, R>, validated by the caller).
+template <typename real, typename valT, int R>
+struct StepKit {
+  static constexpr int kShapes = shape_count<real, R>();
+  // complex numbers per thread of the default shape (the conductivity's
+  // own per-row kernels use it)
+  static constexpr int CPT = Shapes<real, R>::at[0].cpt;
+  static constexpr int64_t kRowPad = 256;   // vector blocks hold whole tiles of every shape
+
+  static int grid(int shape, int64_t n, bool dbl) {
+    return visit_shape<real, valT, R>(shape, [&](auto k) { return decltype(k)::grid(n, dbl); });
+  }
+  static int rows_per_block(int shape) {
+    return visit_shape<real, valT, R>(shape, [](auto k) { return decltype(k)::RPB; });
+  }
+  static bool pipelined(int shape) { return Shapes<real, R>::at[shape].pipelined != 0; }
+  // the largest grid and the smallest block over every shape and mode, so that
+  // a workspace sized once fits whichever shape a later call takes
+  static int max_grid(int64_t n) {
+    int g = 1;
+    for (int s = 0; s < kShapes; ++s) g = std::max(g, std::max(grid(s, n, false), grid(s, n, true)));
+    return g;
+  }
+  static int min_rows_per_block() {
+    int r = kBlock;
+    for (int s = 0; s < kShapes; ++s) r = std::min(r, rows_per_block(s));
+    return r;
+  }
+  static void prepare(int shape) {
+    visit_shape<real, valT, R>(shape, [](auto k) {
+      decltype(k)::prepare();
+      return 0;
+    });
+  }
+  template <bool FIRST, bool DBL, bool SEG>
+  static tb_status step(int shape, int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col,
+                        const valT *val, const valT *diag, const real *x, const real *prev, const real *v0,
+                        real *out, double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
+                        const BatchTables &bt, cudaStream_t st) {
+    return visit_shape<real, valT, R>(shape, [&](auto k) {
+      return decltype(k)::template step<FIRST, DBL, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                                         partial, alpha, shift, flags, slot_stride, bt, st);
+    });
+  }
 };
 
 }  // namespace

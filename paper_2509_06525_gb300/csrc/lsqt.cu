@@ -112,8 +112,15 @@ __global__ void __launch_bounds__(kBlock) velocity_apply_kernel(int64_t n, const
 // else: t_{k+1} = 2 H~ x - t_{k-1} written over io (which holds t_{k-1}),
 // acc += c t_{k+1}.  H~ x = alpha_0 (sum_s val x[col] + (diag_i - shift) x_i)
 // with alpha = 1/a (FIRST) or 2/a.
+// register budget of the propagation kernel: 4 resident CTAs (64 registers)
+// with one FP32 complex number per thread, 3 for FP32 with more, 2 for FP64
+template <typename real, int R, int CPT>
+constexpr int propagate_min_blocks() {
+  return sizeof(real) == 8 ? 2 : (R == 1 ? 4 : (CPT >= 4 ? 2 : 3));
+}
+
 template <typename real, typename valT, int R, int CPT, bool FIRST>
-__global__ void __launch_bounds__(kBlock, direct_min_blocks<real, R, CPT>()) propagate_term_kernel(
+__global__ void __launch_bounds__(kBlock, propagate_min_blocks<real, R, CPT>()) propagate_term_kernel(
     int64_t n, const int64_t *__restrict__ sp, const int32_t *__restrict__ col, const valT *__restrict__ val,
     const valT *__restrict__ diag, const real *__restrict__ x, real *io, real *__restrict__ acc, real alpha,
     real shift, real c0r, real c0i, real cr, real ci) {
@@ -255,9 +262,9 @@ __global__ void vac_series_kernel(const double *__restrict__ coef, int n_times, 
 }
 
 template <typename real, typename valT, int R>
-struct LsqtRunner : StepKit<real, valT, R> {
+struct LsqtRunner {
   using Kit = StepKit<real, valT, R>;
-  using Kit::CPT;
+  static constexpr int CPT = Kit::CPT;
   static constexpr int kVectors = 7;   // phi_L, phi_R, w, A, B, X1, ACC
 
   static int64_t padded_rows(int64_t n) { return (n + Kit::kRowPad - 1) / Kit::kRowPad * Kit::kRowPad; }
@@ -265,7 +272,7 @@ struct LsqtRunner : StepKit<real, valT, R> {
   static size_t workspace(int64_t n, int M) {
     Carver cv(nullptr, 0);
     for (int k = 0; k < kVectors; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
-    cv.take<double>((size_t)(M + 1) * Kit::grid_for(n) * R);
+    cv.take<double>((size_t)(M + 1) * Kit::max_grid(n) * R);
     cv.take<int>(4);
     return cv.used + 256;
   }
@@ -321,7 +328,9 @@ struct LsqtRunner : StepKit<real, valT, R> {
   static tb_status run(int64_t n, const int64_t *sp, const int32_t *col, const valT *val, const valT *diag,
                        const valT *vval, double a, double b, int M, uint64_t seed, int64_t r0, int n_steps,
                        double dt, double *mu_out, void *ws, size_t wsb, cudaStream_t st, double *ms_out) {
-    const int grid = Kit::grid_for(n);
+    const int shape = chosen_shape(sizeof(real) == 4 ? TB_F32 : TB_F64, R, TB_KPM_DIRECT, n);
+    if (shape < 0 || shape >= Kit::kShapes) return fail(TB_ERR_INVALID_ARG, "lsqt_vac: step shape %d", shape);
+    const int grid = Kit::grid(shape, n, false);
     const int64_t np = padded_rows(n);
     Carver cv(ws, wsb);
     real *vec[kVectors];
@@ -329,9 +338,9 @@ struct LsqtRunner : StepKit<real, valT, R> {
     double *partial = cv.take<double>((size_t)(M + 1) * grid * R);
     int *flags = cv.take<int>(4);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "lsqt_vac: workspace too small (%zu < %zu)", wsb, cv.used);
-    if (Kit::use_bulk() && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
+    if (Kit::pipelined(shape) && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
       return fail(TB_ERR_INVALID_ARG, "lsqt_vac: col and val must be 16-byte aligned");
-    Kit::prepare();
+    Kit::prepare(shape);
     real *phi_l = vec[0], *phi_r = vec[1], *w = vec[2], *A = vec[3], *B = vec[4], *x1 = vec[5], *acc = vec[6];
     std::vector<double> cr, ci;
     propagator_coefficients(a, b, dt, cr, ci);
@@ -358,13 +367,13 @@ struct LsqtRunner : StepKit<real, valT, R> {
                                                                                partial, inv_hbar);
       TB_CHECK_LAUNCH();
       // T_m(H~) phi_R, m = 1 .. M-1, dotted with w (A, B alternate; v_2 reads prev = phi_R)
-      s = Kit::template step<true, false, false>(grid, n, sp, col, val, diag, phi_r, nullptr, w, A, partial + ps,
+      s = Kit::template step<true, false, false>(shape, grid, n, sp, col, val, diag, phi_r, nullptr, w, A, partial + ps,
                                                  inv_a, shift, flags, ps, bt, st);
       for (int m = 2; m < M && s == TB_OK; ++m) {
         real *out = (m & 1) ? A : B;
         const real *x = (m & 1) ? B : A;
         const real *prev = (m == 2) ? phi_r : out;
-        s = Kit::template step<false, false, false>(grid, n, sp, col, val, diag, x, prev, w, out,
+        s = Kit::template step<false, false, false>(shape, grid, n, sp, col, val, diag, x, prev, w, out,
                                                     partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
       }
       if (s != TB_OK) break;

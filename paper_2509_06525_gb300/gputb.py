@@ -40,7 +40,14 @@ SIGNATURES = {
     "tb_last_error": (ctypes.c_char_p, []),
     "kpm_moments_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
     "tb_launch_count": (_c_i64, []),
-    "tb_kpm_set_variant": (_c_i32, [_c_i32]),
+    "tb_kpm_shape_count": (_c_i32, [_c_i32, _c_i32]),
+    "tb_kpm_shape_info": (_c_i32, [_c_i32, _c_i32, _c_i32, _c_vp]),
+    "tb_kpm_set_shape": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32, _c_i32]),
+    "tb_kpm_clear_shapes": (_c_i32, []),
+    "tb_kpm_get_shape": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32]),
+    "tb_kpm_shape_grid": (_c_i32, [_c_i64, _c_i32, _c_i32, _c_i32, _c_i32]),
+    "tb_kpm_autotune": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32, _c_i32,
+                                 _c_vp, _c_sz, _c_vp, _c_vp, _c_vp, _c_i32]),
     "kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32, _c_i32,
                              _c_u64, _c_i64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
     "kpm_moments_noalloc": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_dbl, _c_dbl, _c_i32,
@@ -56,7 +63,7 @@ SIGNATURES = {
     "sk_kpm_workspace_size": (_c_sz, [_c_i64, _c_i32]),
     "sk_kpm_moments": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_i64, _c_vp, _c_dbl, _c_dbl, _c_i32, _c_u64, _c_i64,
                                 _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
-    "tb_debug_wait_timeout": (_c_i32, [_c_i32, _c_i64, _c_vp, _c_sz, _c_vp]),
+    "tb_debug_wait_timeout": (_c_i32, [_c_i64, _c_vp, _c_sz, _c_vp]),
     "tb_velocity_values": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp,
                                     _c_vp, _c_vp]),
     "lsqt_vac_workspace_size": (_c_sz, [_c_i64, _c_i32, _c_i32, _c_i32]),
@@ -118,7 +125,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 6   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 7   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -136,6 +143,7 @@ def lib() -> ctypes.CDLL:
             raise ImportError(f"{LIB_PATH} has ABI {handle.tb_abi_version()}, the binding expects {ABI_VERSION}; "
                               "rebuild it with paper_2509_06525_gb300.build.build(force=True)")
         _lib = handle
+        load_tuned_shapes()
     return _lib
 
 
@@ -252,10 +260,135 @@ def kpm_moments_batched(mats, a, b, M: int, R: int, seed: int, doubling: bool = 
     return mu
 
 
-def kpm_set_variant(variant: int):
-    """0 = automatic, 1 = direct-load Chebyshev step, 2 = bulk-copy pipeline,
-    3 = two steps per launch with the matrix read once (doubling mode)."""
-    _check("tb_kpm_set_variant", lib().tb_kpm_set_variant(int(variant)))
+class StepShape(ctypes.Structure):
+    """tb_step_shape of include/gputb.h."""
+    _fields_ = [("pipelined", _c_i32), ("complex_per_thread", _c_i32), ("stages", _c_i32),
+                ("min_blocks", _c_i32), ("rows_per_tile", _c_i32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def _prec(dtype_or_prec) -> int:
+    return dtype_or_prec if isinstance(dtype_or_prec, int) else precision_of(dtype_or_prec)
+
+
+def kpm_shape_count(R: int, dtype) -> int:
+    """Number of compiled Chebyshev-step shapes for (R, precision)."""
+    return int(lib().tb_kpm_shape_count(int(R), _prec(dtype)))
+
+
+def kpm_shape_info(R: int, dtype, shape: int) -> dict:
+    out = StepShape()
+    _check("tb_kpm_shape_info", lib().tb_kpm_shape_info(int(R), _prec(dtype), int(shape), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def kpm_set_shape(n: int, R: int, dtype, mode: int, shape: int):
+    """Table entry of n's size class (n > 0) or the forced entry (n = 0);
+    mode 0 (direct), 1 (doubling) or -1 (both); shape -1 removes it."""
+    _check("tb_kpm_set_shape", lib().tb_kpm_set_shape(int(n), int(R), _prec(dtype), int(mode), int(shape)))
+
+
+def kpm_force_shape(R: int, dtype, shape: int):
+    """Every call with (R, precision) uses `shape` (-1 lifts the override)."""
+    kpm_set_shape(0, R, dtype, -1, shape)
+
+
+def kpm_clear_shapes():
+    _check("tb_kpm_clear_shapes", lib().tb_kpm_clear_shapes())
+
+
+def kpm_get_shape(n: int, R: int, dtype, doubling: bool = False) -> int:
+    return int(lib().tb_kpm_get_shape(int(n), int(R), _prec(dtype), KPM_DOUBLING if doubling else KPM_DIRECT))
+
+
+def kpm_shape_grid(n: int, R: int, dtype, doubling: bool, shape: int) -> int:
+    """CTAs of one step launch of `shape` over n rows (needs the GPU)."""
+    g = int(lib().tb_kpm_shape_grid(int(n), int(R), _prec(dtype), KPM_DOUBLING if doubling else KPM_DIRECT,
+                                    int(shape)))
+    if g < 1:
+        raise GputbError("tb_kpm_shape_grid", TB_ERR_INVALID_ARG, f"no grid for n={n} R={R} shape={shape}")
+    return g
+
+
+def kpm_autotune(H: SellMatrix, a: float, b: float, R: int, doubling: bool = False, reps: int = 20, stream=None,
+                 record: bool = True):
+    """Time every step shape of (R, H's precision) on H (tb_kpm_autotune);
+    the fastest becomes the table entry of H.n's size class.  Returns
+    (best shape, [ms per step of each shape]).  With `record`, the choice is
+    also written to the tuning cache file (see tuned_shapes_path)."""
+    L = lib()
+    prec = H.precision
+    count = kpm_shape_count(R, prec)
+    if count == 0:
+        raise GputbError("tb_kpm_autotune", TB_ERR_INVALID_ARG, f"unsupported R={R}")
+    need = L.kpm_moments_workspace_size(H.n, 2, R, prec)
+    ws = _workspace(need, H.col.device)
+    ms = (ctypes.c_float * count)()
+    best = _c_i32(-1)
+    mode = KPM_DOUBLING if doubling else KPM_DIRECT
+    st = L.tb_kpm_autotune(H.n, _ptr(H.slice_ptr), _ptr(H.col), _ptr(H.val), _ptr(H.diag), prec, float(a), float(b),
+                           int(R), mode, int(reps), _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best), ms,
+                           count)
+    _check("tb_kpm_autotune", st)
+    times = [float(v) for v in ms]
+    if record:
+        _record_tuned(H.n, R, prec, mode, int(best.value))
+    return int(best.value), times
+
+
+def tuned_shapes_path() -> str:
+    """JSON cache of autotuned shapes: $GPUTB_TUNE_CACHE, else
+    tuned_shapes.json beside the library."""
+    return os.environ.get("GPUTB_TUNE_CACHE") or os.path.join(_HERE, "tuned_shapes.json")
+
+
+def _gpu_name() -> str:
+    return torch.cuda.get_device_name(torch.cuda.current_device()) if torch.cuda.is_available() else "none"
+
+
+def _size_class(n: int) -> int:
+    return max(int(n), 1).bit_length() - 1
+
+
+def _record_tuned(n: int, R: int, prec: int, mode: int, shape: int):
+    import json
+    path = tuned_shapes_path()
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        data = {}
+    entries = data.setdefault(_gpu_name(), {})
+    key = f"p{prec}-R{R}-m{mode}-c{_size_class(n)}"
+    entries[key] = {"precision": prec, "R": int(R), "mode": int(mode), "n": int(n), "shape": int(shape),
+                    "desc": kpm_shape_info(R, prec, shape)}
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def load_tuned_shapes(path: Optional[str] = None) -> int:
+    """Apply the cached entries of this GPU model whose shape description
+    still matches the built library; returns how many were applied."""
+    import json
+    try:
+        with open(path or tuned_shapes_path()) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        return 0
+    applied = 0
+    for e in data.get(_gpu_name(), {}).values():
+        try:
+            if kpm_shape_info(e["R"], e["precision"], e["shape"]) != e["desc"]:
+                continue
+            kpm_set_shape(e["n"], e["R"], e["precision"], e["mode"], e["shape"])
+            applied += 1
+        except (GputbError, KeyError, TypeError):
+            continue
+    return applied
 
 
 def kpm_dos(mu_r: torch.Tensor, a: float, b: float, energy: torch.Tensor, kernel: str = "jackson",
@@ -324,12 +457,11 @@ def mlp_set_variant(variant: int):
     _check("tb_mlp_set_variant", lib().tb_mlp_set_variant(int(variant)))
 
 
-def debug_wait_timeout(which: int, polls: int, stream=None):
-    """Test hook: a bounded wait on flags (0) or an mbarrier phase (1) that
-    nothing completes; raises GputbError(TB_ERR_TIMEOUT) when it gives up."""
-    ws = torch.zeros(512, dtype=torch.uint8, device="cuda")
-    _check("tb_debug_wait_timeout", lib().tb_debug_wait_timeout(int(which), int(polls), _ptr(ws), 512,
-                                                                 _stream(stream)))
+def debug_wait_timeout(polls: int, stream=None):
+    """Test hook: a bounded wait on an mbarrier phase that nothing completes;
+    raises GputbError(TB_ERR_TIMEOUT) when it gives up."""
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    _check("tb_debug_wait_timeout", lib().tb_debug_wait_timeout(int(polls), _ptr(ws), 256, _stream(stream)))
 
 
 # ------------------------------------------------------------------ conductivity (Eq. 3 (sigma))

@@ -6,26 +6,38 @@ SLICE = 32
 
 
 def csr_to_sell(indptr, indices, values, n):
-    """(slice_ptr int64, col int32, val float64) with padding col = i, val = 0."""
-    indptr = np.asarray(indptr)
+    """(slice_ptr int64, col int32, val float64) with padding col = i, val = 0.
+
+    Slice k holds rows 32k .. 32k + 31 in `width_k` slots, slot-major: element
+    s of row i sits at slice_ptr[k] + (i mod 32) + 32 s.  Lanes past the last
+    row (n not a multiple of 32) keep col = 0, val = 0."""
+    indptr = np.asarray(indptr, np.int64)
+    indices = np.asarray(indices)
+    values = np.asarray(values, np.float64)
     counts = np.diff(indptr)
     n_slices = (n + SLICE - 1) // SLICE
-    widths = np.zeros(n_slices, np.int64)
-    for k in range(n_slices):
-        widths[k] = counts[k * SLICE:(k + 1) * SLICE].max(initial=0)
+    padded = np.zeros(n_slices * SLICE, np.int64)
+    padded[:n] = counts
+    widths = padded.reshape(n_slices, SLICE).max(axis=1)
     slice_ptr = np.zeros(n_slices + 1, np.int64)
     slice_ptr[1:] = np.cumsum(widths * SLICE)
-    col = np.zeros(slice_ptr[-1], np.int32)
-    val = np.zeros(slice_ptr[-1], np.float64)
-    for i in range(n):
-        k, lane = divmod(i, SLICE)
-        base = slice_ptr[k] + lane
-        row = slice(indptr[i], indptr[i + 1])
-        m = counts[i]
-        pos = base + SLICE * np.arange(widths[k])
-        col[pos] = i
-        col[pos[:m]] = indices[row]
-        val[pos[:m]] = values[row]
+    total = int(slice_ptr[-1])
+    col = np.zeros(total, np.int32)
+    val = np.zeros(total, np.float64)
+    if total == 0:
+        return slice_ptr, col, val
+    pos = np.arange(total, dtype=np.int64)
+    k = np.repeat(np.arange(n_slices, dtype=np.int64), widths * SLICE)
+    off = pos - slice_ptr[k]
+    row = k * SLICE + off % SLICE
+    s = off // SLICE
+    real = row < n
+    pos, row, s = pos[real], row[real], s[real]
+    col[pos] = row
+    used = s < counts[row]
+    src = indptr[row[used]] + s[used]
+    col[pos[used]] = indices[src]
+    val[pos[used]] = values[src]
     return slice_ptr, col, val
 
 

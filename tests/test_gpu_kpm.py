@@ -38,14 +38,21 @@ def gputb():
     return g
 
 
-@pytest.fixture(params=[1, 2, 3], ids=["direct", "pipelined", "paired"])
-def variant(request, gputb):
-    """Chebyshev-step kernels: one step per launch (direct loads or bulk-copy
-    pipeline), or two steps per launch (doubling mode only; the plain mode
-    falls back to single steps)."""
-    gputb.kpm_set_variant(request.param)
+@pytest.fixture(params=range(7), ids=lambda k: f"shape{k}")
+def shape(request, gputb):
+    """Every compiled launch shape of the Chebyshev step (direct loads, or a
+    bulk-copy ring of 2-4 stages, with 1, 2 or 4 complex numbers per thread
+    and several register budgets); a test skips the indices its
+    (R, precision) does not have."""
     yield request.param
-    gputb.kpm_set_variant(0)
+    gputb.kpm_clear_shapes()
+
+
+def use_shape(g, shape, R, dtype):
+    count = g.kpm_shape_count(R, dtype)
+    if shape >= count:
+        pytest.skip(f"R={R} {dtype} has {count} step shapes")
+    g.kpm_force_shape(R, dtype, shape)
 
 
 @pytest.fixture(params=[False, True], ids=["plain", "doubling"])
@@ -65,9 +72,10 @@ def cfg800():
     return s, indptr, idx, t, eps, H, a, b, w
 
 
-def test_fp64_moments_match_oracle(gputb, cfg800, variant, doubling):
+def test_fp64_moments_match_oracle(gputb, cfg800, shape, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
+    use_shape(gputb, shape, R, torch.float64)
     Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
     mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED, doubling=doubling).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
@@ -87,9 +95,10 @@ def test_doubling_odd_and_tiny_moment_counts(gputb, cfg800, M):
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
 
 
-def test_fp32_moments_match_oracle(gputb, cfg800, variant, doubling):
+def test_fp32_moments_match_oracle(gputb, cfg800, shape, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
+    use_shape(gputb, shape, R, torch.float32)
     Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float32)
     mu = gputb.kpm_moments(Hd, a, b, M, R, synth.KPM_SEED, doubling=doubling).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, M, R, synth.KPM_SEED)
@@ -120,9 +129,10 @@ def test_dos_matches_oracle(gputb, cfg800):
 
 @pytest.mark.parametrize("R", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_all_block_widths_ragged_rows(gputb, R, dtype, variant, doubling):
+def test_all_block_widths_ragged_rows(gputb, R, dtype, shape, doubling):
     """Ragged N (not a multiple of 32), an h-BN junction with onsite terms
-    (diag present), every supported R, both Chebyshev-step kernels."""
+    (diag present), every supported R, every Chebyshev-step shape."""
+    use_shape(gputb, shape, R, dtype)
     s = synth.hbn_graphene_junction(6, 7, sigma=0.1, seed=9)   # 168 atoms
     s.positions = s.positions[:-5].copy()                          # ragged, still periodic-valid
     s.species = s.species[:-5].copy()
@@ -139,7 +149,9 @@ def test_all_block_widths_ragged_rows(gputb, R, dtype, variant, doubling):
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33, 300])
-def test_tiny_systems(gputb, n, variant):
+@pytest.mark.parametrize("R", [2, 8])
+def test_tiny_systems(gputb, n, R, shape):
+    use_shape(gputb, shape, R, torch.float64)
     rng = np.random.default_rng(n)
     dense = np.zeros((n, n))
     if n > 1:
@@ -153,8 +165,8 @@ def test_tiny_systems(gputb, n, variant):
     H = oha.csr_hamiltonian(n, off.indptr, off.indices, off.data, onsite)
     a, b = 3.0, 0.1
     Hd = sell_matrix(off.indptr, off.indices, off.data, onsite, n, torch.float64)
-    mu = gputb.kpm_moments(Hd, a, b, 40, 2, 5).cpu().numpy()
-    _, mu_ref = okpm.kpm_moments(H, a, b, 40, 2, 5)
+    mu = gputb.kpm_moments(Hd, a, b, 40, R, 5).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, 40, R, 5)
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
 
 
@@ -166,7 +178,7 @@ def test_bounds_violation_reported(gputb, cfg800):
     assert ei.value.status in (gputb.TB_ERR_BOUNDS, gputb.TB_ERR_NOT_FINITE)
 
 
-def test_wide_rows_fall_back_inside_the_pipeline(gputb, variant):
+def test_wide_rows_fall_back_inside_the_pipeline(gputb, shape):
     """Rows wider than the pipeline's 16-slot tile budget (dense random
     pattern, 40 neighbours per row) take the direct-load path per tile."""
     import scipy.sparse as sp
@@ -202,14 +214,12 @@ def test_first_vector_blocks_compose_the_ensemble(gputb, cfg800, dtype, tol):
     assert np.max(np.abs(hi - ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
 
 
-@pytest.mark.parametrize("which", [0, 1], ids=["flag_wait", "mbarrier_wait"])
-def test_bounded_waits_give_up_and_leave_the_context_usable(gputb, cfg800, which):
-    """The waits of the two-step kernel (stage-1 flags) and of the pipelined
-    step (mbarrier phase) run on a flag / phase that nothing completes: they
-    must give up after their poll limit with TB_ERR_TIMEOUT, and the next
-    call must work."""
+def test_bounded_wait_gives_up_and_leaves_the_context_usable(gputb, cfg800):
+    """The wait of the pipelined step (an mbarrier phase) runs on a phase
+    that nothing completes: it must give up after its poll limit with
+    TB_ERR_TIMEOUT, and the next call must work."""
     with pytest.raises(gputb.GputbError) as ei:
-        gputb.debug_wait_timeout(which, 2000)
+        gputb.debug_wait_timeout(2000)
     assert ei.value.status == gputb.TB_ERR_TIMEOUT
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     Hd = sell_matrix(indptr, idx, t, eps, s.n, torch.float64)
