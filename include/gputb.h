@@ -130,7 +130,7 @@ TB_API int64_t tb_launch_count(void);
  * Synchronises `stream`, then checks |mu_r| <= 1 + 1e-6 (TB_ERR_BOUNDS)
  * and finiteness (TB_ERR_NOT_FINITE).  The pipelined step kernel bounds
  * every wait on its copy barriers and reports TB_ERR_TIMEOUT if one gives
- * up.  col and val must be 16-byte aligned.
+ * up.  col and val must be 16-byte aligned (diag too for shapes of kind 2).
  * ------------------------------------------------------------------- */
 TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_t precision);
 
@@ -155,11 +155,15 @@ TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_
  * changes.
  * ------------------------------------------------------------------- */
 typedef struct {
-  int32_t pipelined;            /* 1: bulk-copy ring, 0: direct loads         */
+  int32_t pipelined;            /* 0: direct loads; 1: bulk-copy ring of col, val
+                                   and vector rows; 2: ring that also stages the
+                                   slice offsets and the diagonal            */
   int32_t complex_per_thread;   /* complex numbers per thread (R / threads per row) */
   int32_t stages;               /* ring depth (0 for direct loads)           */
   int32_t min_blocks;           /* resident CTAs per SM of the register budget */
   int32_t rows_per_tile;        /* rows a CTA processes per tile             */
+  int32_t rows_per_thread;      /* rows each thread takes per tile           */
+  int32_t staged_vectors;       /* 1: v_{n-1} (and v0) rows go through the ring */
 } tb_step_shape;
 
 /* Number of shapes for (R, precision); 0 if R is unsupported. */

@@ -202,9 +202,12 @@ struct KpmRunner {
     return TB_OK;
   }
 
-  static tb_status check_alignment(int shape, const int32_t *col, const valT *val, const char *who) {
+  static tb_status check_alignment(int shape, const int32_t *col, const valT *val, const valT *diag,
+                                   const char *who) {
     if (Kit::pipelined(shape) && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
       return fail(TB_ERR_INVALID_ARG, "%s: col and val must be 16-byte aligned", who);
+    if (Kit::stages_diag(shape) && (reinterpret_cast<uintptr_t>(diag) & 15))
+      return fail(TB_ERR_INVALID_ARG, "%s: diag must be 16-byte aligned", who);
     return TB_OK;
   }
 
@@ -221,7 +224,7 @@ struct KpmRunner {
     double *partial = cv.take<double>((size_t)(M + 1) * grid * R);
     int *flags = cv.take<int>(4);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments: workspace too small (%zu < %zu)", ws_bytes, cv.used);
-    tb_status s = check_alignment(shape, col, val, "kpm_moments");
+    tb_status s = check_alignment(shape, col, val, diag, "kpm_moments");
     if (s != TB_OK) return s;
     Kit::prepare(shape);
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -320,7 +323,7 @@ struct KpmRunner {
     tb_status s = random_phases(0, Kit::grid(0, n, dbl), n, 42, 0, none, false, v0, partial, st);
     if (s != TB_OK) return s;
     for (int shape = 0; shape < Kit::kShapes; ++shape) {
-      s = check_alignment(shape, col, val, "tb_kpm_autotune");
+      s = check_alignment(shape, col, val, diag, "tb_kpm_autotune");
       if (s != TB_OK) return s;
     }
     Kit::prepare(0);
@@ -403,11 +406,13 @@ struct InfoOp {
     *ok = shape >= 0 && shape < Kit::kShapes;
     if (!*ok) return;
     const StepShape &sh = Shapes<real, R>::at[shape];
-    out->pipelined = sh.pipelined;
+    out->pipelined = sh.kind;
     out->complex_per_thread = sh.cpt;
-    out->stages = sh.pipelined ? sh.stages : 0;
+    out->stages = sh.kind ? sh.stages : 0;
     out->min_blocks = sh.minb;
     out->rows_per_tile = Kit::rows_per_block(shape);
+    out->rows_per_thread = sh.kind == 2 ? sh.rpt : 1;
+    out->staged_vectors = sh.kind == 0 ? 0 : sh.svec;
   }
 };
 template <typename real, typename valT, int R>

@@ -390,6 +390,212 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
 
+// ---------------------------------------------------------------------------
+// Second ring kernel: per tile of TR = RPT x (kBlock / TPR) rows the stage
+// also holds the tile's slice offsets (written by warp 0 from slice_ptr) and
+// its diagonal entries (bulk-copied with col and val), so that a consumer
+// thread issues no global load but its neighbour gathers, its own row of x
+// and (with STAGE_VEC = false) its streamed rows of v_{n-1} and v0.  Each
+// thread takes RPT rows per tile, which spreads the per-tile waits and
+// barriers over RPT rows.  Rows of slices at most 12 wide (graphene's 12
+// neighbours within 3 A) take a 12-slot unrolled body.
+// ---------------------------------------------------------------------------
+template <typename real, typename valT, int R, int CPT, int STAGES, int RPT, bool STAGE_VEC, int NV>
+struct Ring2Geom {
+  static constexpr int TPR = R / CPT;
+  static constexpr int TRW = kBlock / TPR;                      // rows per wave of the CTA
+  static constexpr int TR = TRW * RPT;                          // rows per tile
+  static constexpr int kSlices = TR / 32;
+  static constexpr int kEl = TR * kFastW;                       // SELL elements per stage
+  static constexpr size_t kHdrBytes = ((kSlices + 1) * 8 + 15) / 16 * 16;
+  static constexpr size_t kColBytes = kEl * sizeof(int32_t);
+  static constexpr size_t kValBytes = kEl * sizeof(valT);
+  static constexpr size_t kDiagBytes = (TR * sizeof(valT) + 15) / 16 * 16;
+  static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
+  static constexpr size_t kStageBytes = kHdrBytes + kColBytes + kValBytes + kDiagBytes + (STAGE_VEC ? NV : 0) * kVecBytes;
+  static constexpr size_t kSmem = 128 + STAGES * kStageBytes;
+  static constexpr bool kOk = TRW % 32 == 0 && kSmem <= 200 * 1024 && STAGES >= 2 && STAGES <= 8 && kSlices + 1 <= 32;
+};
+
+// y += sum over the row's slots (from shared memory) of h_s x[j_s]
+template <typename real, typename valT, int R, int CPT, int W>
+__device__ __forceinline__ void row_product_smem(const int32_t *cs, const valT *vs, const real *__restrict__ xp,
+                                                 int w, real (&y)[2 * CPT]) {
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    if (s < w) {
+      real xv[2 * CPT];
+      const real h = static_cast<real>(vs[32 * s]);
+      ld_gather<real, CPT>(xp + (int64_t)cs[32 * s] * (R * 2), xv);
+#pragma unroll
+      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+    }
+  }
+}
+
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int RPT, bool STAGE_VEC, bool FIRST,
+          bool DBL, bool SEG>
+__global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
+    int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
+    const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
+    int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
+  using G = Ring2Geom<real, valT, R, CPT, STAGES, RPT, STAGE_VEC, DBL ? 1 : 2>;
+  constexpr int TPR = G::TPR, TRW = G::TRW, TR = G::TR;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *ring = smem + 128;
+  auto s_hdr = [&](int st) { return reinterpret_cast<int64_t *>(ring + st * G::kStageBytes); };
+  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes + G::kHdrBytes); };
+  auto s_val = [&](int st) {
+    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes);
+  };
+  auto s_diag = [&](int st) {
+    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes);
+  };
+  auto s_vec = [&](int st, int q) {
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes +
+                                    G::kDiagBytes + q * G::kVecBytes);
+  };
+  const int64_t ntiles = (n + TR - 1) / TR;
+  const int64_t n_slices = (n + 31) >> 5;
+  const int part = threadIdx.x % TPR;
+  const int lr0 = threadIdx.x / TPR;
+  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
+  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
+  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
+  const real *xp = x + part * CPT * 2;   // this thread's components of every row of x
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // producer (warp 0): the tile's slice offsets into the header, then the
+  // bulk copies of col, val, diag (whole tiles) and the staged vector rows
+  auto issue = [&](int64_t kk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = tile_of(kk);
+    const int st = static_cast<int>(kk % STAGES);
+    const int64_t r0 = tile * TR;
+    const int64_t k0 = r0 >> 5;
+    const int64_t k1 = min(k0 + G::kSlices, n_slices);
+    int64_t off = 0;
+    if (lane <= G::kSlices) {
+      off = slice_ptr[min(k0 + lane, k1)];
+      s_hdr(st)[lane] = off;
+    }
+    const int64_t e0 = __shfl_sync(0xffffffffu, off, 0);
+    const int64_t e1 = __shfl_sync(0xffffffffu, off, G::kSlices);
+    __syncwarp();
+    if (lane == 0) {
+      const bool bulk = (e1 - e0) <= G::kEl;
+      const bool whole = r0 + TR <= n;
+      const uint32_t ebytes = bulk ? static_cast<uint32_t>(e1 - e0) : 0u;
+      uint32_t tx = 0;
+      if (bulk) tx += ebytes * static_cast<uint32_t>(sizeof(int32_t) + sizeof(valT));
+      if (diag && whole) tx += TR * sizeof(valT);
+      if (STAGE_VEC) tx += static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(full + st, tx);
+      if (bulk && ebytes > 0) {
+        bulk_g2s(s_col(st), col + e0, ebytes * sizeof(int32_t), full + st);
+        bulk_g2s(s_val(st), val + e0, ebytes * sizeof(valT), full + st);
+      }
+      if (diag && whole) bulk_g2s(s_diag(st), diag + r0, TR * sizeof(valT), full + st);
+      if (STAGE_VEC) {
+        const size_t voff = (size_t)r0 * R * 2;
+        if (!FIRST) bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+        if (!DBL) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+      }
+    }
+  };
+
+  const int64_t my_tiles =
+      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  int64_t run_head = t_begin;
+  int64_t issued = 0;
+  if (threadIdx.x < 32)
+    for (; issued < my_tiles && issued < STAGES; ++issued) issue(issued);
+
+  DotAcc<real> acc[CPT], acc2[CPT];
+  bool ok = true;
+  int64_t kk = 0;
+  for (; kk < my_tiles; ++kk) {
+    const int st = static_cast<int>(kk % STAGES);
+    const uint32_t parity = static_cast<uint32_t>((kk / STAGES) & 1);
+    ok = __syncthreads_and(mbar_wait_bounded(full + st, parity)) != 0;
+    if (!ok) break;
+    const int64_t tile = tile_of(kk);
+    const int64_t r0 = tile * TR;
+    const int64_t *hdr = s_hdr(st);
+    const int64_t e0 = hdr[0];
+    const bool bulk = (hdr[G::kSlices] - e0) <= G::kEl;
+    const bool whole = r0 + TR <= n;
+#pragma unroll 1
+    for (int q = 0; q < RPT; ++q) {
+      const int lr = lr0 + q * TRW;
+      const int64_t i = r0 + lr;
+      if (i < n) {
+        const int64_t off = (i * R + part * CPT) * 2;
+        real p[2 * CPT], z[2 * CPT];
+        if (STAGE_VEC) {
+          const int loff = (lr * R + part * CPT) * 2;
+          if (!FIRST) memcpy(p, s_vec(st, 0) + loff, sizeof(p));
+          if (!DBL) memcpy(z, s_vec(st, 1) + loff, sizeof(z));
+        } else {
+          if (!FIRST) ld_stream<real, CPT>(prev + off, p);
+          if (!DBL) ld_stream<real, CPT>(v0 + off, z);
+        }
+        real d = real(0);
+        if (diag) d = whole ? static_cast<real>(s_diag(st)[lr]) : static_cast<real>(__ldg(diag + i));
+        d -= shift;
+        const int64_t sb = hdr[lr >> 5];
+        const int w = static_cast<int>((hdr[(lr >> 5) + 1] - sb) >> 5);
+        real y[2 * CPT];
+#pragma unroll
+        for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
+        if (bulk) {
+          const int32_t *cs = s_col(st) + (sb - e0) + (lr & 31);
+          const valT *vs = s_val(st) + (sb - e0) + (lr & 31);
+          if (w <= 12) {
+            row_product_smem<real, valT, R, CPT, 12>(cs, vs, xp, w, y);
+          } else {
+#pragma unroll 1
+            for (int s2 = 0; s2 < w; ++s2) {
+              real xv[2 * CPT];
+              const real h = static_cast<real>(vs[32 * s2]);
+              ld_gather<real, CPT>(xp + (int64_t)cs[32 * s2] * (R * 2), xv);
+#pragma unroll
+              for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+            }
+          }
+        } else {
+          row_product_direct<real, valT, R, CPT>(col, val, x, sb + (i & 31), w, part, y);
+        }
+        real xi[2 * CPT];
+        ld_gather<real, CPT>(x + off, xi);
+        row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
+      }
+    }
+    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x < 32 && issued < my_tiles) issue(issued++);
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 4);
+      for (int64_t q = kk; q < issued; ++q)
+        mbar_wait_bounded(full + q % STAGES, static_cast<uint32_t>((q / STAGES) & 1));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
+  }
+  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
+}
+
 // mu_r[r, m] = (sum over CTAs in index order of partial[m, cta, r]) / n;
 // flags[0] |= 1 if |mu| > bound (when bound > 0), |= 2 if not finite.
 __device__ __forceinline__ double slot_sum(const double *__restrict__ partial, int grid, int R, int m, int r) {
@@ -425,11 +631,16 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 // reproducible.
 // ---------------------------------------------------------------------------
 struct StepShape {
-  int pipelined;   // 1: bulk-copy ring, 0: direct loads
+  int kind;        // 0: direct loads, 1: bulk-copy ring, 2: second ring (offsets, diagonal staged)
   int cpt;         // complex numbers per thread
-  int stages;      // ring depth (pipelined only)
+  int stages;      // ring depth (rings only)
   int minb;        // resident CTAs per SM of the register budget
+  int rpt;         // rows per thread per tile (second ring; 1 otherwise)
+  int svec;        // the ring stages v_{n-1} (and v0) rows in shared memory
 };
+constexpr StepShape D(int cpt, int minb) { return {0, cpt, 0, minb, 1, 0}; }
+constexpr StepShape P(int cpt, int stages, int minb) { return {1, cpt, stages, minb, 1, 1}; }
+constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) { return {2, cpt, stages, minb, rpt, svec}; }
 
 template <typename real, int R> struct Shapes;
 // FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
@@ -437,42 +648,43 @@ template <typename real, int R> struct Shapes;
 // faster than 3), the 3-stage ring with 16-byte accesses (CPT = 2) and 4 CTAs
 // where four or more threads share a row.
 template <> struct Shapes<float, 1> {
-  static constexpr StepShape at[] = {{0, 1, 0, 4}, {0, 1, 0, 3}, {0, 1, 0, 5}};
+  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5)};
 };
 template <> struct Shapes<float, 2> {
-  static constexpr StepShape at[] = {{0, 2, 0, 3}, {0, 1, 0, 4}};
+  static constexpr StepShape at[] = {D(2, 3), D(1, 4)};
 };
 template <> struct Shapes<float, 4> {
-  static constexpr StepShape at[] = {{0, 4, 0, 2}, {0, 2, 0, 3}, {1, 2, 3, 2}};
+  static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), Q(2, 3, 3, 1, 0)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {{1, 2, 3, 4}, {1, 2, 2, 4}, {1, 2, 4, 4}, {1, 1, 3, 4},
-                                     {0, 2, 0, 3}, {0, 1, 0, 4}, {1, 4, 3, 2}};
+  static constexpr StepShape at[] = {P(2, 3, 4),       P(2, 2, 4),       P(2, 4, 4),       D(2, 3),
+                                     Q(2, 3, 4, 1, 0), Q(2, 3, 3, 1, 0), Q(2, 3, 4, 2, 0), Q(2, 3, 3, 2, 0),
+                                     Q(2, 3, 4, 1, 1), Q(2, 3, 3, 1, 1)};
 };
 template <> struct Shapes<float, 16> {
-  static constexpr StepShape at[] = {{1, 2, 3, 4}, {1, 2, 2, 4}, {1, 4, 3, 2}, {0, 2, 0, 3}};
+  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 4, 1, 0), Q(2, 3, 3, 1, 0)};
 };
 template <> struct Shapes<float, 32> {
-  static constexpr StepShape at[] = {{0, 2, 0, 3}, {1, 4, 3, 2}, {0, 4, 0, 2}};
+  static constexpr StepShape at[] = {D(2, 3), P(4, 3, 2), D(4, 2), Q(4, 3, 2, 1, 0)};
 };
 // FP64 vectors (the FP64 pipe, not HBM, limits these on GB300).
 template <> struct Shapes<double, 1> {
-  static constexpr StepShape at[] = {{0, 1, 0, 2}, {0, 1, 0, 3}};
+  static constexpr StepShape at[] = {D(1, 2), D(1, 3)};
 };
 template <> struct Shapes<double, 2> {
-  static constexpr StepShape at[] = {{0, 2, 0, 2}};
+  static constexpr StepShape at[] = {D(2, 2)};
 };
 template <> struct Shapes<double, 4> {
-  static constexpr StepShape at[] = {{0, 2, 0, 2}, {1, 2, 3, 1}};
+  static constexpr StepShape at[] = {D(2, 2), P(2, 3, 1)};
 };
 template <> struct Shapes<double, 8> {
-  static constexpr StepShape at[] = {{1, 2, 3, 1}, {1, 2, 3, 2}, {0, 2, 0, 2}};
+  static constexpr StepShape at[] = {P(2, 3, 1), P(2, 3, 2), D(2, 2), Q(2, 3, 2, 1, 0)};
 };
 template <> struct Shapes<double, 16> {
-  static constexpr StepShape at[] = {{1, 2, 3, 1}, {0, 2, 0, 2}};
+  static constexpr StepShape at[] = {P(2, 3, 1), D(2, 2), Q(2, 3, 2, 1, 0)};
 };
 template <> struct Shapes<double, 32> {
-  static constexpr StepShape at[] = {{0, 2, 0, 2}};
+  static constexpr StepShape at[] = {D(2, 2)};
 };
 
 template <typename real, int R>
@@ -482,22 +694,39 @@ constexpr int shape_count() {
 
 // Everything that depends on one shape: occupancy-derived grid, shared
 // memory opt-in and the launches.
-template <typename real, typename valT, int R, int CPT, int PIPE, int STAGES, int MINB>
+template <typename real, typename valT, int R, int CPT, int KIND, int STAGES, int MINB, int RPT, int SVEC>
 struct ShapeKit {
   static constexpr int TPR = R / CPT;
-  static constexpr int RPB = kBlock / TPR;   // rows per tile (both kernels)
+  static constexpr int RPB = (kBlock / TPR) * (KIND == 2 ? RPT : 1);   // rows per tile
+  static constexpr int S = STAGES >= 2 ? STAGES : 2;
   template <bool DBL>
-  using GB = BulkGeom<real, valT, R, CPT, PIPE ? STAGES : 2, DBL ? 1 : 2>;
+  using GB = BulkGeom<real, valT, R, CPT, S, DBL ? 1 : 2>;
+  template <bool DBL>
+  using G2 = Ring2Geom<real, valT, R, CPT, S, RPT, SVEC != 0, DBL ? 1 : 2>;
+  template <bool DBL>
+  static constexpr size_t smem() {
+    return KIND == 1 ? GB<DBL>::kSmem : (KIND == 2 ? G2<DBL>::kSmem : 0);
+  }
   static_assert(R % CPT == 0 && TPR <= 32, "bad shape");
-  static_assert(!PIPE || (GB<true>::kOk && GB<false>::kOk), "pipelined shape does not fit");
+  static_assert(KIND != 1 || (GB<true>::kOk && GB<false>::kOk), "ring shape does not fit");
+  static_assert(KIND != 2 || (G2<true>::kOk && G2<false>::kOk), "second-ring shape does not fit");
 
   template <bool FIRST, bool DBL, bool SEG>
-  static void opt_in() {
-    if (PIPE)
-      cudaFuncSetAttribute(cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, FIRST, DBL, SEG>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB<DBL>::kSmem);
+  static auto kernel() {
+    if constexpr (KIND == 1)
+      return cheb_step_bulk_kernel<real, valT, R, CPT, S, MINB, FIRST, DBL, SEG>;
+    else if constexpr (KIND == 2)
+      return cheb_step_ring2_kernel<real, valT, R, CPT, S, MINB, RPT, SVEC != 0, FIRST, DBL, SEG>;
+    else
+      return cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG>;
   }
-  // opt every pipelined instantiation into its shared-memory size (before any
+  template <bool FIRST, bool DBL, bool SEG>
+  static void opt_in() {
+    if (KIND != 0)
+      cudaFuncSetAttribute(kernel<FIRST, DBL, SEG>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem<DBL>());
+  }
+  // opt every ring instantiation into its shared-memory size (before any
   // stream capture)
   static void prepare() {
     static bool done = false;
@@ -513,25 +742,17 @@ struct ShapeKit {
     done = true;
   }
   // resident CTAs per SM (doubling mode streams one vector less per stage, so
-  // its pipelined kernel may fit more CTAs)
+  // its ring kernels may fit more CTAs)
   static int per_sm(bool dbl) {
     static int cache[2] = {0, 0};
     int &c = cache[dbl ? 1 : 0];
     if (c == 0) {
       int b = 0;
-      cudaError_t e;
       prepare();
-      if (PIPE && dbl)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, false, true, false>, kBlock,
-            GB<true>::kSmem);
-      else if (PIPE)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, false, false, false>, kBlock,
-            GB<false>::kSmem);
-      else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, cheb_step_kernel<real, valT, R, CPT, MINB, false, false, false>, kBlock, 0);
+      const cudaError_t e =
+          dbl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel<false, true, false>(), kBlock, smem<true>())
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel<false, false, false>(), kBlock,
+                                                              smem<false>());
       c = (e != cudaSuccess || b <= 0) ? MINB : b;
     }
     return c;
@@ -546,21 +767,21 @@ struct ShapeKit {
                         const valT *diag, const real *x, const real *prev, const real *v0, real *out,
                         double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
                         const BatchTables &bt, cudaStream_t st) {
-    if (PIPE)
-      cheb_step_bulk_kernel<real, valT, R, CPT, PIPE ? STAGES : 2, MINB, FIRST, DBL, SEG>
-          <<<grid, kBlock, GB<DBL>::kSmem, st>>>(n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha,
-                                                 shift, flags, slot_stride, bt);
-    else
+    if constexpr (KIND == 0)
       cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
+    else
+      kernel<FIRST, DBL, SEG>()<<<grid, kBlock, smem<DBL>(), st>>>(n, slice_ptr, col, val, diag, x, prev, v0, out,
+                                                                  partial, alpha, shift, flags, slot_stride, bt);
     TB_CHECK_LAUNCH();
     return TB_OK;
   }
 };
 
 template <typename real, typename valT, int R, int I>
-using KitOf = ShapeKit<real, valT, R, Shapes<real, R>::at[I].cpt, Shapes<real, R>::at[I].pipelined,
-                       Shapes<real, R>::at[I].stages, Shapes<real, R>::at[I].minb>;
+using KitOf = ShapeKit<real, valT, R, Shapes<real, R>::at[I].cpt, Shapes<real, R>::at[I].kind,
+                       Shapes<real, R>::at[I].stages, Shapes<real, R>::at[I].minb, Shapes<real, R>::at[I].rpt,
+                       Shapes<real, R>::at[I].svec>;
 
 // Call f(KitOf<..., I>{}) for the runtime shape index `id`.
 template <typename real, typename valT, int R, int I = 0, typename F>
@@ -587,7 +808,9 @@ struct StepKit {
   static int rows_per_block(int shape) {
     return visit_shape<real, valT, R>(shape, [](auto k) { return decltype(k)::RPB; });
   }
-  static bool pipelined(int shape) { return Shapes<real, R>::at[shape].pipelined != 0; }
+  static bool pipelined(int shape) { return Shapes<real, R>::at[shape].kind != 0; }
+  // the second ring bulk-copies the diagonal too
+  static bool stages_diag(int shape) { return Shapes<real, R>::at[shape].kind == 2; }
   // the largest grid and the smallest block over every shape and mode, so that
   // a workspace sized once fits whichever shape a later call takes
   static int max_grid(int64_t n) {

@@ -59,9 +59,11 @@ def test_step_shape_table_host_logic(libpath):
                 info = g.kpm_shape_info(R, prec, k)
                 cpt = info["complex_per_thread"]
                 assert R % cpt == 0
-                assert info["rows_per_tile"] == 256 // (R // cpt)
+                assert info["rows_per_tile"] == 256 // (R // cpt) * info["rows_per_thread"]
                 assert info["min_blocks"] >= 1
                 assert (info["stages"] >= 2) == bool(info["pipelined"])
+                assert info["rows_per_tile"] == 256 // (R // cpt) * info["rows_per_thread"] or \
+                    info["pipelined"] != 2
             with pytest.raises(g.GputbError):
                 g.kpm_shape_info(R, prec, count)
         assert g.kpm_shape_count(3, prec) == 0

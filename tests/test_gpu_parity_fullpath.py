@@ -98,19 +98,30 @@ def test_multitile_ring_and_grid_stride_match_oracle(g, sheet, R, dtype, doublin
         assert err <= TOL[dtype], (shape, err)
 
 
+WIDE = ("junction", 400, 500, 0.1, 5151)        # 800,000 atoms
+
+
+@pytest.fixture(scope="module")
+def wide():
+    s, p, H, ip, idx, t, eps = oracle_pool.oracle_hamiltonian(WIDE)
+    _, _, a, b = obo.spectral_bounds(H, 64, synth.LANCZOS_SEED)
+    _, mu = okpm.kpm_moments(H, a, b, M_SHEET, 1, SEED)
+    return dict(s=s, ip=ip, idx=idx, t=t, eps=eps, a=a, b=b, mu=mu)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
-def test_one_vector_grid_stride_loop_matches_oracle(g, sheet, dtype):
-    """R = 1 (the 1e8-atom headline's block width): one thread per row, the
-    direct kernel's grid-stride loop runs at least twice per CTA."""
-    n = sheet["s"].n
-    Hd = _mat(sheet, dtype)
-    ref = _oracle(sheet, 1)
+def test_one_vector_grid_stride_loop_matches_oracle(g, wide, dtype):
+    """R = 1 (the 1e8-atom headline's block width): one thread per row on an
+    800k-atom junction, so the direct kernel's grid-stride loop runs at least
+    twice per CTA."""
+    n = wide["s"].n
+    Hd = sell_matrix(wide["ip"], wide["idx"], wide["t"], wide["eps"], n, dtype)
     for shape in _shapes(g, 1, dtype):
         for doubling in (False, True):
             _assert_multitile(g, n, 1, dtype, doubling, shape)
             g.kpm_force_shape(1, dtype, shape)
-            mu = g.kpm_moments(Hd, sheet["a"], sheet["b"], M_SHEET, 1, SEED, doubling=doubling).cpu().numpy()
-            assert np.max(np.abs(mu - ref)) <= TOL[dtype], (shape, doubling)
+            mu = g.kpm_moments(Hd, wide["a"], wide["b"], M_SHEET, 1, SEED, doubling=doubling).cpu().numpy()
+            assert np.max(np.abs(mu - wide["mu"])) <= TOL[dtype], (shape, doubling)
 
 
 # eleven uneven junction snapshots, 4,800 .. 96,000 atoms (none a multiple of
