@@ -51,9 +51,27 @@ constexpr int kFastW = 16;
 // Write the CTA's partial sums as entry `idx` of the moment slot (and of the
 // next slot for the doubling pair), then restart the accumulators.  Every
 // thread of the CTA must call it.
-template <typename real, int R, int CPT, bool DBL>
-__device__ __forceinline__ void flush_partials(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
-                                               double *partial, int64_t idx, int64_t slot_stride) {
+// FP32 dot accumulator of the opt-2 ring shapes: a plain FP32 running sum
+// that is folded into an FP64 total every 8 additions, so that no FP32 sum
+// holds more than 8 terms (relative error below 8 x 2^-24 per fold).
+struct FoldAcc {
+  float s = 0.0f;
+  double d = 0.0;
+  int k = 0;
+  __device__ __forceinline__ void add(float ar, float ai, float br, float bi) {
+    s = fmaf(ar, br, fmaf(ai, bi, s));
+    if (++k == 8) {
+      d += (double)s;
+      s = 0.0f;
+      k = 0;
+    }
+  }
+  __device__ __forceinline__ double value() const { return d + (double)s; }
+};
+
+template <typename real, int R, int CPT, bool DBL, typename Acc>
+__device__ __forceinline__ void flush_partials(Acc (&acc)[CPT], Acc (&acc2)[CPT], double *partial, int64_t idx,
+                                               int64_t slot_stride) {
   double sum[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) sum[c] = acc[c].value();
@@ -66,7 +84,7 @@ __device__ __forceinline__ void flush_partials(DotAcc<real> (&acc)[CPT], DotAcc<
     __syncthreads();
   }
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
+  for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = Acc();
 }
 
 // Segmented mode: block `blk` of the current run of RPB-row blocks has just
@@ -74,8 +92,8 @@ __device__ __forceinline__ void flush_partials(DotAcc<real> (&acc)[CPT], DotAcc<
 // the next block of this CTA starts another snapshot (or there is none) the
 // run's sums go into the entry of the run's first block.  Uniform across the
 // CTA.
-template <typename real, int R, int CPT, bool DBL>
-__device__ __forceinline__ void segment_boundary(DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT],
+template <typename real, int R, int CPT, bool DBL, typename Acc>
+__device__ __forceinline__ void segment_boundary(Acc (&acc)[CPT], Acc (&acc2)[CPT],
                                                  double *partial, int64_t slot_stride, const BatchTables &bt,
                                                  int64_t blk, int rpb, int64_t blk_end, int64_t &run_head) {
   const int64_t nxt = blk + 1;
@@ -130,10 +148,10 @@ __device__ __forceinline__ void row_product_direct(const int32_t *__restrict__ c
 
 // The row's tail shared by both kernels: the diagonal term, the output
 // (stored with evict-first) and the dot accumulation.
-template <typename real, int CPT, bool FIRST, bool DBL>
+template <typename real, int CPT, bool FIRST, bool DBL, typename Acc>
 __device__ __forceinline__ void row_finish(real (&y)[2 * CPT], const real (&xi)[2 * CPT], const real (&p)[2 * CPT],
-                                           const real (&z)[2 * CPT], real d, real alpha, real *out,
-                                           DotAcc<real> (&acc)[CPT], DotAcc<real> (&acc2)[CPT]) {
+                                           const real (&z)[2 * CPT], real d, real alpha, real *out, Acc (&acc)[CPT],
+                                           Acc (&acc2)[CPT]) {
 #pragma unroll
   for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(d, xi[c], y[c]);
   real o[2 * CPT];
@@ -240,38 +258,71 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-// NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode)
-template <typename real, typename valT, int R, int CPT, int STAGES, int NV = 2>
+// NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode);
+// HDR: the stage starts with the tile's slice offsets (opt 8)
+template <typename real, typename valT, int R, int CPT, int STAGES, int NV = 2, bool HDR = false>
 struct BulkGeom {
   static constexpr int TPR = R / CPT;
   static constexpr int TR = kBlock / TPR;                       // rows per tile
   static constexpr int kEl = TR * kFastW;                       // SELL elements per stage
+  static constexpr size_t kHdrBytes = HDR ? ((TR / 32 + 1) * 8 + 15) / 16 * 16 : 0;
   static constexpr size_t kColBytes = kEl * sizeof(int32_t);
   static constexpr size_t kValBytes = kEl * sizeof(valT);
   static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
-  static constexpr size_t kStageBytes = kColBytes + kValBytes + NV * kVecBytes;
+  static constexpr size_t kStageBytes = kHdrBytes + kColBytes + kValBytes + NV * kVecBytes;
   static constexpr size_t kSmem = 128 + STAGES * kStageBytes;  // mbarriers first
   static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024 && STAGES >= 2 && STAGES <= 8;
 };
 
-template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, bool FIRST, bool DBL, bool SEG>
+// y += sum over the row's slots (from shared memory) of h_s x[j_s]
+template <typename real, typename valT, int R, int CPT, int W>
+__device__ __forceinline__ void row_product_smem(const int32_t *cs, const valT *vs, const real *__restrict__ xp,
+                                                 int w, real (&y)[2 * CPT]) {
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    if (s < w) {
+      real xv[2 * CPT];
+      const real h = static_cast<real>(vs[32 * s]);
+      ld_gather<real, CPT>(xp + (int64_t)cs[32 * s] * (R * 2), xv);
+#pragma unroll
+      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+    }
+  }
+}
+
+// Options of the ring kernel (bit mask OPT, chosen per shape):
+//   1  rows of slices at most 12 wide take a 12-slot unrolled body
+//   2  FP32 vectors: FoldAcc dot sums (plain FP32, folded into FP64 every 8
+//      terms) instead of Kahan pairs
+//   4  after a tile's wait, one thread per row issues L2 prefetches of the
+//      next tile's neighbour rows of x (from that stage's columns, when the
+//      stage is already complete), so first touches of x rows come from L2
+//   8  the producer writes the tile's slice offsets into the stage, and rows
+//      read them from shared memory instead of slice_ptr
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int OPT, bool FIRST, bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
     int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
-  using G = BulkGeom<real, valT, R, CPT, STAGES, DBL ? 1 : 2>;
+  constexpr bool HDR = (OPT & 8) != 0;
+  using G = BulkGeom<real, valT, R, CPT, STAGES, DBL ? 1 : 2, HDR>;
+  using Acc = std::conditional_t<(OPT & 2) != 0 && sizeof(real) == 4, FoldAcc, DotAcc<real>>;
   constexpr int TPR = G::TPR, TR = G::TR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);
   unsigned char *ring = smem + 128;
-  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes); };
-  auto s_val = [&](int st) { return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kColBytes); };
+  auto s_hdr = [&](int st) { return reinterpret_cast<int64_t *>(ring + st * G::kStageBytes); };
+  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes + G::kHdrBytes); };
+  auto s_val = [&](int st) {
+    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes);
+  };
   auto s_prev = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes);
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes);
   };
   auto s_v0 = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes + G::kVecBytes);
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes +
+                                    G::kVecBytes);
   };
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
@@ -295,6 +346,12 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     const int64_t k0 = r0 >> 5;
     const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
     const int64_t e0 = slice_ptr[k0], e1 = slice_ptr[k1];
+    if (HDR) {
+      int64_t *h = s_hdr(st);
+      h[0] = e0;
+#pragma unroll
+      for (int q = 1; q <= TR / 32; ++q) h[q] = (k0 + q < k1) ? slice_ptr[k0 + q] : e1;
+    }
     const bool bulk = (e1 - e0) <= G::kEl;
     const uint32_t ebytes = bulk ? static_cast<uint32_t>(e1 - e0) : 0u;
     uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
@@ -317,7 +374,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   if (threadIdx.x == 0)
     for (; issued < my_tiles && issued < STAGES; ++issued) issue(issued);
 
-  DotAcc<real> acc[CPT], acc2[CPT];
+  Acc acc[CPT], acc2[CPT];
   bool ok = true;
   int64_t kk = 0;
   for (; kk < my_tiles; ++kk) {
@@ -328,34 +385,58 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     const int64_t tile = tile_of(kk);
     const int64_t r0 = tile * TR;
     const int64_t i = r0 + lr;
+    if ((OPT & 4) && part == 0 && kk + 1 < my_tiles) {
+      // the next tile's neighbour rows of x into L2 (if its stage is complete)
+      const int st1 = static_cast<int>((kk + 1) % STAGES);
+      const int64_t i1 = tile_of(kk + 1) * TR + lr;
+      if (i1 < n && mbar_try_wait(full + st1, static_cast<uint32_t>(((kk + 1) / STAGES) & 1))) {
+        const int64_t k0n = (i1 - lr) >> 5;
+        const int64_t e0n = HDR ? s_hdr(st1)[0] : __ldg(slice_ptr + k0n);
+        const int64_t k1n = min((i1 - lr + TR + 31) >> 5, (n + 31) >> 5);
+        const int64_t e1n = HDR ? s_hdr(st1)[TR / 32] : __ldg(slice_ptr + k1n);
+        if (e1n - e0n <= G::kEl) {
+          const int64_t sbn = HDR ? s_hdr(st1)[lr >> 5] : __ldg(slice_ptr + (i1 >> 5));
+          const int64_t sen = HDR ? s_hdr(st1)[(lr >> 5) + 1] : __ldg(slice_ptr + (i1 >> 5) + 1);
+          const int wn = static_cast<int>((sen - sbn) >> 5);
+          const int32_t *csn = s_col(st1) + (sbn - e0n) + (lr & 31);
+#pragma unroll
+          for (int s = 0; s < kFastW; ++s)
+            if (s < wn) asm volatile("prefetch.global.L2 [%0];" ::"l"(x + (int64_t)csn[32 * s] * R * 2));
+        }
+      }
+    }
     if (i < n) {
       const int64_t k0 = r0 >> 5;
-      const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
-      const int64_t e0 = __ldg(slice_ptr + k0);
-      const bool bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
+      int64_t e0, sb;
+      bool bulk;
+      int w;
+      if (HDR) {
+        const int64_t *h = s_hdr(st);
+        e0 = h[0];
+        bulk = (h[TR / 32] - e0) <= G::kEl;
+        sb = h[lr >> 5];
+        w = static_cast<int>((h[(lr >> 5) + 1] - sb) >> 5);
+      } else {
+        const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
+        e0 = __ldg(slice_ptr + k0);
+        bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
+        sb = __ldg(slice_ptr + (i >> 5));
+        w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
+      }
       const int loff = (lr * R + part * CPT) * 2;
       real p[2 * CPT], z[2 * CPT];
       if (!FIRST) memcpy(p, s_prev(st) + loff, sizeof(p));
       if (!DBL) memcpy(z, s_v0(st) + loff, sizeof(z));
       const real d = (diag ? static_cast<real>(__ldg(diag + i)) : real(0)) - shift;
-      const int64_t sb = __ldg(slice_ptr + (i >> 5));
-      const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
       real y[2 * CPT];
 #pragma unroll
       for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
       if (bulk) {
         const int32_t *cs = s_col(st) + (sb - e0) + (i & 31);
         const valT *vs = s_val(st) + (sb - e0) + (i & 31);
-#pragma unroll
-        for (int s = 0; s < kFastW; ++s) {
-          if (s < w) {
-            real xv[2 * CPT];
-            const real h = static_cast<real>(vs[32 * s]);
-            ld_gather<real, CPT>(x + ((int64_t)cs[32 * s] * R + part * CPT) * 2, xv);
-#pragma unroll
-            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
-          }
-        }
+        const real *xp = x + part * CPT * 2;
+        if ((OPT & 1) && w <= 12) row_product_smem<real, valT, R, CPT, 12>(cs, vs, xp, w, y);
+        else row_product_smem<real, valT, R, CPT, kFastW>(cs, vs, xp, w, y);
       } else {
         int64_t e = sb + (i & 31);
         for (int s = 0; s < w; ++s, e += 32) {
@@ -385,7 +466,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
+    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = Acc();
   }
   if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
@@ -416,22 +497,6 @@ struct Ring2Geom {
   static constexpr size_t kSmem = 128 + STAGES * kStageBytes;
   static constexpr bool kOk = TRW % 32 == 0 && kSmem <= 200 * 1024 && STAGES >= 2 && STAGES <= 8 && kSlices + 1 <= 32;
 };
-
-// y += sum over the row's slots (from shared memory) of h_s x[j_s]
-template <typename real, typename valT, int R, int CPT, int W>
-__device__ __forceinline__ void row_product_smem(const int32_t *cs, const valT *vs, const real *__restrict__ xp,
-                                                 int w, real (&y)[2 * CPT]) {
-#pragma unroll
-  for (int s = 0; s < W; ++s) {
-    if (s < w) {
-      real xv[2 * CPT];
-      const real h = static_cast<real>(vs[32 * s]);
-      ld_gather<real, CPT>(xp + (int64_t)cs[32 * s] * (R * 2), xv);
-#pragma unroll
-      for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
-    }
-  }
-}
 
 template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int RPT, bool STAGE_VEC, bool FIRST,
           bool DBL, bool SEG>
@@ -632,15 +697,16 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 // ---------------------------------------------------------------------------
 struct StepShape {
   int kind;        // 0: direct loads, 1: bulk-copy ring, 2: second ring (offsets, diagonal staged)
+  int opt;         // option bits of the bulk-copy ring (see cheb_step_bulk_kernel)
   int cpt;         // complex numbers per thread
   int stages;      // ring depth (rings only)
   int minb;        // resident CTAs per SM of the register budget
   int rpt;         // rows per thread per tile (second ring; 1 otherwise)
   int svec;        // the ring stages v_{n-1} (and v0) rows in shared memory
 };
-constexpr StepShape D(int cpt, int minb) { return {0, cpt, 0, minb, 1, 0}; }
-constexpr StepShape P(int cpt, int stages, int minb) { return {1, cpt, stages, minb, 1, 1}; }
-constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) { return {2, cpt, stages, minb, rpt, svec}; }
+constexpr StepShape D(int cpt, int minb) { return {0, 0, cpt, 0, minb, 1, 0}; }
+constexpr StepShape P(int cpt, int stages, int minb, int opt = 0) { return {1, opt, cpt, stages, minb, 1, 1}; }
+constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) { return {2, 0, cpt, stages, minb, rpt, svec}; }
 
 template <typename real, int R> struct Shapes;
 // FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
@@ -657,9 +723,9 @@ template <> struct Shapes<float, 4> {
   static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), Q(2, 3, 3, 1, 0)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {P(2, 3, 4),       P(2, 2, 4),       P(2, 4, 4),       D(2, 3),
-                                     Q(2, 3, 4, 1, 0), Q(2, 3, 3, 1, 0), Q(2, 3, 4, 2, 0), Q(2, 3, 3, 2, 0),
-                                     Q(2, 3, 4, 1, 1), Q(2, 3, 3, 1, 1)};
+  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),       P(2, 4, 4),    D(2, 3),
+                                     Q(2, 3, 4, 1, 0), P(2, 3, 4, 1), P(2, 3, 4, 2), P(2, 3, 4, 4),
+                                     P(2, 3, 4, 8), P(2, 3, 4, 15), P(2, 2, 4, 15)};
 };
 template <> struct Shapes<float, 16> {
   static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 4, 1, 0), Q(2, 3, 3, 1, 0)};
@@ -694,13 +760,13 @@ constexpr int shape_count() {
 
 // Everything that depends on one shape: occupancy-derived grid, shared
 // memory opt-in and the launches.
-template <typename real, typename valT, int R, int CPT, int KIND, int STAGES, int MINB, int RPT, int SVEC>
+template <typename real, typename valT, int R, int CPT, int KIND, int STAGES, int MINB, int RPT, int SVEC, int OPT>
 struct ShapeKit {
   static constexpr int TPR = R / CPT;
   static constexpr int RPB = (kBlock / TPR) * (KIND == 2 ? RPT : 1);   // rows per tile
   static constexpr int S = STAGES >= 2 ? STAGES : 2;
   template <bool DBL>
-  using GB = BulkGeom<real, valT, R, CPT, S, DBL ? 1 : 2>;
+  using GB = BulkGeom<real, valT, R, CPT, S, DBL ? 1 : 2, (OPT & 8) != 0>;
   template <bool DBL>
   using G2 = Ring2Geom<real, valT, R, CPT, S, RPT, SVEC != 0, DBL ? 1 : 2>;
   template <bool DBL>
@@ -714,7 +780,7 @@ struct ShapeKit {
   template <bool FIRST, bool DBL, bool SEG>
   static auto kernel() {
     if constexpr (KIND == 1)
-      return cheb_step_bulk_kernel<real, valT, R, CPT, S, MINB, FIRST, DBL, SEG>;
+      return cheb_step_bulk_kernel<real, valT, R, CPT, S, MINB, OPT, FIRST, DBL, SEG>;
     else if constexpr (KIND == 2)
       return cheb_step_ring2_kernel<real, valT, R, CPT, S, MINB, RPT, SVEC != 0, FIRST, DBL, SEG>;
     else
@@ -781,7 +847,7 @@ struct ShapeKit {
 template <typename real, typename valT, int R, int I>
 using KitOf = ShapeKit<real, valT, R, Shapes<real, R>::at[I].cpt, Shapes<real, R>::at[I].kind,
                        Shapes<real, R>::at[I].stages, Shapes<real, R>::at[I].minb, Shapes<real, R>::at[I].rpt,
-                       Shapes<real, R>::at[I].svec>;
+                       Shapes<real, R>::at[I].svec, Shapes<real, R>::at[I].opt>;
 
 // Call f(KitOf<..., I>{}) for the runtime shape index `id`.
 template <typename real, typename valT, int R, int I = 0, typename F>
