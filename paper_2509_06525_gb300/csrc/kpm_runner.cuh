@@ -117,6 +117,17 @@ struct KpmRunner {
 
   static int64_t padded_rows(int64_t n) { return (n + kRowPad - 1) / kRowPad * kRowPad; }
 
+  // band plan storage (banded shapes only): records, then local indices
+  struct PlanWs {
+    BandRec *recs = nullptr;
+    uint16_t *lidx = nullptr;
+  };
+  static void carve_plan(Carver &cv, int64_t n, PlanWs *pw) {
+    if (!Kit::any_banded()) return;
+    pw->recs = cv.take<BandRec>(Kit::plan_records(n));
+    pw->lidx = cv.take<uint16_t>((size_t)padded_rows(n) * kBandSlots);
+  }
+
   static size_t workspace(int64_t n, int M, bool segmented) {
     Carver cv(nullptr, 0);
     for (int k = 0; k < 3; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
@@ -124,7 +135,18 @@ struct KpmRunner {
                                     : Kit::max_grid(n);
     cv.take<double>((size_t)(M + 1) * units * R);
     cv.take<int>(4);
+    PlanWs pw;
+    carve_plan(cv, n, &pw);
     return cv.used + 256;
+  }
+
+  // the band plan of `shape` (a no-op for shapes that need none)
+  static tb_status make_plan(int shape, int64_t n, const int64_t *slice_ptr, const int32_t *col, const PlanWs &pw,
+                             cudaStream_t st, BandPlan *bp) {
+    if (!Kit::banded(shape)) return TB_OK;
+    bp->recs = pw.recs;
+    bp->lidx = pw.lidx;
+    return Kit::plan(shape, n, padded_rows(n), slice_ptr, col, pw.recs, pw.lidx, st);
   }
 
   static tb_status random_phases(int shape, int grid, int64_t n, uint64_t seed, int64_t r0, const BatchTables &bt,
@@ -145,7 +167,8 @@ struct KpmRunner {
   static tb_status enqueue(int shape, int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col,
                            const valT *val, const valT *diag, double a, double b, int M, uint64_t seed, int64_t r0,
                            bool dbl, double *mu_r, real *v0, real *A, real *B, double *partial, int *flags,
-                           const BatchTables &bt, cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                           const BatchTables &bt, cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                           const BandPlan &bp) {
     const int rpb = Kit::rows_per_block(shape);
     const int64_t units = SEG ? (n + rpb - 1) / rpb : grid;   // partials per moment slot
     const int64_t ps = units * R;
@@ -158,9 +181,9 @@ struct KpmRunner {
     const real shift = static_cast<real>(b);
     const real inv_a = static_cast<real>(1.0 / a);
     s = dbl ? Kit::template step<true, true, SEG>(shape, grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A,
-                                                  partial, inv_a, shift, flags, ps, bt, st)
+                                                  partial, inv_a, shift, flags, ps, bt, st, bp)
             : Kit::template step<true, false, SEG>(shape, grid, n, slice_ptr, col, val, diag, v0, nullptr, v0, A,
-                                                   partial + ps, inv_a, shift, flags, ps, bt, st);
+                                                   partial + ps, inv_a, shift, flags, ps, bt, st, bp);
     if (s != TB_OK) return s;
     const real two_over_a = static_cast<real>(2.0 / a);
     const int last = dbl ? (M - 1) / 2 + 1 : M - 1;   // index of the last vector computed
@@ -171,10 +194,10 @@ struct KpmRunner {
       const real *prev = (m == 2) ? v0 : out;
       s = dbl ? Kit::template step<false, true, SEG>(shape, grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
                                                      partial + (size_t)(2 * (m - 1)) * ps, two_over_a, shift,
-                                                     flags, ps, bt, st)
+                                                     flags, ps, bt, st, bp)
               : Kit::template step<false, false, SEG>(shape, grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
                                                       partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt,
-                                                      st);
+                                                      st, bp);
       if (s != TB_OK) return s;
     }
     if (ev_end) TB_CUDA(cudaEventRecord(ev_end, st));
@@ -221,19 +244,24 @@ struct KpmRunner {
     real *v0 = cv.take<real>((size_t)np * R * 2);
     real *A = cv.take<real>((size_t)np * R * 2);
     real *B = cv.take<real>((size_t)np * R * 2);
-    double *partial = cv.take<double>((size_t)(M + 1) * grid * R);
+    double *partial = cv.take<double>((size_t)(M + 1) * Kit::max_grid(n) * R);
     int *flags = cv.take<int>(4);
+    PlanWs pw;
+    carve_plan(cv, n, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments: workspace too small (%zu < %zu)", ws_bytes, cv.used);
     tb_status s = check_alignment(shape, col, val, diag, "kpm_moments");
     if (s != TB_OK) return s;
     Kit::prepare(shape);
+    BandPlan bp;
+    s = make_plan(shape, n, slice_ptr, col, pw, st, &bp);
+    if (s != TB_OK) return s;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (step_ms) {
       TB_CUDA(cudaEventCreate(&ev[0]));
       TB_CUDA(cudaEventCreate(&ev[1]));
     }
     s = enqueue<false>(shape, grid, n, slice_ptr, col, val, diag, a, b, M, seed, r0, dbl, mu_r, v0, A, B, partial,
-                       flags, BatchTables(), st, ev[0], ev[1]);
+                       flags, BatchTables(), st, ev[0], ev[1], bp);
     if (s == TB_OK) s = check_flags(flags, st, "kpm_moments");
     if (step_ms) {
       float ms = 0.f;
@@ -259,10 +287,17 @@ struct KpmRunner {
     real *v0 = cv.take<real>((size_t)n_pad * R * 2);
     real *A = cv.take<real>((size_t)n_pad * R * 2);
     real *B = cv.take<real>((size_t)n_pad * R * 2);
-    double *partial = cv.take<double>((size_t)(M + 1) * ((n_pad + rpb - 1) / rpb) * R);
+    double *partial = cv.take<double>((size_t)(M + 1) * ((n_pad + Kit::min_rows_per_block() - 1) /
+                                                         Kit::min_rows_per_block()) * R);
     int *flags = cv.take<int>(4);
+    PlanWs pw;
+    carve_plan(cv, n_pad, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments_batched: workspace too small");
+    (void)rpb;
     Kit::prepare(shape);
+    BandPlan bp;
+    tb_status sp = make_plan(shape, n_pad, slice_ptr, col, pw, st, &bp);
+    if (sp != TB_OK) return sp;
     cudaStream_t cs = nullptr;
     TB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
@@ -271,7 +306,7 @@ struct KpmRunner {
     tb_status s = TB_OK;
     if (e == cudaSuccess) {
       s = enqueue<true>(shape, grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, 0, dbl, mu, v0, A, B,
-                        partial, flags, bt, cs, nullptr, nullptr);
+                        partial, flags, bt, cs, nullptr, nullptr, bp);
       e = cudaStreamEndCapture(cs, &graph);
     }
     if (e == cudaSuccess && s == TB_OK) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -312,8 +347,10 @@ struct KpmRunner {
     real *v0 = cv.take<real>((size_t)np * R * 2);
     real *A = cv.take<real>((size_t)np * R * 2);
     real *B = cv.take<real>((size_t)np * R * 2);
-    double *partial = cv.take<double>((size_t)2 * gmax * R);
+    double *partial = cv.take<double>((size_t)3 * gmax * R);
     int *flags = cv.take<int>(4);
+    PlanWs pw;
+    carve_plan(cv, n, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_kpm_autotune: workspace too small (%zu < %zu)", ws_bytes, cv.used);
     const int64_t ps = (int64_t)gmax * R;
     const real shift = static_cast<real>(b);
@@ -339,14 +376,18 @@ struct KpmRunner {
     for (int shape = 0; shape < Kit::kShapes && s == TB_OK; ++shape) {
       Kit::prepare(shape);
       const int grid = Kit::grid(shape, n, dbl);
+      BandPlan bp;
+      s = make_plan(shape, n, slice_ptr, col, pw, st, &bp);
+      if (s != TB_OK) break;
       auto one = [&](int k) {
         // the recursion's in-place update: out = 2 H~ x - out
         real *out = (k & 1) ? A : B;
         const real *x = (k & 1) ? B : A;
         return dbl ? Kit::template step<false, true, false>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
-                                                            out, partial, two_over_a, shift, flags, ps, none, st)
+                                                            out, partial, two_over_a, shift, flags, ps, none, st, bp)
                    : Kit::template step<false, false, false>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
-                                                             out, partial, two_over_a, shift, flags, ps, none, st);
+                                                             out, partial, two_over_a, shift, flags, ps, none, st,
+                                                             bp);
       };
       for (int k = 0; k < 2 && s == TB_OK; ++k) s = one(k);
       if (s != TB_OK) break;

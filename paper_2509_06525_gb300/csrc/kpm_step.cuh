@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "kpm_band.cuh"
 #include "kpm_common.cuh"
 
 namespace gputb {
@@ -661,6 +662,204 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
   if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
 
+// ---------------------------------------------------------------------------
+// Banded step (kind 3 shapes; needs the plan of kpm_band.cuh for T =
+// kBlock / TPR).  A stage holds the tile's record, its local indices and
+// values (kBandSlots slots per row at most), its diagonal (whole tiles), its
+// streamed rows of v_{n-1} (and v0) and the ROWS x rows of its bands.  The
+// producer (thread 0) keeps the records one tile ahead in a two-entry ring of
+// its own, so that it knows the bands of a tile when it refills a stage.
+// Tiles with nb < 0 stream only the vector rows and gather from global.
+// ---------------------------------------------------------------------------
+template <typename real, typename valT, int R, int CPT, int STAGES, int ROWS, int NV>
+struct BandGeom {
+  static constexpr int TPR = R / CPT;
+  static constexpr int TR = kBlock / TPR;
+  static constexpr int kEl = TR * kBandSlots;
+  static constexpr size_t kRowBytes = (size_t)R * 2 * sizeof(real);
+  static constexpr size_t kRecBytes = sizeof(BandRec);
+  static constexpr size_t kIdxBytes = (kEl * 2 + 15) / 16 * 16;
+  static constexpr size_t kValBytes = kEl * sizeof(valT);
+  static constexpr size_t kDiagBytes = (TR * sizeof(valT) + 15) / 16 * 16;
+  static constexpr size_t kVecBytes = (size_t)TR * kRowBytes;
+  static constexpr size_t kXBytes = (size_t)ROWS * kRowBytes;
+  static constexpr size_t kStageBytes = kRecBytes + kIdxBytes + kValBytes + kDiagBytes + NV * kVecBytes + kXBytes;
+  static constexpr size_t kSmem = 256 + 2 * kRecBytes + STAGES * kStageBytes;   // barriers, record ring
+  static constexpr bool kOk = TR % 32 == 0 && TR / 32 + 1 <= 9 && kSmem <= 220 * 1024 && STAGES >= 2 &&
+                              STAGES <= 4 && ROWS <= 65535;
+};
+
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int ROWS, bool FIRST, bool DBL, bool SEG>
+__global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
+    int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
+    const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
+    int *__restrict__ flags, int64_t slot_stride, BatchTables bt, const BandRec *__restrict__ recs,
+    const uint16_t *__restrict__ lidx) {
+  using G = BandGeom<real, valT, R, CPT, STAGES, ROWS, DBL ? 1 : 2>;
+  constexpr int TPR = G::TPR, TR = G::TR;
+  constexpr int RE = R * 2;   // reals per x row
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // [STAGES]
+  uint64_t *recbar = full + 8;                                  // [2]
+  BandRec *rring = reinterpret_cast<BandRec *>(smem + 256);     // [2]
+  unsigned char *ring = smem + 256 + 2 * G::kRecBytes;
+  auto s_rec = [&](int st) { return reinterpret_cast<BandRec *>(ring + st * G::kStageBytes); };
+  auto s_idx = [&](int st) { return reinterpret_cast<uint16_t *>(ring + st * G::kStageBytes + G::kRecBytes); };
+  auto s_val = [&](int st) {
+    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kRecBytes + G::kIdxBytes);
+  };
+  auto s_diag = [&](int st) {
+    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kRecBytes + G::kIdxBytes + G::kValBytes);
+  };
+  auto s_vec = [&](int st, int q) {
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kRecBytes + G::kIdxBytes + G::kValBytes +
+                                    G::kDiagBytes + q * G::kVecBytes);
+  };
+  auto s_x = [&](int st) {
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kRecBytes + G::kIdxBytes + G::kValBytes +
+                                    G::kDiagBytes + (DBL ? 1 : 2) * G::kVecBytes);
+  };
+  const int64_t ntiles = (n + TR - 1) / TR;
+  const int part = threadIdx.x % TPR;
+  const int lr = threadIdx.x / TPR;
+  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
+  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
+  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
+  const int64_t my_tiles =
+      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
+    mbar_init(recbar, 1);
+    mbar_init(recbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  bool ok = true;   // thread 0: its own record waits
+  // producer side (thread 0 only)
+  auto fetch_rec = [&](int64_t kk) {   // record of local tile kk into the record ring
+    const int slot = static_cast<int>(kk & 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(recbar + slot, sizeof(BandRec));
+    bulk_g2s(rring + slot, recs + tile_of(kk), sizeof(BandRec), recbar + slot);
+  };
+  auto issue = [&](int64_t kk) -> bool {
+    const int slot = static_cast<int>(kk & 1);
+    if (!mbar_wait_bounded(recbar + slot, static_cast<uint32_t>((kk >> 1) & 1))) {
+      ok = false;
+      return false;
+    }
+    const int64_t tile = tile_of(kk);
+    const int st = static_cast<int>(kk % STAGES);
+    const int64_t r0 = tile * TR;
+    BandRec *dst = s_rec(st);
+    *dst = rring[slot];
+    const BandRec &rc = *dst;
+    if (kk + 1 < my_tiles) fetch_rec(kk + 1);   // the ring slot of kk - 1 is free
+    const bool banded = rc.nb > 0;
+    const bool whole = r0 + TR <= n;
+    const uint32_t cnt = static_cast<uint32_t>(rc.srel[TR / 32 < 9 ? TR / 32 : 8]);
+    uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
+    uint32_t xrows = 0;
+    if (banded) {
+      for (int b = 0; b < rc.nb; ++b) xrows += static_cast<uint32_t>(rc.len[b]);
+      tx += cnt * (2u + static_cast<uint32_t>(sizeof(valT))) + xrows * static_cast<uint32_t>(G::kRowBytes);
+      if (diag && whole) tx += TR * sizeof(valT);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(full + st, tx);
+    if (banded) {
+      if (cnt > 0) {
+        bulk_g2s(s_idx(st), lidx + tile * (int64_t)TR * kBandSlots, cnt * 2u, full + st);
+        bulk_g2s(s_val(st), val + rc.e0, cnt * static_cast<uint32_t>(sizeof(valT)), full + st);
+      }
+      if (diag && whole) bulk_g2s(s_diag(st), diag + r0, TR * sizeof(valT), full + st);
+      for (int b = 0; b < rc.nb; ++b)
+        bulk_g2s(s_x(st) + (size_t)rc.off[b] * RE, x + (size_t)rc.lo[b] * RE,
+                 static_cast<uint32_t>(rc.len[b]) * static_cast<uint32_t>(G::kRowBytes), full + st);
+    }
+    const size_t voff = (size_t)r0 * RE;
+    if (!FIRST) bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    if (!DBL) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    return true;
+  };
+
+  int64_t issued = 0;
+  if (threadIdx.x == 0 && my_tiles > 0) {
+    fetch_rec(0);
+    while (issued < my_tiles && issued < STAGES && issue(issued)) ++issued;
+  }
+
+  int64_t run_head = t_begin;
+  DotAcc<real> acc[CPT], acc2[CPT];
+  int64_t kk = 0;
+  for (; kk < my_tiles; ++kk) {
+    const int st = static_cast<int>(kk % STAGES);
+    const uint32_t parity = static_cast<uint32_t>((kk / STAGES) & 1);
+    const bool mine = threadIdx.x != 0 || ok;
+    ok = __syncthreads_and(mine && mbar_wait_bounded(full + st, parity)) != 0;
+    if (!ok) break;
+    const int64_t tile = tile_of(kk);
+    const int64_t r0 = tile * TR;
+    const int64_t i = r0 + lr;
+    if (i < n) {
+      const BandRec &rc = *s_rec(st);
+      const bool banded = rc.nb > 0;
+      const int64_t off = (i * R + part * CPT) * 2;
+      const int q = lr >> 5;
+      const int sb = rc.srel[q];
+      const int w = (rc.srel[q + 1] - sb) >> 5;
+      real p[2 * CPT], z[2 * CPT];
+      if (!FIRST) memcpy(p, s_vec(st, 0) + (lr * R + part * CPT) * 2, sizeof(p));
+      if (!DBL) memcpy(z, s_vec(st, 1) + (lr * R + part * CPT) * 2, sizeof(z));
+      real d = real(0);
+      if (diag) d = (banded && r0 + TR <= n) ? static_cast<real>(s_diag(st)[lr]) : static_cast<real>(__ldg(diag + i));
+      d -= shift;
+      real y[2 * CPT];
+#pragma unroll
+      for (int c = 0; c < 2 * CPT; ++c) y[c] = real(0);
+      real xi[2 * CPT];
+      if (banded) {
+        const real *xs = s_x(st) + part * CPT * 2;
+        const uint16_t *li = s_idx(st) + sb + (lr & 31);
+        const valT *vs = s_val(st) + sb + (lr & 31);
+#pragma unroll
+        for (int s = 0; s < kBandSlots; ++s) {
+          if (s < w) {
+            real xv[2 * CPT];
+            const real h = static_cast<real>(vs[32 * s]);
+            memcpy(xv, xs + (int)li[32 * s] * RE, sizeof(xv));
+#pragma unroll
+            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+          }
+        }
+        memcpy(xi, xs + (rc.own + lr) * RE, sizeof(xi));
+      } else {
+        row_product_direct<real, valT, R, CPT>(col, val, x, rc.e0 + sb + (lr & 31), w, part, y);
+        ld_gather<real, CPT>(x + off, xi);
+      }
+      row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
+    }
+    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0 && issued < my_tiles && ok && issue(issued)) ++issued;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 4);
+      for (int64_t q = kk; q < issued; ++q)
+        mbar_wait_bounded(full + q % STAGES, static_cast<uint32_t>((q / STAGES) & 1));
+      if (issued < my_tiles) mbar_wait_bounded(recbar + (issued & 1), static_cast<uint32_t>((issued >> 1) & 1));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = DotAcc<real>();
+  }
+  if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
+}
+
 // mu_r[r, m] = (sum over CTAs in index order of partial[m, cta, r]) / n;
 // flags[0] |= 1 if |mu| > bound (when bound > 0), |= 2 if not finite.
 __device__ __forceinline__ double slot_sum(const double *__restrict__ partial, int grid, int R, int m, int r) {
@@ -696,17 +895,22 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 // reproducible.
 // ---------------------------------------------------------------------------
 struct StepShape {
-  int kind;        // 0: direct loads, 1: bulk-copy ring, 2: second ring (offsets, diagonal staged)
+  int kind;        // 0: direct loads, 1: bulk-copy ring, 2: second ring (offsets, diagonal staged),
+                   // 3: banded step (x bands staged; needs the band plan)
   int opt;         // option bits of the bulk-copy ring (see cheb_step_bulk_kernel)
   int cpt;         // complex numbers per thread
   int stages;      // ring depth (rings only)
   int minb;        // resident CTAs per SM of the register budget
   int rpt;         // rows per thread per tile (second ring; 1 otherwise)
   int svec;        // the ring stages v_{n-1} (and v0) rows in shared memory
+  int brows;       // banded step: x rows a stage holds for the tile's bands
 };
-constexpr StepShape D(int cpt, int minb) { return {0, 0, cpt, 0, minb, 1, 0}; }
-constexpr StepShape P(int cpt, int stages, int minb, int opt = 0) { return {1, opt, cpt, stages, minb, 1, 1}; }
-constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) { return {2, 0, cpt, stages, minb, rpt, svec}; }
+constexpr StepShape D(int cpt, int minb) { return {0, 0, cpt, 0, minb, 1, 0, 0}; }
+constexpr StepShape P(int cpt, int stages, int minb, int opt = 0) { return {1, opt, cpt, stages, minb, 1, 1, 0}; }
+constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) {
+  return {2, 0, cpt, stages, minb, rpt, svec, 0};
+}
+constexpr StepShape B(int cpt, int stages, int minb, int brows) { return {3, 0, cpt, stages, minb, 1, 1, brows}; }
 
 template <typename real, int R> struct Shapes;
 // FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
@@ -714,7 +918,7 @@ template <typename real, int R> struct Shapes;
 // faster than 3), the 3-stage ring with 16-byte accesses (CPT = 2) and 4 CTAs
 // where four or more threads share a row.
 template <> struct Shapes<float, 1> {
-  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5)};
+  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5), B(1, 2, 3, 1024), B(1, 2, 2, 1024)};
 };
 template <> struct Shapes<float, 2> {
   static constexpr StepShape at[] = {D(2, 3), D(1, 4)};
@@ -723,12 +927,13 @@ template <> struct Shapes<float, 4> {
   static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), Q(2, 3, 3, 1, 0)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),       P(2, 4, 4),    D(2, 3),
-                                     Q(2, 3, 4, 1, 0), P(2, 3, 4, 1), P(2, 3, 4, 2), P(2, 3, 4, 4),
-                                     P(2, 3, 4, 8), P(2, 3, 4, 15), P(2, 2, 4, 15)};
+  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),         P(2, 4, 4),         D(2, 3),
+                                     P(2, 3, 4, 1), B(2, 2, 3, 320),    B(2, 2, 4, 256),    B(2, 3, 2, 320),
+                                     B(1, 2, 3, 320)};
 };
 template <> struct Shapes<float, 16> {
-  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 4, 1, 0), Q(2, 3, 3, 1, 0)};
+  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 3, 1, 0), B(2, 2, 3, 192),
+                                     B(4, 2, 2, 320)};
 };
 template <> struct Shapes<float, 32> {
   static constexpr StepShape at[] = {D(2, 3), P(4, 3, 2), D(4, 2), Q(4, 3, 2, 1, 0)};
@@ -760,7 +965,15 @@ constexpr int shape_count() {
 
 // Everything that depends on one shape: occupancy-derived grid, shared
 // memory opt-in and the launches.
-template <typename real, typename valT, int R, int CPT, int KIND, int STAGES, int MINB, int RPT, int SVEC, int OPT>
+// Device tables of the banded step (kind 3): one record per tile and the
+// tile-local column indices (built by band_plan_kernel).
+struct BandPlan {
+  const BandRec *recs = nullptr;
+  const uint16_t *lidx = nullptr;
+};
+
+template <typename real, typename valT, int R, int CPT, int KIND, int STAGES, int MINB, int RPT, int SVEC, int OPT,
+          int BROWS>
 struct ShapeKit {
   static constexpr int TPR = R / CPT;
   static constexpr int RPB = (kBlock / TPR) * (KIND == 2 ? RPT : 1);   // rows per tile
@@ -770,12 +983,17 @@ struct ShapeKit {
   template <bool DBL>
   using G2 = Ring2Geom<real, valT, R, CPT, S, RPT, SVEC != 0, DBL ? 1 : 2>;
   template <bool DBL>
+  using GBand = BandGeom<real, valT, R, CPT, S, (BROWS > 0 ? BROWS : 32), (DBL ? 1 : 2)>;
+  template <bool DBL>
   static constexpr size_t smem() {
-    return KIND == 1 ? GB<DBL>::kSmem : (KIND == 2 ? G2<DBL>::kSmem : 0);
+    return KIND == 1 ? GB<DBL>::kSmem : (KIND == 2 ? G2<DBL>::kSmem : (KIND == 3 ? GBand<DBL>::kSmem : 0));
   }
+  // the banded step's x rows must start on 16-byte boundaries
+  static constexpr int kRowAlign = (R * 2 * (int)sizeof(real)) % 16 == 0 ? 1 : 16 / (R * 2 * (int)sizeof(real));
   static_assert(R % CPT == 0 && TPR <= 32, "bad shape");
   static_assert(KIND != 1 || (GB<true>::kOk && GB<false>::kOk), "ring shape does not fit");
   static_assert(KIND != 2 || (G2<true>::kOk && G2<false>::kOk), "second-ring shape does not fit");
+  static_assert(KIND != 3 || (GBand<true>::kOk && GBand<false>::kOk), "banded shape does not fit");
 
   template <bool FIRST, bool DBL, bool SEG>
   static auto kernel() {
@@ -783,6 +1001,8 @@ struct ShapeKit {
       return cheb_step_bulk_kernel<real, valT, R, CPT, S, MINB, OPT, FIRST, DBL, SEG>;
     else if constexpr (KIND == 2)
       return cheb_step_ring2_kernel<real, valT, R, CPT, S, MINB, RPT, SVEC != 0, FIRST, DBL, SEG>;
+    else if constexpr (KIND == 3)
+      return cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), FIRST, DBL, SEG>;
     else
       return cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG>;
   }
@@ -828,14 +1048,30 @@ struct ShapeKit {
     const int64_t cap = (int64_t)per_sm(dbl) * sm_count();
     return static_cast<int>(need < cap ? need : cap);
   }
+  // the band plan of this shape's tiles (kind 3 only)
+  static tb_status plan(int64_t n, int64_t rows_avail, const int64_t *slice_ptr, const int32_t *col, BandRec *recs,
+                        uint16_t *lidx, cudaStream_t st) {
+    if constexpr (KIND == 3) {
+      const int64_t tiles = (n + RPB - 1) / RPB;
+      const int64_t cap = (int64_t)sm_count() * 4;
+      band_plan_kernel<RPB><<<(unsigned)(tiles < cap ? tiles : cap), 256, 0, st>>>(n, slice_ptr, col, BROWS, kRowAlign,
+                                                                                   rows_avail, recs, lidx);
+      TB_CHECK_LAUNCH();
+    }
+    return TB_OK;
+  }
   template <bool FIRST, bool DBL, bool SEG>
   static tb_status step(int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                         const valT *diag, const real *x, const real *prev, const real *v0, real *out,
                         double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
-                        const BatchTables &bt, cudaStream_t st) {
+                        const BatchTables &bt, cudaStream_t st, const BandPlan &bp = BandPlan()) {
     if constexpr (KIND == 0)
       cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
+    else if constexpr (KIND == 3)
+      cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), FIRST, DBL, SEG><<<grid, kBlock, smem<DBL>(), st>>>(
+          n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt, bp.recs,
+          bp.lidx);
     else
       kernel<FIRST, DBL, SEG>()<<<grid, kBlock, smem<DBL>(), st>>>(n, slice_ptr, col, val, diag, x, prev, v0, out,
                                                                   partial, alpha, shift, flags, slot_stride, bt);
@@ -847,7 +1083,7 @@ struct ShapeKit {
 template <typename real, typename valT, int R, int I>
 using KitOf = ShapeKit<real, valT, R, Shapes<real, R>::at[I].cpt, Shapes<real, R>::at[I].kind,
                        Shapes<real, R>::at[I].stages, Shapes<real, R>::at[I].minb, Shapes<real, R>::at[I].rpt,
-                       Shapes<real, R>::at[I].svec, Shapes<real, R>::at[I].opt>;
+                       Shapes<real, R>::at[I].svec, Shapes<real, R>::at[I].opt, Shapes<real, R>::at[I].brows>;
 
 // Call f(KitOf<..., I>{}) for the runtime shape index `id`.
 template <typename real, typename valT, int R, int I = 0, typename F>
@@ -875,8 +1111,28 @@ struct StepKit {
     return visit_shape<real, valT, R>(shape, [](auto k) { return decltype(k)::RPB; });
   }
   static bool pipelined(int shape) { return Shapes<real, R>::at[shape].kind != 0; }
-  // the second ring bulk-copies the diagonal too
-  static bool stages_diag(int shape) { return Shapes<real, R>::at[shape].kind == 2; }
+  static bool banded(int shape) { return Shapes<real, R>::at[shape].kind == 3; }
+  // band-plan storage of the banded shapes (records of the smallest tile,
+  // kBandSlots local indices per row of the padded rows)
+  static size_t plan_records(int64_t n) {
+    int t = kBlock;
+    for (int s = 0; s < kShapes; ++s)
+      if (banded(s)) t = std::min(t, rows_per_block(s));
+    return (size_t)((n + t - 1) / t);
+  }
+  static bool any_banded() {
+    for (int s = 0; s < kShapes; ++s)
+      if (banded(s)) return true;
+    return false;
+  }
+  static tb_status plan(int shape, int64_t n, int64_t rows_avail, const int64_t *slice_ptr, const int32_t *col,
+                        BandRec *recs, uint16_t *lidx, cudaStream_t st) {
+    return visit_shape<real, valT, R>(shape, [&](auto k) {
+      return decltype(k)::plan(n, rows_avail, slice_ptr, col, recs, lidx, st);
+    });
+  }
+  // the second ring and the banded step bulk-copy the diagonal too
+  static bool stages_diag(int shape) { return Shapes<real, R>::at[shape].kind >= 2; }
   // the largest grid and the smallest block over every shape and mode, so that
   // a workspace sized once fits whichever shape a later call takes
   static int max_grid(int64_t n) {
@@ -899,10 +1155,10 @@ struct StepKit {
   static tb_status step(int shape, int grid, int64_t n, const int64_t *slice_ptr, const int32_t *col,
                         const valT *val, const valT *diag, const real *x, const real *prev, const real *v0,
                         real *out, double *partial, real alpha, real shift, int *flags, int64_t slot_stride,
-                        const BatchTables &bt, cudaStream_t st) {
+                        const BatchTables &bt, cudaStream_t st, const BandPlan &bp = BandPlan()) {
     return visit_shape<real, valT, R>(shape, [&](auto k) {
       return decltype(k)::template step<FIRST, DBL, SEG>(grid, n, slice_ptr, col, val, diag, x, prev, v0, out,
-                                                         partial, alpha, shift, flags, slot_stride, bt, st);
+                                                         partial, alpha, shift, flags, slot_stride, bt, st, bp);
     });
   }
 };

@@ -274,6 +274,10 @@ struct LsqtRunner {
     for (int k = 0; k < kVectors; ++k) cv.take<real>((size_t)padded_rows(n) * R * 2);
     cv.take<double>((size_t)(M + 1) * Kit::max_grid(n) * R);
     cv.take<int>(4);
+    if (Kit::any_banded()) {
+      cv.take<BandRec>(Kit::plan_records(n));
+      cv.take<uint16_t>((size_t)padded_rows(n) * kBandSlots);
+    }
     return cv.used + 256;
   }
 
@@ -335,12 +339,27 @@ struct LsqtRunner {
     Carver cv(ws, wsb);
     real *vec[kVectors];
     for (int k = 0; k < kVectors; ++k) vec[k] = cv.take<real>((size_t)np * R * 2);
-    double *partial = cv.take<double>((size_t)(M + 1) * grid * R);
+    double *partial = cv.take<double>((size_t)(M + 1) * Kit::max_grid(n) * R);
     int *flags = cv.take<int>(4);
+    BandPlan bp;
+    BandRec *recs = nullptr;
+    uint16_t *lidx = nullptr;
+    if (Kit::any_banded()) {
+      recs = cv.take<BandRec>(Kit::plan_records(n));
+      lidx = cv.take<uint16_t>((size_t)np * kBandSlots);
+    }
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "lsqt_vac: workspace too small (%zu < %zu)", wsb, cv.used);
     if (Kit::pipelined(shape) && ((reinterpret_cast<uintptr_t>(col) | reinterpret_cast<uintptr_t>(val)) & 15))
       return fail(TB_ERR_INVALID_ARG, "lsqt_vac: col and val must be 16-byte aligned");
+    if (Kit::stages_diag(shape) && (reinterpret_cast<uintptr_t>(diag) & 15))
+      return fail(TB_ERR_INVALID_ARG, "lsqt_vac: diag must be 16-byte aligned");
     Kit::prepare(shape);
+    if (Kit::banded(shape)) {
+      bp.recs = recs;
+      bp.lidx = lidx;
+      const tb_status sp_ = Kit::plan(shape, n, np, sp, col, recs, lidx, st);
+      if (sp_ != TB_OK) return sp_;
+    }
     real *phi_l = vec[0], *phi_r = vec[1], *w = vec[2], *A = vec[3], *B = vec[4], *x1 = vec[5], *acc = vec[6];
     std::vector<double> cr, ci;
     propagator_coefficients(a, b, dt, cr, ci);
@@ -368,13 +387,14 @@ struct LsqtRunner {
       TB_CHECK_LAUNCH();
       // T_m(H~) phi_R, m = 1 .. M-1, dotted with w (A, B alternate; v_2 reads prev = phi_R)
       s = Kit::template step<true, false, false>(shape, grid, n, sp, col, val, diag, phi_r, nullptr, w, A, partial + ps,
-                                                 inv_a, shift, flags, ps, bt, st);
+                                                 inv_a, shift, flags, ps, bt, st, bp);
       for (int m = 2; m < M && s == TB_OK; ++m) {
         real *out = (m & 1) ? A : B;
         const real *x = (m & 1) ? B : A;
         const real *prev = (m == 2) ? phi_r : out;
         s = Kit::template step<false, false, false>(shape, grid, n, sp, col, val, diag, x, prev, w, out,
-                                                    partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st);
+                                                    partial + (size_t)m * ps, two_over_a, shift, flags, ps, bt, st,
+                                                    bp);
       }
       if (s != TB_OK) break;
       moment_reduce_kernel<<<(M * R + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, 0, 0.0,

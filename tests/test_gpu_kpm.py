@@ -38,7 +38,7 @@ def gputb():
     return g
 
 
-@pytest.fixture(params=range(7), ids=lambda k: f"shape{k}")
+@pytest.fixture(params=range(10), ids=lambda k: f"shape{k}")
 def shape(request, gputb):
     """Every compiled launch shape of the Chebyshev step (direct loads, or a
     bulk-copy ring of 2-4 stages, with 1, 2 or 4 complex numbers per thread
@@ -226,3 +226,36 @@ def test_bounded_wait_gives_up_and_leaves_the_context_usable(gputb, cfg800):
     mu = gputb.kpm_moments(Hd, a, b, 64, 2, 3).cpu().numpy()
     _, mu_ref = okpm.kpm_moments(H, a, b, 64, 2, 3)
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+
+
+@pytest.mark.parametrize("R,dtype", [(1, torch.float32), (8, torch.float32), (16, torch.float32), (8, torch.float64)])
+def test_scattered_columns_take_the_gather_path(gputb, shape, R, dtype):
+    """A random symmetric pattern (about 10 neighbours per row, anywhere in
+    the matrix): slices fit the banded step's 16 slots, but a tile's columns
+    fall in far more than 6 bands, so the banded shapes take their
+    global-gather path for every tile; mixed with a cell-ordered block where
+    tiles are banded."""
+    import scipy.sparse as sp
+    use_shape(gputb, shape, R, dtype)
+    rng = np.random.default_rng(17)
+    n = 3000
+    A = sp.random(n, n, density=5 / n, random_state=rng, format="csr")
+    A = (A + A.T).tocsr()
+    A.setdiag(0)
+    A.eliminate_zeros()
+    # rows 2000.. get a banded nearest-neighbour chain instead
+    A = A.tolil()
+    for i in range(2000, n):
+        A.rows[i], A.data[i] = [], []
+    A = A.tocsr()
+    chain = sp.diags([np.full(999, -1.0), np.full(999, -1.0)], [-1, 1], shape=(1000, 1000), format="csr")
+    A = sp.bmat([[A[:2000, :2000], None], [None, chain]], format="csr")
+    A.sort_indices()
+    onsite = rng.uniform(-0.3, 0.3, n)
+    H = oha.csr_hamiltonian(n, A.indptr, A.indices, A.data, onsite)
+    _, _, a, b = obo.spectral_bounds(H, 64, 7)
+    Hd = sell_matrix(A.indptr, A.indices, A.data, onsite, n, dtype)
+    for doubling in (False, True):
+        mu = gputb.kpm_moments(Hd, a, b, 64, R, 77, doubling=doubling).cpu().numpy()
+        _, mu_ref = okpm.kpm_moments(H, a, b, 64, R, 77)
+        assert np.max(np.abs(mu - mu_ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
