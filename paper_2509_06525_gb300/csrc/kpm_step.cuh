@@ -222,8 +222,9 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
 // counts).  All warps compute on one stage while the next ones are in
 // flight, and the neighbour gathers take their indices from shared memory,
 // so a row's gathers are issued without waiting for its column loads.  A
-// tile whose slices are wider than kFastW falls back to direct loads of col
-// and val.  Every wait is bounded: on timeout the CTA drains its own copies
+// tile with more elements than a stage holds (TR x kFastW) falls back to
+// direct loads of col and val; a slice wider than kFastW in a tile that fits
+// loops over its slots in shared memory.  Every wait is bounded: on timeout the CTA drains its own copies
 // (bounded again), raises flags[0] |= 4 and returns.
 // ---------------------------------------------------------------------------
 constexpr long long kWaitPolls = 1ll << 21;
@@ -436,8 +437,21 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
         const int32_t *cs = s_col(st) + (sb - e0) + (i & 31);
         const valT *vs = s_val(st) + (sb - e0) + (i & 31);
         const real *xp = x + part * CPT * 2;
-        if ((OPT & 1) && w <= 12) row_product_smem<real, valT, R, CPT, 12>(cs, vs, xp, w, y);
-        else row_product_smem<real, valT, R, CPT, kFastW>(cs, vs, xp, w, y);
+        if ((OPT & 1) && w <= 12) {
+          row_product_smem<real, valT, R, CPT, 12>(cs, vs, xp, w, y);
+        } else if (w <= kFastW) {
+          row_product_smem<real, valT, R, CPT, kFastW>(cs, vs, xp, w, y);
+        } else {
+          // a slice wider than kFastW inside a tile that still fits the stage
+#pragma unroll 1
+          for (int s = 0; s < w; ++s) {
+            real xv[2 * CPT];
+            const real h = static_cast<real>(vs[32 * s]);
+            ld_gather<real, CPT>(xp + (int64_t)cs[32 * s] * (R * 2), xv);
+#pragma unroll
+            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+          }
+        }
       } else {
         int64_t e = sb + (i & 31);
         for (int s = 0; s < w; ++s, e += 32) {
