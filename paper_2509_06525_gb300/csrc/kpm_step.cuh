@@ -751,9 +751,13 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   }
   __syncthreads();
 
-  bool ok = true;   // thread 0: its own record waits
-  // producer side (thread 0 only)
-  auto fetch_rec = [&](int64_t kk) {   // record of local tile kk into the record ring
+  bool ok = true;   // warp 0: its record waits
+  // producer side (warp 0): lane 0 keeps the records one tile ahead; after a
+  // record arrives every lane reads it and the lanes issue the tile's copies
+  // in parallel (lane b < nb: band b; lanes 8..12: indices, values, diagonal,
+  // vector rows)
+  const int lane = threadIdx.x & 31;
+  auto fetch_rec = [&](int64_t kk) {   // record of local tile kk into the record ring (lane 0)
     const int slot = static_cast<int>(kk & 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(recbar + slot, sizeof(BandRec));
@@ -761,48 +765,57 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   };
   auto issue = [&](int64_t kk) -> bool {
     const int slot = static_cast<int>(kk & 1);
-    if (!mbar_wait_bounded(recbar + slot, static_cast<uint32_t>((kk >> 1) & 1))) {
+    const bool got = mbar_wait_bounded(recbar + slot, static_cast<uint32_t>((kk >> 1) & 1));
+    if (!__all_sync(0xffffffffu, got)) {
       ok = false;
       return false;
     }
     const int64_t tile = tile_of(kk);
     const int st = static_cast<int>(kk % STAGES);
     const int64_t r0 = tile * TR;
+    const BandRec &rc = rring[slot];
     BandRec *dst = s_rec(st);
-    *dst = rring[slot];
-    const BandRec &rc = *dst;
-    if (kk + 1 < my_tiles) fetch_rec(kk + 1);   // the ring slot of kk - 1 is free
-    const bool banded = rc.nb > 0;
+    if (lane < 8) reinterpret_cast<int4 *>(dst)[lane] = reinterpret_cast<const int4 *>(&rc)[lane];
+    const int nb = rc.nb;
+    const bool banded = nb > 0;
     const bool whole = r0 + TR <= n;
     const uint32_t cnt = static_cast<uint32_t>(rc.srel[TR / 32 < 9 ? TR / 32 : 8]);
-    uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
-    uint32_t xrows = 0;
-    if (banded) {
-      for (int b = 0; b < rc.nb; ++b) xrows += static_cast<uint32_t>(rc.len[b]);
-      tx += cnt * (2u + static_cast<uint32_t>(sizeof(valT))) + xrows * static_cast<uint32_t>(G::kRowBytes);
-      if (diag && whole) tx += TR * sizeof(valT);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(full + st, tx);
-    if (banded) {
-      if (cnt > 0) {
-        bulk_g2s(s_idx(st), lidx + tile * (int64_t)TR * kBandSlots, cnt * 2u, full + st);
-        bulk_g2s(s_val(st), val + rc.e0, cnt * static_cast<uint32_t>(sizeof(valT)), full + st);
+    const int lo_b = lane < kBandMax ? rc.lo[lane] : 0;
+    const int len_b = lane < kBandMax ? rc.len[lane] : 0;
+    const int off_b = lane < kBandMax ? rc.off[lane] : 0;
+    const int64_t e0 = rc.e0;
+    __syncwarp();   // every lane has read the ring slot and the stage record is written
+    if (lane == 0) {
+      uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
+      if (banded) {
+        uint32_t xrows = 0;
+        for (int b = 0; b < nb; ++b) xrows += static_cast<uint32_t>(rc.len[b]);
+        tx += cnt * (2u + static_cast<uint32_t>(sizeof(valT))) + xrows * static_cast<uint32_t>(G::kRowBytes);
+        if (diag && whole) tx += TR * sizeof(valT);
       }
-      if (diag && whole) bulk_g2s(s_diag(st), diag + r0, TR * sizeof(valT), full + st);
-      for (int b = 0; b < rc.nb; ++b)
-        bulk_g2s(s_x(st) + (size_t)rc.off[b] * RE, x + (size_t)rc.lo[b] * RE,
-                 static_cast<uint32_t>(rc.len[b]) * static_cast<uint32_t>(G::kRowBytes), full + st);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(full + st, tx);
+      if (kk + 1 < my_tiles) fetch_rec(kk + 1);   // the ring slot of kk - 1 is free
+    }
+    __syncwarp();
+    if (banded) {
+      if (lane < nb)
+        bulk_g2s(s_x(st) + (size_t)off_b * RE, x + (size_t)lo_b * RE,
+                 static_cast<uint32_t>(len_b) * static_cast<uint32_t>(G::kRowBytes), full + st);
+      if (lane == 8 && cnt > 0) bulk_g2s(s_idx(st), lidx + tile * (int64_t)TR * kBandSlots, cnt * 2u, full + st);
+      if (lane == 9 && cnt > 0)
+        bulk_g2s(s_val(st), val + e0, cnt * static_cast<uint32_t>(sizeof(valT)), full + st);
+      if (lane == 10 && diag && whole) bulk_g2s(s_diag(st), diag + r0, TR * sizeof(valT), full + st);
     }
     const size_t voff = (size_t)r0 * RE;
-    if (!FIRST) bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
-    if (!DBL) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    if (!FIRST && lane == 11) bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    if (!DBL && lane == 12) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
     return true;
   };
 
   int64_t issued = 0;
-  if (threadIdx.x == 0 && my_tiles > 0) {
-    fetch_rec(0);
+  if (threadIdx.x < 32 && my_tiles > 0) {
+    if (lane == 0) fetch_rec(0);
     while (issued < my_tiles && issued < STAGES && issue(issued)) ++issued;
   }
 
@@ -812,7 +825,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   for (; kk < my_tiles; ++kk) {
     const int st = static_cast<int>(kk % STAGES);
     const uint32_t parity = static_cast<uint32_t>((kk / STAGES) & 1);
-    const bool mine = threadIdx.x != 0 || ok;
+    const bool mine = threadIdx.x >= 32 || ok;
     ok = __syncthreads_and(mine && mbar_wait_bounded(full + st, parity)) != 0;
     if (!ok) break;
     const int64_t tile = tile_of(kk);
@@ -839,7 +852,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
         const real *xs = s_x(st) + part * CPT * 2;
         const uint16_t *li = s_idx(st) + sb + (lr & 31);
         const valT *vs = s_val(st) + sb + (lr & 31);
-#pragma unroll
+        // 64-register budgets (4 CTAs) keep four slots in flight, larger ones all
+#pragma unroll(MINB >= 4 ? 4 : kBandSlots)
         for (int s = 0; s < kBandSlots; ++s) {
           if (s < w) {
             real xv[2 * CPT];
@@ -858,7 +872,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     }
     if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
     __syncthreads();  // every thread is done with this stage
-    if (threadIdx.x == 0 && issued < my_tiles && ok && issue(issued)) ++issued;
+    if (threadIdx.x < 32 && issued < my_tiles && ok && issue(issued)) ++issued;
   }
   if (!ok) {
     if (threadIdx.x == 0) {
