@@ -103,3 +103,61 @@ def test_species_mixing_is_applied_per_ordered_pair():
     # the ordered pair matters: (B, N) and (N, B) mix differently
     c_rev = de.mixed_descriptor(r[:1], zj[:1], zi[:1], cmix, 3.0)
     assert not np.allclose(C[0], c_rev[0])
+
+
+def _chain3():
+    """Three atoms on an open line, 1.42 A apart (no periodic direction):
+    neighbours within 3 A by hand: 0 -> {1, 2}, 1 -> {0, 2}, 2 -> {0, 1};
+    bond lengths 1.42 (0-1, 1-2) and 2.84 (0-2)."""
+    pos = np.array([[0.0, 0.0, 0.0], [1.42, 0.0, 0.0], [2.84, 0.0, 0.0]]) + 10.0
+    box = np.diag([40.0, 40.0, 40.0])
+    pbc = np.array([0, 0, 0], np.int32)
+    return pos, box, pbc
+
+
+def _f_library(r, rc=3.0, k=8):
+    """f_k(r) = (T_k(2(r/rc - 1)^2 - 1) + 1)/2 * (1 + cos(pi r/rc))/2 with T_k
+    from numpy's Chebyshev series routine (a library evaluation, not the
+    oracle's recurrence)."""
+    xx = 2.0 * (r / rc - 1.0) ** 2 - 1.0
+    t = np.array([npcheb.chebval(xx, np.eye(k)[m]) for m in range(k)])
+    return 0.5 * (t + 1.0) * 0.5 * (1.0 + math.cos(math.pi * r / rc))
+
+
+def test_edge_input_blocks_and_onsite_receiver_on_an_open_chain():
+    """Eq. 2 / the per-pair network's input and outputs on a chain where the
+    two endpoints of a bond have different environments (v_0 != v_1): the
+    edge input of 0 -> 1 is [C(r_01), v_0, v_1, C(r_01) (v_0 + v_1)] -- the
+    source atom's block first -- and the onsite share y1(i -> j) goes to the
+    source atom i, the hopping H_ij to (y0(i->j) + y0(j->i))/2.  Swapping the
+    v blocks, or crediting y1 to j, fails here."""
+    pos, box, pbc = _chain3()
+    indptr, idx, d = nb.neighbors(pos, box, pbc, 3.0)
+    assert list(idx[indptr[0]:indptr[1]]) == [1, 2]
+    assert list(idx[indptr[1]:indptr[2]]) == [0, 2]
+    assert list(idx[indptr[2]:indptr[3]]) == [0, 1]
+    cmix = synth.descriptor_mixing("identity")
+    species = np.zeros(3, np.int32)
+    C, v, x = de.descriptors(species, indptr, idx, d, cmix, 3.0)
+    f1, f2 = _f_library(1.42), _f_library(2.84)
+    v0, v1 = f1 + f2, 2.0 * f1
+    np.testing.assert_allclose(v[0], v0, atol=1e-13)
+    np.testing.assert_allclose(v[1], v1, atol=1e-13)
+    np.testing.assert_allclose(v[2], v0, atol=1e-13)
+    assert np.max(np.abs(v0 - v1)) > 1e-2
+    e01 = indptr[0] + 0          # edge 0 -> 1
+    expect = np.concatenate([f1, v0, v1, f1 * (v0 + v1)])
+    np.testing.assert_allclose(x[e01], expect, atol=1e-13)
+    e10 = indptr[1] + 0          # edge 1 -> 0: the blocks swap with the direction
+    np.testing.assert_allclose(x[e10], np.concatenate([f1, v1, v0, f1 * (v1 + v0)]), atol=1e-13)
+
+    from oracle import mlp as om
+    # distinctive outputs per directed edge: y0 = 100 i + j, y1 = 10 i + j
+    rows = np.repeat(np.arange(3), np.diff(indptr))
+    y = np.stack([100.0 * rows + idx, 10.0 * rows + idx], axis=1)
+    hop, eps = om.learned_hamiltonian(indptr, idx, y, species, np.array([0.5, 0.0, 0.0]))
+    np.testing.assert_allclose(eps, [0.5 + 1 + 2, 0.5 + 10 + 12, 0.5 + 20 + 21])
+    # H_01 = (y0(0->1) + y0(1->0)) / 2 = (1 + 100) / 2, H_02 = (2 + 200) / 2, H_12 = (102 + 201) / 2
+    np.testing.assert_allclose(hop[indptr[0]:indptr[1]], [50.5, 101.0])
+    np.testing.assert_allclose(hop[indptr[1]:indptr[2]], [50.5, 151.5])
+    np.testing.assert_allclose(hop[indptr[2]:indptr[3]], [101.0, 151.5])
