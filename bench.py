@@ -214,10 +214,21 @@ class Pipeline:
         return mu, rho
 
     def step_e2e(self, kind, dtype):
-        pos = self.pos_host.to("cuda", non_blocking=True)
-        spc = self.spc_host.to("cuda", non_blocking=True)
-        mu, rho = self.step(pos, spc, kind, dtype, record=False)
-        return mu.cpu(), rho.cpu()
+        """The step from page-locked host arrays: positions and species enter
+        through tb_copy_to_device, the moments and the DOS leave through
+        tb_copy_to_host (the C ABI's host boundary)."""
+        g = self.g
+        if not hasattr(self, "pos_e2e"):
+            self.pos_e2e = torch_empty_like_device(self.pos_host)
+            self.spc_e2e = torch_empty_like_device(self.spc_host)
+            self.mu_host = self.torch.empty((self.R, self.M), dtype=self.torch.float64).pin_memory()
+            self.rho_host = self.torch.empty(self.w["K"], dtype=self.torch.float64).pin_memory()
+        g.copy_to_device(self.pos_e2e, self.pos_host)
+        g.copy_to_device(self.spc_e2e, self.spc_host)
+        mu, rho = self.step(self.pos_e2e, self.spc_e2e, kind, dtype, record=False)
+        g.copy_to_host(self.mu_host, mu)
+        g.copy_to_host(self.rho_host, rho)
+        return self.mu_host, self.rho_host
 
 
 def step_bytes(nnz, n_atoms, R, sv, sc, has_diag, doubling, shape_desc):
@@ -233,6 +244,11 @@ def step_bytes(nnz, n_atoms, R, sv, sc, has_diag, doubling, shape_desc):
     else:
         matrix = nnz * (sv + 4)
     return matrix + (n_atoms * sv if has_diag else 0) + n_atoms * R * streams * sc
+
+
+def torch_empty_like_device(host):
+    import torch
+    return torch.empty(host.shape, dtype=host.dtype, device="cuda")
 
 
 def timed(torch, dist, fn, steps, warmup):

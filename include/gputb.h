@@ -92,6 +92,15 @@ TB_API const char *tb_last_error(void);
 /* Number of kernel launches this process has issued through the library. */
 TB_API int64_t tb_launch_count(void);
 
+/* Host <-> device boundary (no counterpart in the paper).  Every other call
+ * takes device arrays; host inputs (positions, species) enter through
+ * tb_copy_to_device and results (moments, DOS) leave through
+ * tb_copy_to_host, each one cudaMemcpyAsync on `stream` (page-locked host
+ * memory makes them asynchronous DMA transfers).  tb_copy_to_host
+ * synchronises `stream` before returning, so the host array is filled. */
+TB_API tb_status tb_copy_to_device(void *dst_device, const void *src_host, size_t bytes, void *stream);
+TB_API tb_status tb_copy_to_host(void *dst_host, const void *src_device, size_t bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * KPM moments (Sec. 2.4: Chebyshev expansion, KPM, SpMV, random phases).
  *
@@ -439,6 +448,7 @@ TB_API tb_status tb_build_neighbors(const double *positions, int64_t n, const do
  *   hop_prefactor  host double [3][3] P (eV);  onsite  host double [3] (eV)
  *   val            device float/double [slice_ptr[last]] output
  *   diag           device float/double [N] output (onsite), or NULL
+ *   workspace      device, >= 256 bytes, 256-byte aligned (the species check)
  * Synchronises `stream`.
  * ------------------------------------------------------------------- */
 TB_API tb_status tb_build_hamiltonian_teacher(const double *positions, const int32_t *species, int64_t n,
@@ -447,7 +457,8 @@ TB_API tb_status tb_build_hamiltonian_teacher(const double *positions, const int
                                               const int32_t *cnt, const int32_t *ncount,
                                               const double *hop_prefactor, const double *onsite,
                                               double a_cc, double beta, double gamma, double rcut,
-                                              int32_t precision, void *val, void *diag, void *stream);
+                                              int32_t precision, void *val, void *diag, void *workspace,
+                                              size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------------
  * FP64 spectral bounds for the Chebyshev rescaling of Sec. 2.4.
@@ -506,11 +517,21 @@ TB_API tb_status tb_edge_features(const double *positions, const int32_t *specie
                                   const float *inv_std, float *x_raw, void *x_bf16, void *stream);
 
 /* Per-feature mean and standard deviation (population) of x_raw over the
- * real (non-padding) elements of rows 0..n-1, accumulated in FP64.
- * workspace >= 96 * 8 * 4 * (SM count) bytes. */
+ * real (non-padding) elements of rows 0..n-1, accumulated in FP64, and,
+ * when inv_std (device float [32]) is given, the input normalisation
+ *   inv_std[f] = mask[f] / max(std[f], 1e-6)
+ * with mask (device float [32], may be NULL = all ones) switching features
+ * off.  workspace >= 96 * 8 * 4 * (SM count) bytes. */
 TB_API tb_status tb_feature_stats(const float *x_raw, int64_t n, const int64_t *slice_ptr,
-                                  const int32_t *cnt, float *mean, float *stdv, void *workspace,
-                                  size_t workspace_bytes, void *stream);
+                                  const int32_t *cnt, float *mean, float *stdv, float *inv_std,
+                                  const float *mask, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+/* inv_std[f] = mask[f] / max(stdv[f], 1e-6) for f < n (device float arrays;
+ * mask may be NULL): the normalisation of tb_feature_stats for a caller's
+ * own standard deviations. */
+TB_API tb_status tb_inverse_std(const float *stdv, const float *mask, float *inv_std, int32_t n,
+                                void *stream);
 
 /* Workspace bytes of tb_mlp_backward for n_edges edges. */
 TB_API size_t tb_mlp_workspace_size(int64_t n_edges);

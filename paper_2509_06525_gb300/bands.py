@@ -112,6 +112,11 @@ class BandTrainer:
 
     def __init__(self, model: g.EnvModel, batch: CellBatch, max_sweeps: int = 30, group=None,
                  n_cells_total: Optional[int] = None):
+        import torch.distributed as dist
+        several = dist.is_initialized() and dist.get_world_size(group) > 1
+        if several and n_cells_total is None:
+            raise ValueError("a process group of several ranks needs n_cells_total (the cells of all ranks); "
+                             "without it each rank would train on its own cells with no exchange")
         self.model, self.batch, self.max_sweeps = model, batch, max_sweeps
         dev = batch.feat.device
         self.grad = torch.empty(g.ENV_NPARAM, dtype=torch.float32, device=dev)
@@ -122,10 +127,7 @@ class BandTrainer:
         self.stats = torch.zeros(3, dtype=torch.float64, device=dev)
         self.group = group
         self.n_cells_total = batch.n_cells if n_cells_total is None else int(n_cells_total)
-        self.sharded = False
-        if n_cells_total is not None:
-            import torch.distributed as dist
-            self.sharded = dist.is_initialized() and dist.get_world_size(group) > 1
+        self.sharded = n_cells_total is not None and several
         if self.sharded:
             from .distributed import gather_blocks
             self.e_ref_all = gather_blocks(batch.e_ref, self.n_cells_total, group)

@@ -45,3 +45,22 @@ int sm_count() {
 extern "C" int32_t tb_abi_version(void) { return GPUTB_ABI_VERSION; }
 extern "C" const char *tb_last_error(void) { return gputb::g_err; }
 extern "C" int64_t tb_launch_count(void) { return gputb::g_launches.load(); }
+
+// Host <-> device copies of the C ABI (the boundary where host arrays enter
+// and results leave): one cudaMemcpyAsync on `stream`; the copy to the host
+// synchronises the stream so the data is there when the call returns.
+extern "C" tb_status tb_copy_to_device(void *dst_device, const void *src_host, size_t bytes, void *stream) {
+  TB_REQUIRE(bytes == 0 || (dst_device && src_host), "tb_copy_to_device: null pointer argument");
+  if (bytes == 0) return TB_OK;
+  TB_CUDA(cudaMemcpyAsync(dst_device, src_host, bytes, cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)));
+  return TB_OK;
+}
+
+extern "C" tb_status tb_copy_to_host(void *dst_host, const void *src_device, size_t bytes, void *stream) {
+  TB_REQUIRE(bytes == 0 || (dst_host && src_device), "tb_copy_to_host: null pointer argument");
+  if (bytes == 0) return TB_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TB_CUDA(cudaMemcpyAsync(dst_host, src_device, bytes, cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  return TB_OK;
+}

@@ -309,6 +309,17 @@ __global__ void feature_stats_kernel(const float *__restrict__ xraw, int64_t n, 
   }
 }
 
+// inv_std[f] = mask[f] / max(std[f], kStdFloor) (mask 1 when absent): the
+// normalisation factor of the network inputs; features with a zero mask
+// are switched off
+constexpr float kStdFloor = 1e-6f;
+__global__ void inverse_std_kernel(const float *__restrict__ stdv, const float *__restrict__ mask,
+                                   float *__restrict__ inv_std, int n) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  inv_std[f] = (mask ? mask[f] : 1.0f) / fmaxf(stdv[f], kStdFloor);
+}
+
 __global__ void feature_stats_finish(const double *__restrict__ part, int grid, float *__restrict__ mean,
                                      float *__restrict__ stdv) {
   const int f = threadIdx.x;
@@ -1046,8 +1057,8 @@ extern "C" tb_status tb_edge_features(const double *positions, const int32_t *sp
 }
 
 extern "C" tb_status tb_feature_stats(const float *x_raw, int64_t n, const int64_t *slice_ptr, const int32_t *cnt,
-                                      float *mean, float *stdv, void *workspace, size_t workspace_bytes,
-                                      void *stream) {
+                                      float *mean, float *stdv, float *inv_std, const float *mask, void *workspace,
+                                      size_t workspace_bytes, void *stream) {
   TB_REQUIRE(n >= 1 && x_raw && slice_ptr && cnt && mean && stdv && workspace, "tb_feature_stats: bad argument");
   const int grid = grid_cap((n + 7) / 8, 4);
   if (workspace_bytes < (size_t)grid * 96 * sizeof(double))
@@ -1057,6 +1068,17 @@ extern "C" tb_status tb_feature_stats(const float *x_raw, int64_t n, const int64
   feature_stats_kernel<<<grid, 256, 0, st>>>(x_raw, n, slice_ptr, cnt, part);
   TB_CHECK_LAUNCH();
   feature_stats_finish<<<1, 32, 0, st>>>(part, grid, mean, stdv);
+  TB_CHECK_LAUNCH();
+  if (inv_std) {
+    inverse_std_kernel<<<1, 32, 0, st>>>(stdv, mask, inv_std, 32);
+    TB_CHECK_LAUNCH();
+  }
+  return TB_OK;
+}
+
+extern "C" tb_status tb_inverse_std(const float *stdv, const float *mask, float *inv_std, int32_t n, void *stream) {
+  TB_REQUIRE(n >= 1 && n <= (1 << 20) && stdv && inv_std, "tb_inverse_std: bad argument");
+  inverse_std_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(stdv, mask, inv_std, n);
   TB_CHECK_LAUNCH();
   return TB_OK;
 }

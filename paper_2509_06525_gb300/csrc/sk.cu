@@ -28,10 +28,14 @@ constexpr int kSkThreads = 128;
 constexpr float kR3 = 1.7320508075688772f;
 
 // 13 planes: l, m, n, then V_0..V_9 (ss_s, sp_s, pp_s, pp_p, sd_s, pd_s, pd_p, dd_s, dd_p, dd_d)
+// the ten SK bond integrals at r = a_cc, passed by value (kernel parameter space)
+struct SkV0 {
+  float v[10];
+};
+
 __global__ void sk_geometry_kernel(const double *__restrict__ pos, int64_t n, int64_t n_slices, Box B,
                                    const int64_t *__restrict__ sp, const int32_t *__restrict__ col, int64_t total,
-                                   const float *__restrict__ v0, double a_cc, double beta, double rcut,
-                                   float *__restrict__ geom) {
+                                   const SkV0 v0, double a_cc, double beta, double rcut, float *__restrict__ geom) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_slices * 32) return;
   const int64_t sb = sp[i >> 5];
@@ -54,7 +58,7 @@ __global__ void sk_geometry_kernel(const double *__restrict__ pos, int64_t n, in
           const double ch = cospi(0.5 * r / rcut);
           const double radial = exp(-beta * (r / a_cc - 1.0)) * ch * ch;
 #pragma unroll
-          for (int k = 0; k < 10; ++k) g[3 + k] = (float)((double)v0[k] * radial);
+          for (int k = 0; k < 10; ++k) g[3 + k] = (float)((double)v0.v[k] * radial);
         }
       }
     }
@@ -320,16 +324,12 @@ extern "C" tb_status tb_sk_geometry(const double *positions, int64_t n, const do
   tb_status s = make_box(box, pbc, rcut, &B);
   if (s != TB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  float *dv0 = nullptr;
-  TB_CUDA(cudaMallocAsync(&dv0, 10 * sizeof(float), st));
-  float hv[10];
-  for (int k = 0; k < 10; ++k) hv[k] = (float)v0[k];
-  TB_CUDA(cudaMemcpyAsync(dv0, hv, sizeof(hv), cudaMemcpyHostToDevice, st));
+  SkV0 hv;
+  for (int k = 0; k < 10; ++k) hv.v[k] = (float)v0[k];
   const int64_t n_slices = (n + 31) / 32;
   sk_geometry_kernel<<<(unsigned)((n_slices * 32 + 255) / 256), 256, 0, st>>>(positions, n, n_slices, B, slice_ptr,
-                                                                               col, total, dv0, a_cc, beta, rcut, geom);
+                                                                               col, total, hv, a_cc, beta, rcut, geom);
   TB_CHECK_LAUNCH();
-  TB_CUDA(cudaFreeAsync(dv0, st));
   TB_CUDA(cudaStreamSynchronize(st));
   return TB_OK;
 }

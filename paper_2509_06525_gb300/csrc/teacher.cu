@@ -84,12 +84,15 @@ extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const
                                                   const int32_t *col, const int32_t *cnt, const int32_t *ncount,
                                                   const double *hop_prefactor, const double *onsite, double a_cc,
                                                   double beta, double gamma, double rcut, int32_t precision,
-                                                  void *val, void *diag, void *stream) {
+                                                  void *val, void *diag, void *workspace, size_t workspace_bytes,
+                                                  void *stream) {
   TB_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "tb_build_hamiltonian_teacher: bad n");
   TB_REQUIRE(positions && species && slice_ptr && cnt && ncount && hop_prefactor && onsite,
              "tb_build_hamiltonian_teacher: null pointer argument");
   TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian_teacher: bad precision");
   TB_REQUIRE(a_cc > 0.0 && rcut > 0.0, "tb_build_hamiltonian_teacher: need a_cc > 0 and rcut > 0");
+  TB_REQUIRE(workspace && workspace_bytes >= 256 && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0,
+             "tb_build_hamiltonian_teacher: need a 256-byte aligned workspace of at least 256 bytes");
   Box B;
   tb_status s = make_box(box, pbc, rcut, &B);
   if (s != TB_OK) return s;
@@ -103,8 +106,7 @@ extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const
   T.rcut = rcut;
   T.n_species = 3;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int *flags = nullptr;
-  TB_CUDA(cudaMallocAsync(&flags, sizeof(int), st));
+  int *flags = static_cast<int *>(workspace);
   TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
   const unsigned nb = (unsigned)((((n + 31) / 32) * 32 + 255) / 256);
   if (precision == TB_F32)
@@ -116,7 +118,6 @@ extern "C" tb_status tb_build_hamiltonian_teacher(const double *positions, const
   TB_CHECK_LAUNCH();
   int h = 0;
   TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TB_CUDA(cudaFreeAsync(flags, st));
   TB_CUDA(cudaStreamSynchronize(st));
   if (h & 1) return fail(TB_ERR_INVALID_ARG, "tb_build_hamiltonian_teacher: species outside [0, 3)");
   return TB_OK;

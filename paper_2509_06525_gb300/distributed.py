@@ -41,16 +41,36 @@ def vector_shard(r_total: int, rank: int, world: int) -> Tuple[int, int]:
     return block_shard(r_total, rank, world)
 
 
+def _staged(t: torch.Tensor, group) -> bool:
+    """Device tensors go through host memory on the gloo backend (which does
+    not gather device tensors); NCCL takes them as they are."""
+    return t.is_cuda and dist.get_backend(group) == "gloo"
+
+
 def gather_blocks(local: torch.Tensor, total: int, group: Optional[dist.ProcessGroup] = None) -> torch.Tensor:
     """All ranks' blocks [count_k, ...] (block_shard order) -> [total, ...]
     on every rank."""
     world = dist.get_world_size(group)
     width = -(-total // world)
-    padded = torch.zeros((width,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
-    padded[:local.shape[0]] = local
+    dev = local.device
+    src = local.cpu() if _staged(local, group) else local
+    padded = torch.zeros((width,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    padded[:src.shape[0]] = src
     parts = [torch.empty_like(padded) for _ in range(world)]
     dist.all_gather(parts, padded, group=group)
-    return torch.cat([parts[k][:block_shard(total, k, world)[1]] for k in range(world)], 0)
+    out = torch.cat([parts[k][:block_shard(total, k, world)[1]] for k in range(world)], 0)
+    return out.to(dev)
+
+
+def all_reduce_sum(t: torch.Tensor, group: Optional[dist.ProcessGroup] = None) -> torch.Tensor:
+    """In-place sum over ranks (through host memory on gloo)."""
+    if _staged(t, group):
+        h = t.cpu()
+        dist.all_reduce(h, op=dist.ReduceOp.SUM, group=group)
+        t.copy_(h)
+    else:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t
 
 
 def gather_moments(mu_local: torch.Tensor, r_total: int, group: Optional[dist.ProcessGroup] = None) -> torch.Tensor:
@@ -79,7 +99,7 @@ def band_step(forward_local: Callable, loss_all: Callable, backward_local: Calla
     e_all = gather_blocks(e_local, n_cells, group)
     dLdE_all, stats = loss_all(e_all, e_ref_all)
     grad = backward_local(ctx, dLdE_all[first:first + count].contiguous())
-    dist.all_reduce(grad, op=dist.ReduceOp.SUM, group=group)
+    all_reduce_sum(grad, group)
     return stats, grad
 
 

@@ -76,12 +76,15 @@ SIGNATURES = {
                                     _c_vp, _c_vp, ctypes.POINTER(_c_i64), _c_vp, _c_sz, _c_vp]),
     "tb_build_hamiltonian_teacher": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
                                               _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i32, _c_vp,
-                                              _c_vp, _c_vp]),
+                                              _c_vp, _c_vp, _c_sz, _c_vp]),
     "tb_compute_descriptors": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp,
                                         _c_vp, _c_vp]),
     "tb_edge_features": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
                                   _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]),
-    "tb_feature_stats": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_feature_stats": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_inverse_std": (_c_i32, [_c_vp, _c_vp, _c_vp, _c_i32, _c_vp]),
+    "tb_copy_to_device": (_c_i32, [_c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_copy_to_host": (_c_i32, [_c_vp, _c_vp, _c_sz, _c_vp]),
     "tb_mlp_workspace_size": (_c_sz, [_c_i64]),
     "tb_mlp_forward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]),
     "tb_mlp_backward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
@@ -576,11 +579,12 @@ def build_hamiltonian_teacher(positions: torch.Tensor, species: torch.Tensor, bo
     onsite = np.ascontiguousarray(np.asarray(teacher.onsite, np.float64).reshape(3))
     val = torch.empty(max(nb.total, 1), dtype=dtype, device=dev)
     diag = torch.empty(nb.n, dtype=dtype, device=dev) if with_diag else None
+    ws = _workspace(256, dev)
     st = L.tb_build_hamiltonian_teacher(
         _ptr(positions), _ptr(species), nb.n, bptr, pptr, _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(nb.cnt),
         _ptr(nb.ncount), pref.ctypes.data_as(ctypes.c_void_p), onsite.ctypes.data_as(ctypes.c_void_p),
         float(teacher.a_cc), float(teacher.beta), float(teacher.gamma), float(teacher.rcut), precision_of(dtype),
-        _ptr(val), _ptr(diag), _stream(stream))
+        _ptr(val), _ptr(diag), _ptr(ws), ws.numel(), _stream(stream))
     _check("tb_build_hamiltonian_teacher", st)
     return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
 
@@ -649,14 +653,13 @@ class MLPModel:
         self.mean = None if mean is None else torch.as_tensor(mean, dtype=torch.float32, device=device)
         self.inv_std = None
         if std is not None:
-            s = torch.as_tensor(std, dtype=torch.float32, device=device)
-            self.inv_std = 1.0 / torch.clamp(s, min=1e-6)
+            self.inv_std = inverse_std(torch.as_tensor(std, dtype=torch.float32, device=device), stream=stream)
         self.step = 0
         _check("tb_mlp_pack_weights", lib().tb_mlp_pack_weights(_ptr(self.p), _ptr(self.wb), _stream(stream)))
 
-    def set_normalisation(self, mean: torch.Tensor, std: torch.Tensor):
+    def set_normalisation(self, mean: torch.Tensor, std: torch.Tensor, mask: Optional[torch.Tensor] = None):
         self.mean = mean.to(torch.float32).contiguous()
-        self.inv_std = (1.0 / torch.clamp(std.to(torch.float32), min=1e-6)).contiguous()
+        self.inv_std = inverse_std(std.to(torch.float32).contiguous(), mask)
 
     def params_numpy(self) -> dict:
         return unpack_params(self.p.cpu().numpy())
@@ -686,15 +689,48 @@ def edge_features(positions, species, box, pbc, rcut, nb: Neighbors, cmix, v, me
     return (xr[:nb.total] if raw else None), (xb[:nb.total] if bf16 else None)
 
 
-def feature_stats(x_raw, n, slice_ptr, cnt, stream=None):
+def feature_stats(x_raw, n, slice_ptr, cnt, mask: Optional[torch.Tensor] = None, stream=None):
+    """(mean, std, inv_std) of the edge inputs (tb_feature_stats); mask
+    (float [32]) switches features off in inv_std."""
     dev = x_raw.device
     mean = torch.empty(32, dtype=torch.float32, device=dev)
     std = torch.empty(32, dtype=torch.float32, device=dev)
+    inv = torch.empty(32, dtype=torch.float32, device=dev)
+    m = None if mask is None else torch.as_tensor(mask, dtype=torch.float32, device=dev).contiguous()
     ws = _workspace(96 * 8 * 8 * 1024, dev)
-    st = lib().tb_feature_stats(_ptr(x_raw), n, _ptr(slice_ptr), _ptr(cnt), _ptr(mean), _ptr(std), _ptr(ws),
-                                ws.numel(), _stream(stream))
+    st = lib().tb_feature_stats(_ptr(x_raw), n, _ptr(slice_ptr), _ptr(cnt), _ptr(mean), _ptr(std), _ptr(inv),
+                                _ptr(m), _ptr(ws), ws.numel(), _stream(stream))
     _check("tb_feature_stats", st)
-    return mean, std
+    return mean, std, inv
+
+
+def inverse_std(std: torch.Tensor, mask: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """tb_inverse_std: mask / max(std, 1e-6) on the device."""
+    out = torch.empty_like(std)
+    m = None if mask is None else torch.as_tensor(mask, dtype=torch.float32, device=std.device).contiguous()
+    _check("tb_inverse_std", lib().tb_inverse_std(_ptr(std), _ptr(m), _ptr(out), std.numel(), _stream(stream)))
+    return out
+
+
+def copy_to_device(dst: torch.Tensor, src_host: torch.Tensor, stream=None):
+    """tb_copy_to_device: a host tensor (page-locked for an asynchronous
+    transfer) into a device tensor of the same size."""
+    if src_host.is_cuda or not dst.is_cuda or dst.numel() * dst.element_size() != src_host.numel() * src_host.element_size():
+        raise ValueError("copy_to_device: host source and device destination of equal size")
+    _check("tb_copy_to_device", lib().tb_copy_to_device(_ptr(dst), ctypes.c_void_p(src_host.data_ptr()),
+                                                        dst.numel() * dst.element_size(), _stream(stream)))
+    return dst
+
+
+def copy_to_host(dst_host: torch.Tensor, src: torch.Tensor, stream=None):
+    """tb_copy_to_host: a device tensor into a host tensor (synchronises)."""
+    if dst_host.is_cuda or not src.is_cuda or dst_host.numel() * dst_host.element_size() != src.numel() * src.element_size():
+        raise ValueError("copy_to_host: device source and host destination of equal size")
+    if not src.is_contiguous() or not dst_host.is_contiguous():
+        raise ValueError("copy_to_host: contiguous tensors only")
+    _check("tb_copy_to_host", lib().tb_copy_to_host(ctypes.c_void_p(dst_host.data_ptr()), _ptr(src),
+                                                    src.numel() * src.element_size(), _stream(stream)))
+    return dst_host
 
 
 def mlp_forward(x_bf16, model: MLPModel, stream=None):

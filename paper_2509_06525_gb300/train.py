@@ -81,13 +81,10 @@ def fit_normalisation(model: g.MLPModel, ds: SnapshotSet, feature_mask: Optional
     snapshot with tb_edge_features.  Features where feature_mask is 0 are
     switched off (inv_std = 0), e.g. the environment blocks for a
     radial-only model."""
-    mean, std = g.feature_stats(ds.x_raw, ds.n_rows, ds.slice_ptr, ds.cnt)
-    mean_h = mean.cpu().numpy()
-    inv_h = 1.0 / np.maximum(std.cpu().numpy(), 1e-6)
-    if feature_mask is not None:
-        inv_h = inv_h * np.asarray(feature_mask, np.float32)
-    model.mean = torch.tensor(mean_h, dtype=torch.float32, device="cuda")
-    model.inv_std = torch.tensor(inv_h.astype(np.float32), device="cuda")
+    mask = None if feature_mask is None else np.asarray(feature_mask, np.float32)
+    mean, _, inv_std = g.feature_stats(ds.x_raw, ds.n_rows, ds.slice_ptr, ds.cnt, mask=mask)
+    model.mean = mean
+    model.inv_std = inv_std
     xs = []
     for (s, pos, spc, nb, v) in ds.parts:
         _, xb = g.edge_features(pos, spc, s.box, s.pbc, ds.rcut, nb, model.cmix, v, model.mean,

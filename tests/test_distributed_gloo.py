@@ -176,3 +176,29 @@ def test_gloo_ranks_reproduce_the_single_process_band_step(tmp_path, n_cells, wo
     L, grad, _ = oe.cell_loss_and_grad(flat, cells, kpts, e_ref, w, np.zeros(3))
     assert got[0] == pytest.approx(L, rel=1e-12)
     np.testing.assert_allclose(got[1:], grad, rtol=1e-10, atol=1e-12 * np.max(np.abs(grad)))
+
+
+def _unsharded_worker(rank, world, port, out_path):
+    from paper_2509_06525_gb300.bands import BandTrainer
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        try:
+            BandTrainer(None, None)
+            result = "accepted"
+        except ValueError:
+            result = "rejected"
+        if rank == 0:
+            with open(out_path, "w") as fh:
+                fh.write(result)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_band_trainer_refuses_a_group_without_the_total_cell_count(tmp_path):
+    """With several ranks and no n_cells_total, each rank would silently
+    train on its own cells; the trainer must refuse."""
+    out = str(tmp_path / "r.txt")
+    mp.start_processes(_unsharded_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    assert open(out).read() == "rejected"

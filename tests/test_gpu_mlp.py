@@ -66,9 +66,15 @@ def test_descriptors_and_edge_features(g, kind):
     assert np.all(xr[mask] == 0.0)
     np.testing.assert_array_equal(xb.to(torch.float32).cpu().numpy(),
                                   torch.tensor(xr).to(torch.bfloat16).to(torch.float32).numpy())
-    mean, std = g.feature_stats(torch.tensor(xr, device="cuda"), s.n, nb.slice_ptr, nb.cnt)
+    fmask = np.ones(32, np.float32)
+    fmask[8:16] = 0.0
+    mean, std, inv = g.feature_stats(torch.tensor(xr, device="cuda"), s.n, nb.slice_ptr, nb.cnt, mask=fmask)
     np.testing.assert_allclose(mean.cpu().numpy(), x_ref.mean(0), rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(std.cpu().numpy(), x_ref.std(0), rtol=1e-4, atol=1e-5)
+    # the normalisation: mask / max(std, 1e-6), from the library
+    sd = std.cpu().numpy()
+    np.testing.assert_allclose(inv.cpu().numpy(), fmask / np.maximum(sd, np.float32(1e-6)), rtol=1e-6)
+    np.testing.assert_array_equal(g.inverse_std(std).cpu().numpy(), np.float32(1.0) / np.maximum(sd, np.float32(1e-6)))
 
 
 def _model(g, seed, bias=True):
