@@ -258,8 +258,17 @@ TB_API tb_status kpm_moments_noalloc(int64_t n, const int64_t *slice_ptr, const 
  * whole recursion as a CUDA graph launched on `stream`.  The workspace-size
  * query reads each snapshot's element count from its slice_ptr and
  * synchronises `stream`.
+ *
+ * The graph holds the fold of every snapshot, the band plan (banded step
+ * shapes), the random phases, every Chebyshev step and the reduction.  The
+ * library keeps the instantiated graph of the last call and launches it
+ * again while the next call has the same device, pointers, sizes, element
+ * counts, (a, b), M, R, seed, mode, step shape and workspace; any
+ * difference captures a new one (the first call of a layout pays the
+ * capture and instantiation).  Calls are serialised by a mutex.
  *   mu         device double [n_snap][R][M] output
  *   graph_ms   host double or NULL: CUDA-event time of the graph launch
+ *              (fold and recursion; not the capture)
  * Synchronises `stream`; TB_ERR_BOUNDS / TB_ERR_NOT_FINITE as kpm_moments.
  * ------------------------------------------------------------------- */
 TB_API size_t kpm_moments_batched_workspace_size(int32_t n_snap, const int64_t *const *slice_ptr,
@@ -273,6 +282,21 @@ TB_API tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows,
                                      int32_t M, int32_t R, uint64_t seed, int32_t mode, double *mu,
                                      void *workspace, size_t workspace_bytes, void *stream,
                                      double *graph_ms);
+
+/* Autotuner of the batched path (no counterpart in the paper): folds the
+ * batch as kpm_moments_batched does (same arguments and workspace), then
+ * times every step shape on the folded block-diagonal matrix as
+ * tb_kpm_autotune does and stores the fastest as the table entry of the
+ * batch's padded row count.  Synchronises `stream`. */
+TB_API tb_status kpm_moments_batched_autotune(int32_t n_snap, const int64_t *n_rows,
+                                              const int64_t *const *slice_ptr,
+                                              const int32_t *const *col, const void *const *val,
+                                              const void *const *diag, int32_t precision,
+                                              const double *a, const double *b, int32_t R,
+                                              int32_t mode, int32_t reps, void *workspace,
+                                              size_t workspace_bytes, void *stream,
+                                              int32_t *best_shape, float *ms_per_step,
+                                              int32_t ms_capacity);
 
 /* ---------------------------------------------------------------------
  * KPM density of states, Eq. 4, per orbital per eV (integrates to 1):

@@ -32,6 +32,7 @@ tb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
 int sm_count() {
   int dev = 0, n = 0;

@@ -14,8 +14,10 @@ void set_error(const char *fmt, ...);
 tb_status fail(tb_status code, const char *fmt, ...);
 tb_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 int sm_count();
-// process-wide count of kernel launches issued by the library
+// process-wide count of kernel launches issued by the library (a graph
+// launch adds the kernels it holds)
 void note_launch();
+void note_launches(long long count);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -353,41 +353,66 @@ extern "C" size_t kpm_moments_batched_workspace_size(int32_t n_snap, const int64
   return batch_prefix_bytes(L, n_snap, precision == TB_F32 ? 4 : 8) + run + 256;
 }
 
-extern "C" tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows, const int64_t *const *slice_ptr,
-                                         const int32_t *const *col, const void *const *val, const void *const *diag,
-                                         int32_t precision, const double *a, const double *b, int32_t M, int32_t R,
-                                         uint64_t seed, int32_t mode, double *mu, void *workspace,
-                                         size_t workspace_bytes, void *stream, double *graph_ms) {
-  TB_REQUIRE(n_snap >= 1 && n_rows && slice_ptr && col && val && a && b && mu && workspace,
-             "kpm_moments_batched: bad argument");
-  TB_REQUIRE(M >= 2, "kpm_moments_batched: M must be >= 2");
-  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "kpm_moments_batched: bad precision");
-  TB_REQUIRE(mode == TB_KPM_DIRECT || mode == TB_KPM_DOUBLING, "kpm_moments_batched: bad mode");
-  TB_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "kpm_moments_batched: workspace alignment");
-  TB_REQUIRE(tb_kpm_shape_count(R, precision) > 0, "kpm_moments_batched: unsupported R=%d", R);
+namespace gputb {
+namespace {
+
+// Checks shared by the batched entry points.
+tb_status check_batch_args(const char *who, int32_t n_snap, const int64_t *n_rows, const int64_t *const *slice_ptr,
+                           const int32_t *const *col, const void *const *val, int32_t precision, const double *a,
+                           const double *b, int32_t R, int32_t mode, void *workspace) {
+  TB_REQUIRE(n_snap >= 1 && n_rows && slice_ptr && col && val && a && b && workspace, "%s: bad argument", who);
+  TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "%s: bad precision", who);
+  TB_REQUIRE(mode == TB_KPM_DIRECT || mode == TB_KPM_DOUBLING, "%s: bad mode", who);
+  TB_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "%s: workspace alignment", who);
+  TB_REQUIRE(tb_kpm_shape_count(R, precision) > 0, "%s: unsupported R=%d", who, R);
   for (int s = 0; s < n_snap; ++s)
-    TB_REQUIRE(a[s] > 0.0 && std::isfinite(a[s]) && std::isfinite(b[s]), "kpm_moments_batched: bad a/b of %d", s);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  BatchLayout L;
-  tb_status status = batch_layout(n_snap, n_rows, slice_ptr, true, st, &L);
-  if (status != TB_OK) return status;
-  const size_t vs = precision == TB_F32 ? 4 : 8;
+    TB_REQUIRE(a[s] > 0.0 && std::isfinite(a[s]) && std::isfinite(b[s]), "%s: bad a/b of snapshot %d", who, s);
+  return TB_OK;
+}
+
+// The batch matrix in the workspace: pointers carved in a fixed order.
+struct FoldedBatch {
+  int64_t *sp = nullptr;
+  int32_t *col = nullptr;
+  char *val = nullptr;
+  char *diag = nullptr;
+  int32_t *tile = nullptr;
+  int64_t *row0 = nullptr;
+  int64_t *rows = nullptr;
+  void *run_ws = nullptr;
+  size_t run_bytes = 0;
+};
+
+tb_status carve_folded(const BatchLayout &L, int n_snap, size_t vs, void *workspace, size_t workspace_bytes,
+                       FoldedBatch *F) {
   Carver cv(workspace, workspace_bytes);
-  int64_t *dsp = cv.take<int64_t>(L.n_pad / 32 + 1);
-  int32_t *dcol = cv.take<int32_t>(L.elements > 0 ? L.elements : 1);
-  char *dval = cv.take<char>((L.elements > 0 ? L.elements : 1) * vs);
-  char *ddiag = cv.take<char>(L.n_pad * vs);
-  int32_t *dtile = cv.take<int32_t>(L.tile_snap.size());
-  int64_t *drow0 = cv.take<int64_t>(n_snap);
-  int64_t *drows = cv.take<int64_t>(n_snap);
+  F->sp = cv.take<int64_t>(L.n_pad / 32 + 1);
+  F->col = cv.take<int32_t>(L.elements > 0 ? L.elements : 1);
+  F->val = cv.take<char>((L.elements > 0 ? L.elements : 1) * vs);
+  F->diag = cv.take<char>(L.n_pad * vs);
+  F->tile = cv.take<int32_t>(L.tile_snap.size());
+  F->row0 = cv.take<int64_t>(n_snap);
+  F->rows = cv.take<int64_t>(n_snap);
   cv.used = align_up(cv.used, 256);
   if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments_batched: workspace too small");
-  void *run_ws = static_cast<char *>(workspace) + cv.used;
-  const size_t run_bytes = workspace_bytes - cv.used;
-  TB_CUDA(cudaMemcpyAsync(dtile, L.tile_snap.data(), L.tile_snap.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+  F->run_ws = static_cast<char *>(workspace) + cv.used;
+  F->run_bytes = workspace_bytes - cv.used;
+  return TB_OK;
+}
+
+// the layout tables to the device (on `st`)
+tb_status upload_tables(const BatchLayout &L, int n_snap, const FoldedBatch &F, cudaStream_t st) {
+  TB_CUDA(cudaMemcpyAsync(F.tile, L.tile_snap.data(), L.tile_snap.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                           st));
-  TB_CUDA(cudaMemcpyAsync(drow0, L.row0.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  TB_CUDA(cudaMemcpyAsync(drows, L.rows.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  TB_CUDA(cudaMemcpyAsync(F.row0, L.row0.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  TB_CUDA(cudaMemcpyAsync(F.rows, L.rows.data(), n_snap * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  return TB_OK;
+}
+
+// every snapshot into the block-diagonal matrix with its rescaling folded in
+tb_status enqueue_fold(const BatchLayout &L, int n_snap, const int64_t *const *slice_ptr, const int32_t *const *col,
+                       const void *const *val, const void *const *diag, int32_t precision, const double *a,
+                       const double *b, const FoldedBatch &F, cudaStream_t st) {
   for (int s = 0; s < n_snap; ++s) {
     const int64_t work = std::max(L.total[s], L.pad_slices[s] * 32 + 1);
     const unsigned nb = (unsigned)((work + 255) / 256);
@@ -395,27 +420,192 @@ extern "C" tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows, 
       batch_fold_kernel<float><<<nb, 256, 0, st>>>(slice_ptr[s], col[s], static_cast<const float *>(val[s]),
                                                    diag ? static_cast<const float *>(diag[s]) : nullptr, L.rows[s],
                                                    L.slices[s], L.pad_slices[s], L.total[s], L.row0[s], L.e0[s],
-                                                   1.0 / a[s], b[s], dsp, dcol, reinterpret_cast<float *>(dval),
-                                                   reinterpret_cast<float *>(ddiag));
+                                                   1.0 / a[s], b[s], F.sp, F.col, reinterpret_cast<float *>(F.val),
+                                                   reinterpret_cast<float *>(F.diag));
     else
       batch_fold_kernel<double><<<nb, 256, 0, st>>>(slice_ptr[s], col[s], static_cast<const double *>(val[s]),
                                                     diag ? static_cast<const double *>(diag[s]) : nullptr,
                                                     L.rows[s], L.slices[s], L.pad_slices[s], L.total[s], L.row0[s],
-                                                    L.e0[s], 1.0 / a[s], b[s], dsp, dcol,
-                                                    reinterpret_cast<double *>(dval),
-                                                    reinterpret_cast<double *>(ddiag));
+                                                    L.e0[s], 1.0 / a[s], b[s], F.sp, F.col,
+                                                    reinterpret_cast<double *>(F.val),
+                                                    reinterpret_cast<double *>(F.diag));
     TB_CHECK_LAUNCH();
   }
-  TB_CUDA(cudaStreamSynchronize(st));  // the host tables above may go out of scope
-  BatchDesc bd{dtile, drow0, drows, n_snap};
+  return TB_OK;
+}
+
+// One instantiated graph (fold + recursion + reduction) of the last batched
+// call, reused while every argument that its kernels see is the same.
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int *flags = nullptr;
+  int launches = 0;
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch_graph;
+
+void batch_key(std::vector<uint64_t> &k, int device, int32_t n_snap, const BatchLayout &L,
+               const int64_t *const *slice_ptr, const int32_t *const *col, const void *const *val,
+               const void *const *diag, int32_t precision, const double *a, const double *b, int32_t M, int32_t R,
+               uint64_t seed, int32_t mode, int shape, const double *mu, const void *ws, size_t wsb) {
+  auto put = [&](uint64_t v) { k.push_back(v); };
+  auto ptr = [&](const void *p) { put(reinterpret_cast<uintptr_t>(p)); };
+  auto dbl = [&](double d) {
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    put(u);
+  };
+  put(device), put(n_snap), put(precision), put(M), put(R), put(seed), put(mode), put(shape);
+  ptr(mu), ptr(ws), put(wsb);
+  for (int s = 0; s < n_snap; ++s) {
+    ptr(slice_ptr[s]), ptr(col[s]), ptr(val[s]), ptr(diag ? diag[s] : nullptr);
+    put(L.rows[s]), put(L.total[s]);
+    dbl(a[s]), dbl(b[s]);
+  }
+}
+
+tb_status batch_flags_check(const int *flags, cudaStream_t st) {
+  int h[4] = {0, 0, 0, 0};
+  TB_CUDA(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  if (h[0] & 4) return fail(TB_ERR_TIMEOUT, "kpm_moments_batched: a pipeline wait timed out");
+  if (h[0] & 2) return fail(TB_ERR_NOT_FINITE, "kpm_moments_batched: non-finite moment");
+  if (h[0] & 1)
+    return fail(TB_ERR_BOUNDS, "kpm_moments_batched: |mu_n| > 1 + 1e-6; a spectrum is not inside [b - a, b + a]");
+  return TB_OK;
+}
+
+}  // namespace
+}  // namespace gputb
+
+extern "C" tb_status kpm_moments_batched(int32_t n_snap, const int64_t *n_rows, const int64_t *const *slice_ptr,
+                                         const int32_t *const *col, const void *const *val, const void *const *diag,
+                                         int32_t precision, const double *a, const double *b, int32_t M, int32_t R,
+                                         uint64_t seed, int32_t mode, double *mu, void *workspace,
+                                         size_t workspace_bytes, void *stream, double *graph_ms) {
+  tb_status status =
+      check_batch_args("kpm_moments_batched", n_snap, n_rows, slice_ptr, col, val, precision, a, b, R, mode, workspace);
+  if (status != TB_OK) return status;
+  TB_REQUIRE(mu && M >= 2, "kpm_moments_batched: need mu and M >= 2");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchLayout L;
+  status = batch_layout(n_snap, n_rows, slice_ptr, true, st, &L);
+  if (status != TB_OK) return status;
+  const size_t vs = precision == TB_F32 ? 4 : 8;
+  FoldedBatch F;
+  status = carve_folded(L, n_snap, vs, workspace, workspace_bytes, &F);
+  if (status != TB_OK) return status;
   const int shape = chosen_shape(precision, R, mode, L.n_pad);
-  const bool ok = precision == TB_F32
-                      ? KpmEntry<float>::run_batched(R, &status, shape, L.n_pad, dsp, dcol, dval, ddiag, (int)M, seed,
-                                                     (int)mode, bd, mu, run_ws, run_bytes, st, graph_ms)
-                      : KpmEntry<double>::run_batched(R, &status, shape, L.n_pad, dsp, dcol, dval, ddiag, (int)M,
-                                                      seed, (int)mode, bd, mu, run_ws, run_bytes, st, graph_ms);
-  if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: unsupported R=%d", R);
+  const bool prep = precision == TB_F32 ? KpmEntry<float>::prepare(R, shape) : KpmEntry<double>::prepare(R, shape);
+  if (!prep) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: bad shape %d for R=%d", shape, R);
+  int device = 0;
+  TB_CUDA(cudaGetDevice(&device));
+  std::vector<uint64_t> key;
+  batch_key(key, device, n_snap, L, slice_ptr, col, val, diag, precision, a, b, M, R, seed, mode, shape, mu,
+            workspace, workspace_bytes);
+
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchGraph &G = g_batch_graph;
+  if (G.exec == nullptr || G.key != key) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = BatchGraph();
+    // capture on a private stream: the fold of every snapshot, the band plan
+    // (banded shapes), the random phases, the recursion and the reduction
+    cudaStream_t cs = nullptr;
+    TB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int64_t l0 = tb_launch_count();
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int *flags = nullptr;
+    if (e == cudaSuccess) {
+      status = enqueue_fold(L, n_snap, slice_ptr, col, val, diag, precision, a, b, F, cs);
+      BatchDesc bd{F.tile, F.row0, F.rows, n_snap};
+      bool ok = true;
+      if (status == TB_OK)
+        ok = precision == TB_F32
+                 ? KpmEntry<float>::enqueue_batched(R, &status, shape, L.n_pad, F.sp, F.col, F.val, F.diag, (int)M,
+                                                    seed, (int)mode, bd, mu, F.run_ws, F.run_bytes, cs, &flags)
+                 : KpmEntry<double>::enqueue_batched(R, &status, shape, L.n_pad, F.sp, F.col, F.val, F.diag,
+                                                     (int)M, seed, (int)mode, bd, mu, F.run_ws, F.run_bytes, cs,
+                                                     &flags);
+      if (!ok && status == TB_OK) status = fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: unsupported R=%d", R);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      G.graph = graph;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "kpm_moments_batched capture", __FILE__, __LINE__);
+    if (status != TB_OK) return status;
+    e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+    if (e != cudaSuccess) {
+      G.exec = nullptr;
+      return cuda_fail(e, "kpm_moments_batched graph", __FILE__, __LINE__);
+    }
+    G.key = key;
+    G.flags = flags;
+    G.launches = static_cast<int>(tb_launch_count() - l0);
+    note_launches(-G.launches);   // captured, not yet run: counted at each graph launch below
+  }
+  // the tables the graph's kernels read, then the graph itself
+  status = upload_tables(L, n_snap, F, st);
+  if (status != TB_OK) return status;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (graph_ms) {
+    TB_CUDA(cudaEventCreate(&ev[0]));
+    TB_CUDA(cudaEventCreate(&ev[1]));
+    TB_CUDA(cudaEventRecord(ev[0], st));
+  }
+  cudaError_t e = cudaGraphLaunch(G.exec, st);
+  if (e == cudaSuccess) note_launches(G.launches);
+  if (e == cudaSuccess && graph_ms) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) status = batch_flags_check(G.flags, st);
+  if (graph_ms) {
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    *graph_ms = ms;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kpm_moments_batched launch", __FILE__, __LINE__);
   return status;
+}
+
+extern "C" tb_status kpm_moments_batched_autotune(int32_t n_snap, const int64_t *n_rows,
+                                                  const int64_t *const *slice_ptr, const int32_t *const *col,
+                                                  const void *const *val, const void *const *diag,
+                                                  int32_t precision, const double *a, const double *b, int32_t R,
+                                                  int32_t mode, int32_t reps, void *workspace,
+                                                  size_t workspace_bytes, void *stream, int32_t *best_shape,
+                                                  float *ms_per_step, int32_t ms_capacity) {
+  tb_status status = check_batch_args("kpm_moments_batched_autotune", n_snap, n_rows, slice_ptr, col, val, precision,
+                                      a, b, R, mode, workspace);
+  if (status != TB_OK) return status;
+  TB_REQUIRE(best_shape && reps >= 1 && reps <= 10000, "kpm_moments_batched_autotune: bad argument");
+  TB_REQUIRE(ms_capacity >= 0 && (ms_capacity == 0 || ms_per_step), "kpm_moments_batched_autotune: bad ms buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchLayout L;
+  status = batch_layout(n_snap, n_rows, slice_ptr, true, st, &L);
+  if (status != TB_OK) return status;
+  FoldedBatch F;
+  status = carve_folded(L, n_snap, precision == TB_F32 ? 4 : 8, workspace, workspace_bytes, &F);
+  if (status != TB_OK) return status;
+  status = upload_tables(L, n_snap, F, st);
+  if (status == TB_OK) status = enqueue_fold(L, n_snap, slice_ptr, col, val, diag, precision, a, b, F, st);
+  if (status != TB_OK) return status;
+  int best = 0;
+  const bool ok = precision == TB_F32
+                      ? KpmEntry<float>::autotune(R, &status, L.n_pad, F.sp, F.col, F.val, F.diag, 1.0, 0.0, (int)mode,
+                                                  (int)reps, F.run_ws, F.run_bytes, st, &best, ms_per_step,
+                                                  ms_capacity)
+                      : KpmEntry<double>::autotune(R, &status, L.n_pad, F.sp, F.col, F.val, F.diag, 1.0, 0.0,
+                                                   (int)mode, (int)reps, F.run_ws, F.run_bytes, st, &best,
+                                                   ms_per_step, ms_capacity);
+  if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched_autotune: unsupported R=%d", R);
+  if (status != TB_OK) return status;
+  *best_shape = best;
+  return tb_kpm_set_shape(L.n_pad, R, precision, mode, best);
 }
 
 // ---------------------------------------------------------------------------

@@ -34,10 +34,14 @@ struct KpmEntry {
   static bool run(int R, tb_status *status, int shape, int64_t n, const int64_t *slice_ptr, const int32_t *col,
                   const void *val, const void *diag, double a, double b, int M, uint64_t seed, int64_t r0,
                   int mode, double *mu_r, void *ws, size_t ws_bytes, cudaStream_t st, double *step_ms);
-  static bool run_batched(int R, tb_status *status, int shape, int64_t n_pad, const int64_t *slice_ptr,
-                          const int32_t *col, const void *val, const void *diag, int M, uint64_t seed, int mode,
-                          const BatchDesc &bt, double *mu, void *ws, size_t ws_bytes, cudaStream_t st,
-                          double *graph_ms);
+  // opt the shape's kernels into their shared memory (before any capture)
+  static bool prepare(int R, int shape);
+  // enqueue the batched recursion on `st` (capturable); *flags receives the
+  // device status flags to check after it ran
+  static bool enqueue_batched(int R, tb_status *status, int shape, int64_t n_pad, const int64_t *slice_ptr,
+                              const int32_t *col, const void *val, const void *diag, int M, uint64_t seed, int mode,
+                              const BatchDesc &bt, double *mu, void *ws, size_t ws_bytes, cudaStream_t st,
+                              int **flags);
   // time `reps` Chebyshev steps of every candidate shape on this matrix;
   // ms[shape] receives the mean time per step, *best the fastest shape
   static bool autotune(int R, tb_status *status, int64_t n, const int64_t *slice_ptr, const int32_t *col,

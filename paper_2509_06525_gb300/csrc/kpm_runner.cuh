@@ -273,16 +273,17 @@ struct KpmRunner {
     return s;
   }
 
-  // Batched: the caller's block-diagonal, already rescaled matrix of
-  // n_pad rows (see kpm_moments_batched); the recursion is captured once as
-  // a CUDA graph and launched on `st`.
-  static tb_status run_batched(int shape, int64_t n_pad, const int64_t *slice_ptr, const int32_t *col,
-                               const valT *val, const valT *diag, int M, uint64_t seed, int mode,
-                               const BatchTables &bt, double *mu, void *ws, size_t ws_bytes, cudaStream_t st,
-                               double *graph_ms) {
+  // Batched: the caller's block-diagonal, already rescaled matrix of n_pad
+  // rows (see kpm_moments_batched).  Enqueues the band plan (banded shapes),
+  // the random phases, the recursion and the segmented reduction on `st`
+  // (which kpm_moments_batched captures into a CUDA graph); *flags_out
+  // receives the status flags to check after the launch.
+  static tb_status enqueue_batched(int shape, int64_t n_pad, const int64_t *slice_ptr, const int32_t *col,
+                                   const valT *val, const valT *diag, int M, uint64_t seed, int mode,
+                                   const BatchTables &bt, double *mu, void *ws, size_t ws_bytes, cudaStream_t st,
+                                   int **flags_out) {
     const bool dbl = mode == TB_KPM_DOUBLING;
     const int grid = Kit::grid(shape, n_pad, dbl);
-    const int rpb = Kit::rows_per_block(shape);
     Carver cv(ws, ws_bytes);
     real *v0 = cv.take<real>((size_t)n_pad * R * 2);
     real *A = cv.take<real>((size_t)n_pad * R * 2);
@@ -293,44 +294,12 @@ struct KpmRunner {
     PlanWs pw;
     carve_plan(cv, n_pad, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "kpm_moments_batched: workspace too small");
-    (void)rpb;
-    Kit::prepare(shape);
+    *flags_out = flags;
     BandPlan bp;
-    tb_status sp = make_plan(shape, n_pad, slice_ptr, col, pw, st, &bp);
-    if (sp != TB_OK) return sp;
-    cudaStream_t cs = nullptr;
-    TB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    tb_status s = TB_OK;
-    if (e == cudaSuccess) {
-      s = enqueue<true>(shape, grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, 0, dbl, mu, v0, A, B,
-                        partial, flags, bt, cs, nullptr, nullptr, bp);
-      e = cudaStreamEndCapture(cs, &graph);
-    }
-    if (e == cudaSuccess && s == TB_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (e == cudaSuccess && s == TB_OK && graph_ms) {
-      cudaEventCreate(&ev[0]);
-      cudaEventCreate(&ev[1]);
-      cudaEventRecord(ev[0], st);
-    }
-    if (e == cudaSuccess && s == TB_OK) e = cudaGraphLaunch(exec, st);
-    if (ev[1]) cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess && s == TB_OK) s = check_flags(flags, st, "kpm_moments_batched");
-    if (graph_ms && ev[1]) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      *graph_ms = ms;
-    }
-    if (ev[0]) cudaEventDestroy(ev[0]);
-    if (ev[1]) cudaEventDestroy(ev[1]);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return cuda_fail(e, "kpm_moments_batched graph", __FILE__, __LINE__);
-    return s;
+    tb_status s = make_plan(shape, n_pad, slice_ptr, col, pw, st, &bp);
+    if (s != TB_OK) return s;
+    return enqueue<true>(shape, grid, n_pad, slice_ptr, col, val, diag, 1.0, 0.0, M, seed, 0, dbl, mu, v0, A, B,
+                         partial, flags, bt, st, nullptr, nullptr, bp);
   }
 
   // Autotuner: v0 from the random phases, v1 = H~ v0 with the default shape,
@@ -482,10 +451,18 @@ struct RunOp {
   }
 };
 template <typename real, typename valT, int R>
-struct BatchRunOp {
+struct PrepOp {
+  static void apply(int shape, bool *ok) {
+    using Kit = StepKit<real, valT, R>;
+    *ok = shape >= 0 && shape < Kit::kShapes;
+    if (*ok) Kit::prepare(shape);
+  }
+};
+template <typename real, typename valT, int R>
+struct BatchEnqueueOp {
   static void apply(tb_status *status, int shape, int64_t n_pad, const int64_t *sp, const int32_t *col,
                     const void *val, const void *diag, int M, uint64_t seed, int mode, const BatchDesc &bd,
-                    double *mu, void *ws, size_t wsb, cudaStream_t st, double *ms) {
+                    double *mu, void *ws, size_t wsb, cudaStream_t st, int **flags) {
     if (shape < 0 || shape >= StepKit<real, valT, R>::kShapes) {
       *status = fail(TB_ERR_INVALID_ARG, "kpm_moments_batched: step shape %d out of range", shape);
       return;
@@ -495,9 +472,9 @@ struct BatchRunOp {
     bt.row0 = bd.row0;
     bt.rows = bd.rows;
     bt.n_snap = bd.n_snap;
-    *status = KpmRunner<real, valT, R>::run_batched(shape, n_pad, sp, col, static_cast<const valT *>(val),
-                                                    static_cast<const valT *>(diag), M, seed, mode, bt, mu, ws, wsb,
-                                                    st, ms);
+    *status = KpmRunner<real, valT, R>::enqueue_batched(shape, n_pad, sp, col, static_cast<const valT *>(val),
+                                                        static_cast<const valT *>(diag), M, seed, mode, bt, mu, ws,
+                                                        wsb, st, flags);
   }
 };
 template <typename real, typename valT, int R>
@@ -544,12 +521,17 @@ struct TuneOp {
                                                 r0, mode, mu_r, ws, ws_bytes, st, step_ms);                       \
   }                                                                                                                \
   template <>                                                                                                      \
-  bool KpmEntry<REAL>::run_batched(int R, tb_status *status, int shape, int64_t n_pad, const int64_t *slice_ptr,  \
-                                   const int32_t *col, const void *val, const void *diag, int M, uint64_t seed,   \
-                                   int mode, const BatchDesc &bt, double *mu, void *ws, size_t ws_bytes,          \
-                                   cudaStream_t st, double *graph_ms) {                                           \
-    return KpmDispatch<REAL, REAL>::call<BatchRunOp>(R, status, shape, n_pad, slice_ptr, col, val, diag, M, seed, \
-                                                     mode, bt, mu, ws, ws_bytes, st, graph_ms);                   \
+  bool KpmEntry<REAL>::prepare(int R, int shape) {                                                                 \
+    bool ok = false;                                                                                               \
+    return KpmDispatch<REAL, REAL>::call<PrepOp>(R, shape, &ok) && ok;                                             \
+  }                                                                                                                \
+  template <>                                                                                                      \
+  bool KpmEntry<REAL>::enqueue_batched(int R, tb_status *status, int shape, int64_t n_pad,                         \
+                                       const int64_t *slice_ptr, const int32_t *col, const void *val,              \
+                                       const void *diag, int M, uint64_t seed, int mode, const BatchDesc &bt,      \
+                                       double *mu, void *ws, size_t ws_bytes, cudaStream_t st, int **flags) {      \
+    return KpmDispatch<REAL, REAL>::call<BatchEnqueueOp>(R, status, shape, n_pad, slice_ptr, col, val, diag, M,   \
+                                                         seed, mode, bt, mu, ws, ws_bytes, st, flags);             \
   }                                                                                                                \
   template <>                                                                                                      \
   bool KpmEntry<REAL>::autotune(int R, tb_status *status, int64_t n, const int64_t *slice_ptr, const int32_t *col, \

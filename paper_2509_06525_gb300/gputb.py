@@ -55,6 +55,8 @@ SIGNATURES = {
     "kpm_moments_batched_workspace_size": (_c_sz, [_c_i32, _c_vp, _c_vp, _c_i32, _c_i32, _c_i32, _c_vp]),
     "kpm_moments_batched": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_i32, _c_i32,
                                      _c_u64, _c_i32, _c_vp, _c_vp, _c_sz, _c_vp, ctypes.POINTER(_c_dbl)]),
+    "kpm_moments_batched_autotune": (_c_i32, [_c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp,
+                                              _c_i32, _c_i32, _c_i32, _c_vp, _c_sz, _c_vp, _c_vp, _c_vp, _c_i32]),
     "kpm_dos": (_c_i32, [_c_vp, _c_i32, _c_i32, _c_i32, _c_dbl, _c_dbl, _c_dbl, _c_vp, _c_i32, _c_vp, _c_vp]),
     "tb_mlp_set_variant": (_c_i32, [_c_i32]),
     "tb_sk_geometry": (_c_i32, [_c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_i64, _c_vp, _c_dbl, _c_dbl,
@@ -226,37 +228,77 @@ def kpm_moments(H: SellMatrix, a: float, b: float, M: int, R: int, seed: int,
     return mu
 
 
-def kpm_moments_batched(mats, a, b, M: int, R: int, seed: int, doubling: bool = False, stream=None,
-                        timing: Optional[list] = None) -> torch.Tensor:
-    """Moments of every snapshot in one graph launch: mu [S, R, M] (float64,
-    device).  Snapshot s uses seed + s."""
-    import numpy as np
+class _BatchArgs:
+    """Marshalled host arrays of a batch of SELL matrices (kept alive with
+    the call)."""
+
+    def __init__(self, mats, a, b):
+        import numpy as np
+        self.S = len(mats)
+        self.prec = mats[0].precision
+        if any(m.precision != self.prec for m in mats):
+            raise ValueError("all snapshots must share one precision")
+        self.rows = np.array([m.n for m in mats], np.int64)
+        self.aa = np.ascontiguousarray(np.asarray(a, np.float64))
+        self.bb = np.ascontiguousarray(np.asarray(b, np.float64))
+        arr = lambda ts: (ctypes.c_void_p * self.S)(*[(t.data_ptr() if t is not None else None) for t in ts])
+        self.sp, self.col = arr([m.slice_ptr for m in mats]), arr([m.col for m in mats])
+        self.val, self.dg = arr([m.val for m in mats]), arr([m.diag for m in mats])
+        self.dev = mats[0].col.device
+
+    def ptrs(self):
+        c = lambda x: ctypes.cast(x, ctypes.c_void_p)
+        return (self.S, self.rows.ctypes.data_as(ctypes.c_void_p), c(self.sp), c(self.col), c(self.val), c(self.dg),
+                self.prec, self.aa.ctypes.data_as(ctypes.c_void_p), self.bb.ctypes.data_as(ctypes.c_void_p))
+
+
+_BATCH_WS = {}
+
+
+def _batch_workspace(args: "_BatchArgs", M: int, R: int, stream=None) -> torch.Tensor:
+    """A workspace for the batch, reused across calls of the same size so
+    that the library's cached graph (keyed by the workspace) stays valid."""
     L = lib()
-    S = len(mats)
-    prec = mats[0].precision
-    if any(m.precision != prec for m in mats):
-        raise ValueError("all snapshots must share one precision")
-    rows = np.array([m.n for m in mats], np.int64)
-    aa = np.ascontiguousarray(np.asarray(a, np.float64))
-    bb = np.ascontiguousarray(np.asarray(b, np.float64))
-    arr = lambda ts: (ctypes.c_void_p * S)(*[(t.data_ptr() if t is not None else None) for t in ts])
-    sp, col = arr([m.slice_ptr for m in mats]), arr([m.col for m in mats])
-    val, dg = arr([m.val for m in mats]), arr([m.diag for m in mats])
-    need = L.kpm_moments_batched_workspace_size(S, ctypes.cast(sp, ctypes.c_void_p), rows.ctypes.data_as(ctypes.c_void_p),
-                                                M, R, prec, _stream(stream))
+    need = L.kpm_moments_batched_workspace_size(args.S, ctypes.cast(args.sp, ctypes.c_void_p),
+                                                args.rows.ctypes.data_as(ctypes.c_void_p), M, R, args.prec,
+                                                _stream(stream))
     if need == 0:
         raise GputbError("kpm_moments_batched_workspace_size", TB_ERR_INVALID_ARG, f"unsupported R={R} M={M}")
-    dev = mats[0].col.device
-    ws = _workspace(need, dev)
-    ws.fill_(0xFF)  # contents on entry are ignored by the library; keep stale data visible to tests
-    mu = torch.empty((S, R, M), dtype=torch.float64, device=dev)
+    ws = _BATCH_WS.get(args.dev)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, args.dev)
+        _BATCH_WS[args.dev] = ws
+    return ws
+
+
+def kpm_moments_batched_autotune(mats, a, b, R: int, doubling: bool = False, reps: int = 20, stream=None):
+    """Time every step shape on the folded batch; the fastest becomes the
+    table entry of the batch's padded size.  Returns (best, [ms per step])."""
+    args = _BatchArgs(mats, a, b)
+    ws = _batch_workspace(args, 2, R, stream)
+    count = kpm_shape_count(R, args.prec)
+    ms = (ctypes.c_float * count)()
+    best = _c_i32(-1)
+    st = lib().kpm_moments_batched_autotune(*args.ptrs(), int(R), KPM_DOUBLING if doubling else KPM_DIRECT,
+                                            int(reps), _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(best),
+                                            ms, count)
+    _check("kpm_moments_batched_autotune", st)
+    return int(best.value), [float(v) for v in ms]
+
+
+def kpm_moments_batched(mats, a, b, M: int, R: int, seed: int, doubling: bool = False, stream=None,
+                        timing: Optional[list] = None, mu: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Moments of every snapshot in one graph launch: mu [S, R, M] (float64,
+    device).  Snapshot s uses seed + s.  Pass the previous call's `mu` to
+    reuse the library's cached graph of an identical call."""
+    args = _BatchArgs(mats, a, b)
+    ws = _batch_workspace(args, M, R, stream)
+    if mu is None or mu.shape != (args.S, R, M):
+        mu = torch.empty((args.S, R, M), dtype=torch.float64, device=args.dev)
     ms = ctypes.c_double(0.0)
-    st = L.kpm_moments_batched(S, rows.ctypes.data_as(ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
-                               ctypes.cast(col, ctypes.c_void_p), ctypes.cast(val, ctypes.c_void_p),
-                               ctypes.cast(dg, ctypes.c_void_p), prec, aa.ctypes.data_as(ctypes.c_void_p),
-                               bb.ctypes.data_as(ctypes.c_void_p), int(M), int(R), int(seed) & ((1 << 64) - 1),
-                               KPM_DOUBLING if doubling else KPM_DIRECT, _ptr(mu), _ptr(ws), ws.numel(),
-                               _stream(stream), ctypes.byref(ms) if timing is not None else None)
+    st = lib().kpm_moments_batched(*args.ptrs(), int(M), int(R), int(seed) & ((1 << 64) - 1),
+                                   KPM_DOUBLING if doubling else KPM_DIRECT, _ptr(mu), _ptr(ws), ws.numel(),
+                                   _stream(stream), ctypes.byref(ms) if timing is not None else None)
     _check("kpm_moments_batched", st)
     if timing is not None:
         timing.append(ms.value)

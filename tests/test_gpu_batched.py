@@ -131,3 +131,30 @@ def test_large_batch_spans_many_blocks_per_cta(g):
             for k in range(len(mats)):
                 single = g.kpm_moments(mats[k], a[k], b[k], 40, R, 9 + k, doubling=doubling).cpu().numpy()
                 assert np.max(np.abs(mu[k] - single)) <= 1e-12, (doubling, R, k)
+
+
+def test_cached_graph_relaunch_and_recapture(g, snaps):
+    """A second identical call launches the cached graph (same moments bit
+    for bit); changing one snapshot's rescaling recaptures and matches the
+    oracle for the new values; the batched autotuner's choice is correct."""
+    mats = [sell_matrix(ip, idx, t, eps, s.n, torch.float32) for (s, ip, idx, t, eps, H, a, b) in snaps]
+    a = [x[6] for x in snaps]
+    b = [x[7] for x in snaps]
+    m1 = g.kpm_moments_batched(mats, a, b, 64, 8, 3, doubling=True)
+    m2 = g.kpm_moments_batched(mats, a, b, 64, 8, 3, doubling=True, mu=m1.clone())
+    assert torch.equal(m1, m2)
+    a2 = list(a)
+    a2[1] = 1.25 * a2[1]
+    m3 = g.kpm_moments_batched(mats, a2, b, 64, 8, 3, doubling=True).cpu().numpy()
+    s, ip, idx, t, eps, H, _, bk = snaps[1]
+    _, ref = okpm.kpm_moments(H, a2[1], bk, 64, 8, 3 + 1)
+    assert np.max(np.abs(m3[1] - ref)) <= 2e-4
+    best, times = g.kpm_moments_batched_autotune(mats, a, b, 8, doubling=True, reps=3)
+    assert 0 <= best < g.kpm_shape_count(8, torch.float32) and len(times) == g.kpm_shape_count(8, torch.float32)
+    try:
+        m4 = g.kpm_moments_batched(mats, a, b, 64, 8, 3, doubling=True).cpu().numpy()
+        for k, (s, ip, idx, t, eps, H, ak, bk) in enumerate(snaps):
+            _, ref = okpm.kpm_moments(H, ak, bk, 64, 8, 3 + k)
+            assert np.max(np.abs(m4[k] - ref)) <= 2e-4
+    finally:
+        g.kpm_clear_shapes()

@@ -259,3 +259,34 @@ def test_scattered_columns_take_the_gather_path(gputb, shape, R, dtype):
         mu = gputb.kpm_moments(Hd, a, b, 64, R, 77, doubling=doubling).cpu().numpy()
         _, mu_ref = okpm.kpm_moments(H, a, b, 64, R, 77)
         assert np.max(np.abs(mu - mu_ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
+
+
+@pytest.mark.parametrize("R,dtype", [(1, torch.float32), (8, torch.float32), (8, torch.float64)])
+def test_autotuned_shape_matches_oracle(gputb, R, dtype, tmp_path, monkeypatch):
+    """tb_kpm_autotune times every shape on the caller's matrix and stores
+    the fastest for its size class; the next kpm_moments call uses it and
+    matches the oracle; the choice is written to the tuning cache file."""
+    monkeypatch.setenv("GPUTB_TUNE_CACHE", str(tmp_path / "tuned.json"))
+    s = synth.hbn_graphene_junction(40, 30, 0.1, 19)
+    p = synth.teacher_hbn_graphene()
+    indptr, idx, t, eps = _teacher_csr(s, p)
+    H = oha.csr_hamiltonian(s.n, indptr, idx, t, eps)
+    _, _, a, b = obo.spectral_bounds(H, 64, 7)
+    Hd = sell_matrix(indptr, idx, t, eps, s.n, dtype)
+    try:
+        best, times = gputb.kpm_autotune(Hd, a, b, R, doubling=True, reps=3)
+        assert len(times) == gputb.kpm_shape_count(R, dtype) and all(x > 0 for x in times)
+        assert times[best] == min(times)
+        assert gputb.kpm_get_shape(s.n, R, dtype, True) == best
+        mu = gputb.kpm_moments(Hd, a, b, 96, R, 5, doubling=True).cpu().numpy()
+        _, ref = okpm.kpm_moments(H, a, b, 96, R, 5)
+        assert np.max(np.abs(mu - ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
+        import json
+        data = json.load(open(tmp_path / "tuned.json"))
+        entries = list(data.values())[0]
+        assert any(e["shape"] == best and e["R"] == R for e in entries.values())
+        gputb.kpm_clear_shapes()
+        assert gputb.load_tuned_shapes() >= 1
+        assert gputb.kpm_get_shape(s.n, R, dtype, True) == best
+    finally:
+        gputb.kpm_clear_shapes()
