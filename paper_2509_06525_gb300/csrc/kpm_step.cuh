@@ -89,15 +89,18 @@ __device__ __forceinline__ void flush_partials(Acc (&acc)[CPT], Acc (&acc2)[CPT]
 }
 
 // Segmented mode: block `blk` of the current run of RPB-row blocks has just
-// been processed.  Every block of the run except its first gets zeros; when
-// the next block of this CTA starts another snapshot (or there is none) the
+// been processed; the CTA's blocks are blk, blk + step, ... (the grid-stride
+// order of the single-matrix path, so that the CTAs stream neighbouring
+// memory at any moment).  Every block of a run except its first gets zeros;
+// when the CTA's next block lies in another snapshot (or there is none) the
 // run's sums go into the entry of the run's first block.  Uniform across the
 // CTA.
 template <typename real, int R, int CPT, bool DBL, typename Acc>
 __device__ __forceinline__ void segment_boundary(Acc (&acc)[CPT], Acc (&acc2)[CPT],
                                                  double *partial, int64_t slot_stride, const BatchTables &bt,
-                                                 int64_t blk, int rpb, int64_t blk_end, int64_t &run_head) {
-  const int64_t nxt = blk + 1;
+                                                 int64_t blk, int rpb, int64_t blk_end, int64_t &run_head,
+                                                 int64_t step) {
+  const int64_t nxt = blk + step;
   const bool ends = nxt >= blk_end || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
   if (blk != run_head && threadIdx.x < R) {  // every block but the run's first holds zero
     partial[blk * R + threadIdx.x] = 0.0;
@@ -183,12 +186,12 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
   constexpr int RPB = kBlock / TPR;
   const int part = threadIdx.x % TPR;
   DotAcc<real> acc[CPT], acc2[CPT];
-  // SEG (batched): each CTA takes a contiguous run of blocks and reduces
-  // only where the snapshot changes; other blocks' entries are zero
+  // SEG (batched): the CTA's blocks (grid-stride) form runs within one
+  // snapshot, reduced where the snapshot changes; other blocks' entries are 0
   const int64_t nblk = (n + RPB - 1) / RPB;
-  const int64_t b_first = SEG ? nblk * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t b_last = SEG ? nblk * (blockIdx.x + 1) / gridDim.x : nblk;
-  const int64_t b_step = SEG ? 1 : gridDim.x;
+  const int64_t b_first = blockIdx.x;
+  const int64_t b_last = nblk;
+  const int64_t b_step = gridDim.x;
   int64_t run_head = b_first;
   for (int64_t blk = b_first; blk < b_last; blk += b_step) {
     const int64_t row0 = blk * RPB;
@@ -209,7 +212,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
       ld_gather<real, CPT>(x + off, xi);
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head);
+    if (SEG)
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head, b_step);
   }
   if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
@@ -329,10 +333,10 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
-  // tiles of this CTA: grid-stride, or one contiguous run in SEG mode
-  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
-  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
+  // tiles of this CTA: grid-stride (in SEG mode too)
+  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
+  const int64_t t_end = ntiles;
+  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   };
 
   const int64_t my_tiles =
-      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   int64_t run_head = t_begin;
   int64_t issued = 0;
   if (threadIdx.x == 0)
@@ -468,7 +472,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
       ld_gather<real, CPT>(x + off, xi);
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
+    if (SEG)
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x == 0 && issued < my_tiles) issue(issued++);
   }
@@ -541,9 +546,9 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
   const int64_t n_slices = (n + 31) >> 5;
   const int part = threadIdx.x % TPR;
   const int lr0 = threadIdx.x / TPR;
-  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
-  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
+  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
+  const int64_t t_end = ntiles;
+  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
   const real *xp = x + part * CPT * 2;   // this thread's components of every row of x
 
   if (threadIdx.x == 0) {
@@ -593,7 +598,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
   };
 
   const int64_t my_tiles =
-      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   int64_t run_head = t_begin;
   int64_t issued = 0;
   if (threadIdx.x < 32)
@@ -659,7 +664,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
         row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
       }
     }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
+    if (SEG)
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x < 32 && issued < my_tiles) issue(issued++);
   }
@@ -737,11 +743,11 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
-  const int64_t t_begin = SEG ? ntiles * blockIdx.x / gridDim.x : blockIdx.x;
-  const int64_t t_end = SEG ? ntiles * (blockIdx.x + 1) / gridDim.x : ntiles;
-  auto tile_of = [&](int64_t kk) { return SEG ? t_begin + kk : blockIdx.x + kk * gridDim.x; };
+  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
+  const int64_t t_end = ntiles;
+  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
   const int64_t my_tiles =
-      SEG ? t_end - t_begin : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
@@ -870,7 +876,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
       }
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
-    if (SEG) segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head);
+    if (SEG)
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x < 32 && issued < my_tiles && ok && issue(issued)) ++issued;
   }

@@ -7,8 +7,8 @@ Here the structures are large enough that, for every launch shape,
 * a CTA of the bulk-copy ring processes more tiles than the ring has
   stages, so stages are reused and the mbarrier phase parity flips;
 * a CTA of the direct-load kernel iterates its grid-stride loop;
-* in the batched (segmented) form each CTA owns a run of several row blocks
-  that crosses snapshot boundaries.
+* in the batched (segmented) form each CTA visits blocks of several
+  snapshots, in runs of one or several blocks per snapshot.
 The launch geometry is asserted from the library's own grid query, and the
 moments are compared element by element with the FP64 oracle on the same
 seeded inputs.  Tolerances: FP64 moments <= 1e-12 absolute, FP32 <= 2e-4
@@ -150,15 +150,18 @@ def test_batched_runs_cross_snapshots_and_match_oracle(g, batch, dtype):
     n_pad = sum(-(-x["s"].n // 256) * 256 for x in batch)
     assert n_pad >= 400_000
     smallest = min(x["s"].n for x in batch)
+    largest = max(x["s"].n for x in batch)
     for shape in _shapes(g, R, dtype):
         for doubling in (False, True):
             info = g.kpm_shape_info(R, dtype, shape)
             grid = g.kpm_shape_grid(n_pad, R, dtype, doubling, shape)
             blocks = n_pad // info["rows_per_tile"]
-            # several blocks per CTA, and a snapshot spans several CTAs' runs,
-            # so runs start and end inside snapshots and cross their ends
+            # every CTA visits several blocks (grid-stride); in the largest
+            # snapshot a CTA's run holds two or more of them, in the smallest
+            # one at most one, so runs of both kinds end at snapshot changes
             assert blocks // grid >= 3
-            assert smallest // info["rows_per_tile"] > blocks // grid
+            assert largest // info["rows_per_tile"] >= 2 * grid
+            assert smallest // info["rows_per_tile"] < grid
             g.kpm_force_shape(R, dtype, shape)
             mu = g.kpm_moments_batched(mats, a, b, M, R, seed, doubling=doubling).cpu().numpy()
             for k, ref in enumerate(refs):
