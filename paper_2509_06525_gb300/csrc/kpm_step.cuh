@@ -88,20 +88,40 @@ __device__ __forceinline__ void flush_partials(Acc (&acc)[CPT], Acc (&acc2)[CPT]
   for (int c = 0; c < CPT; ++c) acc[c] = acc2[c] = Acc();
 }
 
+// The order in which a CTA visits the tiles (or row blocks): chunks of C
+// consecutive tiles, the chunks dealt out grid-stride.  C = 1 is the plain
+// grid-stride order of the single-matrix path; the segmented (batched) mode
+// takes C = kSegChunk, so that a CTA's run within one snapshot spans up to C
+// tiles (one reduction per run) while the CTAs still stream neighbouring
+// memory at any moment (a window of C x grid tiles).
+constexpr int kSegChunk = 8;
+template <int C>
+struct TileWalk {
+  int64_t ntiles, nchunks;
+  __device__ __forceinline__ explicit TileWalk(int64_t nt) : ntiles(nt), nchunks((nt + C - 1) / C) {}
+  // tiles this CTA visits (the last chunk may be short)
+  __device__ __forceinline__ int64_t count() const {
+    const int64_t b = blockIdx.x;
+    if (b >= nchunks) return 0;
+    const int64_t owned = (nchunks - 1 - b) / gridDim.x + 1;
+    const bool last = (nchunks - 1 - b) % gridDim.x == 0;
+    return owned * C - (last ? nchunks * C - ntiles : 0);
+  }
+  __device__ __forceinline__ int64_t tile(int64_t kk) const {
+    return ((kk / C) * gridDim.x + blockIdx.x) * C + kk % C;
+  }
+};
+
 // Segmented mode: block `blk` of the current run of RPB-row blocks has just
-// been processed; the CTA's blocks are blk, blk + step, ... (the grid-stride
-// order of the single-matrix path, so that the CTAs stream neighbouring
-// memory at any moment).  Every block of a run except its first gets zeros;
-// when the CTA's next block lies in another snapshot (or there is none) the
-// run's sums go into the entry of the run's first block.  Uniform across the
-// CTA.
+// been processed; `nxt` is this CTA's next block (-1 if none).  Every block
+// of a run except its first gets zeros; when the next block lies in another
+// snapshot (or there is none) the run's sums go into the entry of the run's
+// first block.  Uniform across the CTA.
 template <typename real, int R, int CPT, bool DBL, typename Acc>
 __device__ __forceinline__ void segment_boundary(Acc (&acc)[CPT], Acc (&acc2)[CPT],
                                                  double *partial, int64_t slot_stride, const BatchTables &bt,
-                                                 int64_t blk, int rpb, int64_t blk_end, int64_t &run_head,
-                                                 int64_t step) {
-  const int64_t nxt = blk + step;
-  const bool ends = nxt >= blk_end || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
+                                                 int64_t blk, int rpb, int64_t nxt, int64_t &run_head) {
+  const bool ends = nxt < 0 || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
   if (blk != run_head && threadIdx.x < R) {  // every block but the run's first holds zero
     partial[blk * R + threadIdx.x] = 0.0;
     if (DBL) partial[slot_stride + blk * R + threadIdx.x] = 0.0;
@@ -188,12 +208,11 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
   DotAcc<real> acc[CPT], acc2[CPT];
   // SEG (batched): the CTA's blocks (grid-stride) form runs within one
   // snapshot, reduced where the snapshot changes; other blocks' entries are 0
-  const int64_t nblk = (n + RPB - 1) / RPB;
-  const int64_t b_first = blockIdx.x;
-  const int64_t b_last = nblk;
-  const int64_t b_step = gridDim.x;
-  int64_t run_head = b_first;
-  for (int64_t blk = b_first; blk < b_last; blk += b_step) {
+  const TileWalk<SEG ? kSegChunk : 1> walk((n + RPB - 1) / RPB);
+  const int64_t my_blocks = walk.count();
+  int64_t run_head = walk.tile(0);
+  for (int64_t kb = 0; kb < my_blocks; ++kb) {
+    const int64_t blk = walk.tile(kb);
     const int64_t row0 = blk * RPB;
     const int64_t i = row0 + threadIdx.x / TPR;
     if (i < n) {
@@ -213,7 +232,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
     if (SEG)
-      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB, b_last, run_head, b_step);
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, blk, RPB,
+                                          kb + 1 < my_blocks ? walk.tile(kb + 1) : -1, run_head);
   }
   if (!SEG) flush_partials<real, R, CPT, DBL>(acc, acc2, partial, blockIdx.x, slot_stride);
 }
@@ -334,9 +354,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
   // tiles of this CTA: grid-stride (in SEG mode too)
-  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
-  const int64_t t_end = ntiles;
-  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
+  const TileWalk<SEG ? kSegChunk : 1> walk(ntiles);   // this CTA's tiles, in order
+  auto tile_of = [&](int64_t kk) { return walk.tile(kk); };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
@@ -373,9 +392,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     if (!DBL) bulk_g2s(s_v0(st), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
   };
 
-  const int64_t my_tiles =
-      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  int64_t run_head = t_begin;
+  const int64_t my_tiles = walk.count();
+  int64_t run_head = tile_of(0);
   int64_t issued = 0;
   if (threadIdx.x == 0)
     for (; issued < my_tiles && issued < STAGES; ++issued) issue(issued);
@@ -473,7 +491,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
     if (SEG)
-      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR,
+                                          kk + 1 < my_tiles ? tile_of(kk + 1) : -1, run_head);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x == 0 && issued < my_tiles) issue(issued++);
   }
@@ -546,9 +565,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
   const int64_t n_slices = (n + 31) >> 5;
   const int part = threadIdx.x % TPR;
   const int lr0 = threadIdx.x / TPR;
-  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
-  const int64_t t_end = ntiles;
-  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
+  const TileWalk<SEG ? kSegChunk : 1> walk(ntiles);   // this CTA's tiles, in order
+  auto tile_of = [&](int64_t kk) { return walk.tile(kk); };
   const real *xp = x + part * CPT * 2;   // this thread's components of every row of x
 
   if (threadIdx.x == 0) {
@@ -597,9 +615,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
     }
   };
 
-  const int64_t my_tiles =
-      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  int64_t run_head = t_begin;
+  const int64_t my_tiles = walk.count();
+  int64_t run_head = tile_of(0);
   int64_t issued = 0;
   if (threadIdx.x < 32)
     for (; issued < my_tiles && issued < STAGES; ++issued) issue(issued);
@@ -665,7 +682,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_ring2_kernel(
       }
     }
     if (SEG)
-      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR,
+                                          kk + 1 < my_tiles ? tile_of(kk + 1) : -1, run_head);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x < 32 && issued < my_tiles) issue(issued++);
   }
@@ -743,11 +761,9 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
-  const int64_t t_begin = blockIdx.x;   // grid-stride over tiles (segmented mode too)
-  const int64_t t_end = ntiles;
-  auto tile_of = [&](int64_t kk) { return blockIdx.x + kk * gridDim.x; };
-  const int64_t my_tiles =
-      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const TileWalk<SEG ? kSegChunk : 1> walk(ntiles);   // this CTA's tiles, in order
+  auto tile_of = [&](int64_t kk) { return walk.tile(kk); };
+  const int64_t my_tiles = walk.count();
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
@@ -825,7 +841,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     while (issued < my_tiles && issued < STAGES && issue(issued)) ++issued;
   }
 
-  int64_t run_head = t_begin;
+  int64_t run_head = tile_of(0);
   DotAcc<real> acc[CPT], acc2[CPT];
   int64_t kk = 0;
   for (; kk < my_tiles; ++kk) {
@@ -877,7 +893,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
       row_finish<real, CPT, FIRST, DBL>(y, xi, p, z, d, alpha, out + off, acc, acc2);
     }
     if (SEG)
-      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR, t_end, run_head, gridDim.x);
+      segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR,
+                                          kk + 1 < my_tiles ? tile_of(kk + 1) : -1, run_head);
     __syncthreads();  // every thread is done with this stage
     if (threadIdx.x < 32 && issued < my_tiles && ok && issue(issued)) ++issued;
   }
