@@ -84,30 +84,49 @@ __global__ void __launch_bounds__(kBlock) random_phase_kernel(int64_t n, uint64_
   if (!SEG) cta_partial<R, CPT>(acc, partial + (int64_t)blockIdx.x * R);
 }
 
-// batched: mu[s][r][m] from the rpb-row block partials of snapshot s (block order)
-__global__ void batched_reduce_kernel(BatchTables bt, int M, int R, int rpb, int64_t nblk,
-                                      const double *__restrict__ partial, int doubling, double *__restrict__ mu,
-                                      int *__restrict__ flags) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)bt.n_snap * R * M) return;
-  const int m = static_cast<int>(t % M);
-  const int r = static_cast<int>((t / M) % R);
-  const int s = static_cast<int>(t / ((int64_t)M * R));
+// batched reduction, step 1: one warp per (snapshot s, moment slot m) sums
+// the slot's block partials of s -- a contiguous run of (b1 - b0) R doubles,
+// read coalesced; lane l takes entries l, l + 32, ... (vector l mod R), then
+// lanes of one vector are added in a fixed shuffle tree -- and writes the
+// raw sums S_m into mu[s][r][m] (deterministic)
+__global__ void batched_slot_sum_kernel(BatchTables bt, int M, int R, int rpb, int64_t nblk,
+                                        const double *__restrict__ partial, double *__restrict__ mu) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)bt.n_snap * M) return;
+  const int s = static_cast<int>(w / M), m = static_cast<int>(w % M);
   const int64_t rows = bt.rows[s];
   const int64_t b0 = bt.row0[s] / rpb;
   const int64_t b1 = (bt.row0[s] + (rows + kBatchTile - 1) / kBatchTile * kBatchTile) / rpb;
-  const double inv_n = 1.0 / (double)rows;
-  auto slot = [&](int k) {
-    const double *p = partial + (int64_t)k * nblk * R + r;
-    double acc = 0.0;
-    for (int64_t q = b0; q < b1; ++q) acc += p[q * R];
-    return acc * inv_n;
-  };
-  double v = slot(m);
-  if (doubling && m >= 2) v = 2.0 * v - slot(m & 1);
-  mu[t] = v;
-  if (!isfinite(v)) atomicOr(flags, 2);
-  else if (fabs(v) > 1.0 + 1e-6) atomicOr(flags, 1);
+  const double *p = partial + (int64_t)m * nblk * R + b0 * R;
+  const int64_t cnt = (b1 - b0) * R;
+  double acc = 0.0;
+  for (int64_t e = lane; e < cnt; e += 32) acc += p[e];
+  for (int off = 16; off >= R; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane < R) mu[((int64_t)s * R + lane) * M + m] = acc;
+}
+
+// step 2: one thread per (snapshot, vector) turns the raw sums into moments
+// in place: mu_m = S_m / n, and in doubling mode mu_m = 2 S_m / n - mu_(m mod 2)
+// for m >= 2 (Weisse et al. 2006)
+__global__ void batched_moments_kernel(BatchTables bt, int M, int R, int doubling, double *__restrict__ mu,
+                                       int *__restrict__ flags) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)bt.n_snap * R) return;
+  const int s = static_cast<int>(t / R);
+  double *row = mu + t * M;
+  const double inv_n = 1.0 / (double)bt.rows[s];
+  const double mu0 = row[0] * inv_n, mu1 = M > 1 ? row[1] * inv_n : 0.0;
+  bool bad = false, big = false;
+  for (int m = 0; m < M; ++m) {
+    double v = m == 0 ? mu0 : (m == 1 ? mu1 : row[m] * inv_n);
+    if (doubling && m >= 2) v = 2.0 * v - ((m & 1) ? mu1 : mu0);
+    row[m] = v;
+    bad = bad || !isfinite(v);
+    big = big || fabs(v) > 1.0 + 1e-6;
+  }
+  if (bad) atomicOr(flags, 2);
+  else if (big) atomicOr(flags, 1);
 }
 
 template <typename real, typename valT, int R>
@@ -202,9 +221,12 @@ struct KpmRunner {
     }
     if (ev_end) TB_CUDA(cudaEventRecord(ev_end, st));
     if (SEG) {
-      const int64_t total = (int64_t)bt.n_snap * M * R;
-      batched_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(bt, M, R, rpb, units, partial,
-                                                                             dbl ? 1 : 0, mu_r, flags);
+      const int64_t warps = (int64_t)bt.n_snap * M;
+      batched_slot_sum_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(bt, M, R, rpb, units, partial,
+                                                                                     mu_r);
+      TB_CHECK_LAUNCH();
+      const int64_t vecs = (int64_t)bt.n_snap * R;
+      batched_moments_kernel<<<(unsigned)((vecs + 127) / 128), 128, 0, st>>>(bt, M, R, dbl ? 1 : 0, mu_r, flags);
     } else {
       const int total = M * R;
       moment_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(partial, grid, R, M, 1.0 / (double)n, dbl ? 1 : 0,

@@ -121,7 +121,10 @@ template <typename real, int R, int CPT, bool DBL, typename Acc>
 __device__ __forceinline__ void segment_boundary(Acc (&acc)[CPT], Acc (&acc2)[CPT],
                                                  double *partial, int64_t slot_stride, const BatchTables &bt,
                                                  int64_t blk, int rpb, int64_t nxt, int64_t &run_head) {
-  const bool ends = nxt < 0 || bt.tile_snap[(nxt * rpb) / kBatchTile] != bt.tile_snap[(blk * rpb) / kBatchTile];
+  // snapshots start on kBatchTile-row boundaries: blocks inside one such
+  // group share their snapshot, so only a group change needs the table
+  const int64_t g_nxt = (nxt * rpb) / kBatchTile, g_blk = (blk * rpb) / kBatchTile;
+  const bool ends = nxt < 0 || (g_nxt != g_blk && __ldg(bt.tile_snap + g_nxt) != __ldg(bt.tile_snap + g_blk));
   if (blk != run_head && threadIdx.x < R) {  // every block but the run's first holds zero
     partial[blk * R + threadIdx.x] = 0.0;
     if (DBL) partial[slot_stride + blk * R + threadIdx.x] = 0.0;
