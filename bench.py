@@ -50,16 +50,17 @@ L2_BYTES = 126 * 1024 * 1024
 # of the same structure (see profiles/); scaled to a full launch by the rows
 # processed.  Keyed by (precision, R, mode, shape description); any kernel
 # without an entry, or changed since its capture, reports null.
-def _shape_key(pipelined, cpt, stages, minb, rows_per_tile):
+def _shape_key(pipelined, cpt, stages, minb, rows_per_tile, options=0, band_rows=0):
     return tuple(sorted(dict(pipelined=pipelined, complex_per_thread=cpt, stages=stages, min_blocks=minb,
-                             rows_per_tile=rows_per_tile, rows_per_thread=1, staged_vectors=1).items()))
+                             rows_per_tile=rows_per_tile, rows_per_thread=1, staged_vectors=1, options=options,
+                             band_rows=band_rows).items()))
 
 
 MEASURED_TRAFFIC_PER_ROW = {
     # profiles/traffic_cheb_step_small_cases.md: 2M-row thermal sheet, 560.3 MB per launch
     ("f32", 8, "doubling", _shape_key(1, 2, 2, 4, 64)): 560_320_768 / 2_000_000,
     # 8M-row pristine sheet, 764.6 MB per launch
-    ("f32", 1, "doubling", _shape_key(3, 1, 2, 3, 256)): 764_593_536 / 8_000_000,
+    ("f32", 1, "doubling", _shape_key(3, 1, 2, 3, 256, 0, 1024)): 764_593_536 / 8_000_000,
 }
 
 

@@ -166,13 +166,21 @@ TB_API size_t kpm_moments_workspace_size(int64_t n, int32_t M, int32_t R, int32_
 typedef struct {
   int32_t pipelined;            /* 0: direct loads; 1: bulk-copy ring of col, val
                                    and vector rows; 2: ring that also stages the
-                                   slice offsets and the diagonal            */
+                                   slice offsets and the diagonal; 3: banded
+                                   step (x bands staged, needs the band plan,
+                                   which kpm_moments builds in its workspace) */
   int32_t complex_per_thread;   /* complex numbers per thread (R / threads per row) */
   int32_t stages;               /* ring depth (0 for direct loads)           */
   int32_t min_blocks;           /* resident CTAs per SM of the register budget */
   int32_t rows_per_tile;        /* rows a CTA processes per tile             */
   int32_t rows_per_thread;      /* rows each thread takes per tile           */
   int32_t staged_vectors;       /* 1: v_{n-1} (and v0) rows go through the ring */
+  int32_t options;              /* ring (1): 1 = 12-slot body, 2 = FP32 dot sums
+                                   folded to FP64, 4 = L2 prefetch of the next
+                                   tile's neighbours, 8 = staged slice offsets;
+                                   banded (3): 1 = no CTA barrier per tile
+                                   (stages released per warp)              */
+  int32_t band_rows;            /* banded (3): x rows a stage holds          */
 } tb_step_shape;
 
 /* Number of shapes for (R, precision); 0 if R is unsupported. */

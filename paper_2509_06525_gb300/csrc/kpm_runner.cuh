@@ -445,6 +445,8 @@ struct InfoOp {
     out->rows_per_tile = Kit::rows_per_block(shape);
     out->rows_per_thread = sh.kind == 2 ? sh.rpt : 1;
     out->staged_vectors = sh.kind == 0 ? 0 : sh.svec;
+    out->options = sh.opt;
+    out->band_rows = sh.kind == 3 ? sh.brows : 0;
   }
 };
 template <typename real, typename valT, int R>

@@ -730,7 +730,15 @@ struct BandGeom {
                               STAGES <= 4 && ROWS <= 65535;
 };
 
-template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int ROWS, bool FIRST, bool DBL, bool SEG>
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// FREE: no CTA barrier per tile; each warp releases a stage on its "empty"
+// mbarrier (8 arrivals), and warp 0 refills a stage once its previous tile
+// is released by every warp, before waiting on its own next stage.
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int ROWS, bool FREE, bool FIRST,
+          bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
@@ -743,6 +751,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // [STAGES]
   uint64_t *recbar = full + 8;                                  // [2]
+  uint64_t *empty = full + 10;                                  // [STAGES] (FREE)
   BandRec *rring = reinterpret_cast<BandRec *>(smem + 256);     // [2]
   unsigned char *ring = smem + 256 + 2 * G::kRecBytes;
   auto s_rec = [&](int st) { return reinterpret_cast<BandRec *>(ring + st * G::kStageBytes); };
@@ -770,6 +779,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(full + st, 1);
+    if (FREE)
+      for (int st = 0; st < STAGES; ++st) mbar_init(empty + st, kWarps);
     mbar_init(recbar, 1);
     mbar_init(recbar + 1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -850,8 +861,26 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   for (; kk < my_tiles; ++kk) {
     const int st = static_cast<int>(kk % STAGES);
     const uint32_t parity = static_cast<uint32_t>((kk / STAGES) & 1);
-    const bool mine = threadIdx.x >= 32 || ok;
-    ok = __syncthreads_and(mine && mbar_wait_bounded(full + st, parity)) != 0;
+    if (FREE) {
+      if (threadIdx.x < 32) {
+        // refill the stages up to tile kk + STAGES - 1, each once every warp
+        // has released its previous tile
+        while (ok && issued < my_tiles && issued <= kk + STAGES - 1) {
+          const int64_t prev_use = issued / STAGES - 1;
+          const bool freed = mbar_wait_bounded(empty + issued % STAGES, static_cast<uint32_t>(prev_use & 1));
+          if (!__all_sync(0xffffffffu, freed) || !issue(issued)) {
+            ok = false;
+            break;
+          }
+          ++issued;
+        }
+      }
+      const bool got = ok && mbar_wait_bounded(full + st, parity);
+      ok = __all_sync(0xffffffffu, got);
+    } else {
+      const bool mine = threadIdx.x >= 32 || ok;
+      ok = __syncthreads_and(mine && mbar_wait_bounded(full + st, parity)) != 0;
+    }
     if (!ok) break;
     const int64_t tile = tile_of(kk);
     const int64_t r0 = tile * TR;
@@ -898,9 +927,15 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     if (SEG)
       segment_boundary<real, R, CPT, DBL>(acc, acc2, partial, slot_stride, bt, tile, TR,
                                           kk + 1 < my_tiles ? tile_of(kk + 1) : -1, run_head);
-    __syncthreads();  // every thread is done with this stage
-    if (threadIdx.x < 32 && issued < my_tiles && ok && issue(issued)) ++issued;
+    if (FREE) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + st);   // this warp is done with the stage
+    } else {
+      __syncthreads();  // every thread is done with this stage
+      if (threadIdx.x < 32 && issued < my_tiles && ok && issue(issued)) ++issued;
+    }
   }
+  if (FREE) ok = __syncthreads_and(ok) != 0;   // a warp that gave up reports for the CTA
   if (!ok) {
     if (threadIdx.x == 0) {
       atomicOr(flags, 4);
@@ -965,7 +1000,9 @@ constexpr StepShape P(int cpt, int stages, int minb, int opt = 0) { return {1, o
 constexpr StepShape Q(int cpt, int stages, int minb, int rpt, int svec) {
   return {2, 0, cpt, stages, minb, rpt, svec, 0};
 }
-constexpr StepShape B(int cpt, int stages, int minb, int brows) { return {3, 0, cpt, stages, minb, 1, 1, brows}; }
+constexpr StepShape B(int cpt, int stages, int minb, int brows, int opt = 0) {
+  return {3, opt, cpt, stages, minb, 1, 1, brows};
+}
 
 template <typename real, int R> struct Shapes;
 // FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
@@ -973,7 +1010,8 @@ template <typename real, int R> struct Shapes;
 // faster than 3), the 3-stage ring with 16-byte accesses (CPT = 2) and 4 CTAs
 // where four or more threads share a row.
 template <> struct Shapes<float, 1> {
-  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5), B(1, 2, 3, 1024), B(1, 2, 2, 1024)};
+  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5), B(1, 2, 3, 1024), B(1, 2, 2, 1024),
+                                     B(1, 2, 3, 1024, 1), B(1, 3, 2, 1024, 1)};
 };
 template <> struct Shapes<float, 2> {
   static constexpr StepShape at[] = {D(2, 3), D(1, 4)};
@@ -982,9 +1020,9 @@ template <> struct Shapes<float, 4> {
   static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), Q(2, 3, 3, 1, 0)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),         P(2, 4, 4),         D(2, 3),
-                                     P(2, 3, 4, 1), B(2, 2, 3, 320),    B(2, 2, 4, 256),    B(2, 3, 2, 320),
-                                     B(1, 2, 3, 320)};
+  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),      P(2, 4, 4),      D(2, 3),
+                                     P(2, 3, 4, 1), B(2, 2, 3, 320), B(2, 3, 2, 320), B(4, 2, 2, 480),
+                                     B(2, 2, 3, 320, 1), B(2, 3, 2, 320, 1)};
 };
 template <> struct Shapes<float, 16> {
   static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 3, 1, 0), B(2, 2, 3, 192),
@@ -1057,7 +1095,8 @@ struct ShapeKit {
     else if constexpr (KIND == 2)
       return cheb_step_ring2_kernel<real, valT, R, CPT, S, MINB, RPT, SVEC != 0, FIRST, DBL, SEG>;
     else if constexpr (KIND == 3)
-      return cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), FIRST, DBL, SEG>;
+      return cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0, FIRST, DBL,
+                                   SEG>;
     else
       return cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG>;
   }
@@ -1124,7 +1163,8 @@ struct ShapeKit {
       cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
     else if constexpr (KIND == 3)
-      cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), FIRST, DBL, SEG><<<grid, kBlock, smem<DBL>(), st>>>(
+      cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0, FIRST, DBL, SEG>
+          <<<grid, kBlock, smem<DBL>(), st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt, bp.recs,
           bp.lidx);
     else

@@ -309,7 +309,7 @@ class StepShape(ctypes.Structure):
     """tb_step_shape of include/gputb.h."""
     _fields_ = [("pipelined", _c_i32), ("complex_per_thread", _c_i32), ("stages", _c_i32),
                 ("min_blocks", _c_i32), ("rows_per_tile", _c_i32), ("rows_per_thread", _c_i32),
-                ("staged_vectors", _c_i32)]
+                ("staged_vectors", _c_i32), ("options", _c_i32), ("band_rows", _c_i32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
