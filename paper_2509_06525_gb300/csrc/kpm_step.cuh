@@ -906,17 +906,23 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
         const real *xs = s_x(st) + part * CPT * 2;
         const uint16_t *li = s_idx(st) + sb + (lr & 31);
         const valT *vs = s_val(st) + sb + (lr & 31);
-        // 64-register budgets (4 CTAs) keep four slots in flight, larger ones all
-#pragma unroll(MINB >= 4 ? 4 : kBandSlots)
-        for (int s = 0; s < kBandSlots; ++s) {
-          if (s < w) {
-            real xv[2 * CPT];
-            const real h = static_cast<real>(vs[32 * s]);
-            memcpy(xv, xs + (int)li[32 * s] * RE, sizeof(xv));
+        // rows of slices at most 12 wide (graphene within 3 A) take a 12-slot
+        // body; 64-register budgets (4 CTAs) keep four slots in flight
+        auto slots = [&](auto wmax) {
+          constexpr int W = decltype(wmax)::value;
+#pragma unroll(MINB >= 4 ? 4 : W)
+          for (int s = 0; s < W; ++s) {
+            if (s < w) {
+              real xv[2 * CPT];
+              const real h = static_cast<real>(vs[32 * s]);
+              memcpy(xv, xs + (int)li[32 * s] * RE, sizeof(xv));
 #pragma unroll
-            for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+              for (int c = 0; c < 2 * CPT; ++c) y[c] = fma(h, xv[c], y[c]);
+            }
           }
-        }
+        };
+        if (w <= 12) slots(std::integral_constant<int, 12>{});
+        else slots(std::integral_constant<int, kBandSlots>{});
         memcpy(xi, xs + (rc.own + lr) * RE, sizeof(xi));
       } else {
         row_product_direct<real, valT, R, CPT>(col, val, x, rc.e0 + sb + (lr & 31), w, part, y);
@@ -1021,8 +1027,8 @@ template <> struct Shapes<float, 4> {
 };
 template <> struct Shapes<float, 8> {
   static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),      P(2, 4, 4),      D(2, 3),
-                                     P(2, 3, 4, 1), B(2, 2, 3, 320), B(2, 3, 2, 320), B(4, 2, 2, 480),
-                                     B(2, 2, 3, 320, 1), B(2, 3, 2, 320, 1)};
+                                     P(2, 3, 4, 1), B(2, 2, 3, 320), B(2, 2, 3, 320, 1), B(4, 2, 2, 480, 1),
+                                     B(2, 2, 4, 256, 1)};
 };
 template <> struct Shapes<float, 16> {
   static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 3, 1, 0), B(2, 2, 3, 192),
