@@ -175,11 +175,9 @@ typedef struct {
   int32_t rows_per_tile;        /* rows a CTA processes per tile             */
   int32_t rows_per_thread;      /* rows each thread takes per tile           */
   int32_t staged_vectors;       /* 1: v_{n-1} (and v0) rows go through the ring */
-  int32_t options;              /* ring (1): 1 = 12-slot body, 2 = FP32 dot sums
-                                   folded to FP64, 4 = L2 prefetch of the next
-                                   tile's neighbours, 8 = staged slice offsets;
-                                   banded (3): 1 = no CTA barrier per tile
-                                   (stages released per warp)              */
+  int32_t options;              /* ring (1): 1 = 12-slot body for slices at most
+                                   12 wide; banded (3): 1 = no CTA barrier per
+                                   tile (stages released per warp)          */
   int32_t band_rows;            /* banded (3): x rows a stage holds          */
 } tb_step_shape;
 

@@ -52,24 +52,6 @@ constexpr int kFastW = 16;
 // Write the CTA's partial sums as entry `idx` of the moment slot (and of the
 // next slot for the doubling pair), then restart the accumulators.  Every
 // thread of the CTA must call it.
-// FP32 dot accumulator of the opt-2 ring shapes: a plain FP32 running sum
-// that is folded into an FP64 total every 8 additions, so that no FP32 sum
-// holds more than 8 terms (relative error below 8 x 2^-24 per fold).
-struct FoldAcc {
-  float s = 0.0f;
-  double d = 0.0;
-  int k = 0;
-  __device__ __forceinline__ void add(float ar, float ai, float br, float bi) {
-    s = fmaf(ar, br, fmaf(ai, bi, s));
-    if (++k == 8) {
-      d += (double)s;
-      s = 0.0f;
-      k = 0;
-    }
-  }
-  __device__ __forceinline__ double value() const { return d + (double)s; }
-};
-
 template <typename real, int R, int CPT, bool DBL, typename Acc>
 __device__ __forceinline__ void flush_partials(Acc (&acc)[CPT], Acc (&acc2)[CPT], double *partial, int64_t idx,
                                                int64_t slot_stride) {
@@ -287,18 +269,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-// NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode);
-// HDR: the stage starts with the tile's slice offsets (opt 8)
-template <typename real, typename valT, int R, int CPT, int STAGES, int NV = 2, bool HDR = false>
+// NV: vector rows streamed per stage (v_{n-1}, and v0 unless in doubling mode)
+template <typename real, typename valT, int R, int CPT, int STAGES, int NV = 2>
 struct BulkGeom {
   static constexpr int TPR = R / CPT;
   static constexpr int TR = kBlock / TPR;                       // rows per tile
   static constexpr int kEl = TR * kFastW;                       // SELL elements per stage
-  static constexpr size_t kHdrBytes = HDR ? ((TR / 32 + 1) * 8 + 15) / 16 * 16 : 0;
   static constexpr size_t kColBytes = kEl * sizeof(int32_t);
   static constexpr size_t kValBytes = kEl * sizeof(valT);
   static constexpr size_t kVecBytes = (size_t)TR * R * 2 * sizeof(real);
-  static constexpr size_t kStageBytes = kHdrBytes + kColBytes + kValBytes + NV * kVecBytes;
+  static constexpr size_t kStageBytes = kColBytes + kValBytes + NV * kVecBytes;
   static constexpr size_t kSmem = 128 + STAGES * kStageBytes;  // mbarriers first
   static constexpr bool kOk = TR % 32 == 0 && kSmem <= 200 * 1024 && STAGES >= 2 && STAGES <= 8;
 };
@@ -319,39 +299,27 @@ __device__ __forceinline__ void row_product_smem(const int32_t *cs, const valT *
   }
 }
 
-// Options of the ring kernel (bit mask OPT, chosen per shape):
+// Option of the ring kernel (bit mask OPT, chosen per shape):
 //   1  rows of slices at most 12 wide take a 12-slot unrolled body
-//   2  FP32 vectors: FoldAcc dot sums (plain FP32, folded into FP64 every 8
-//      terms) instead of Kahan pairs
-//   4  after a tile's wait, one thread per row issues L2 prefetches of the
-//      next tile's neighbour rows of x (from that stage's columns, when the
-//      stage is already complete), so first touches of x rows come from L2
-//   8  the producer writes the tile's slice offsets into the stage, and rows
-//      read them from shared memory instead of slice_ptr
 template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int OPT, bool FIRST, bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
     int *__restrict__ flags, int64_t slot_stride, BatchTables bt) {
-  constexpr bool HDR = (OPT & 8) != 0;
-  using G = BulkGeom<real, valT, R, CPT, STAGES, DBL ? 1 : 2, HDR>;
-  using Acc = std::conditional_t<(OPT & 2) != 0 && sizeof(real) == 4, FoldAcc, DotAcc<real>>;
+  using G = BulkGeom<real, valT, R, CPT, STAGES, DBL ? 1 : 2>;
+  using Acc = DotAcc<real>;
   constexpr int TPR = G::TPR, TR = G::TR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);
   unsigned char *ring = smem + 128;
-  auto s_hdr = [&](int st) { return reinterpret_cast<int64_t *>(ring + st * G::kStageBytes); };
-  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes + G::kHdrBytes); };
-  auto s_val = [&](int st) {
-    return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes);
-  };
+  auto s_col = [&](int st) { return reinterpret_cast<int32_t *>(ring + st * G::kStageBytes); };
+  auto s_val = [&](int st) { return reinterpret_cast<valT *>(ring + st * G::kStageBytes + G::kColBytes); };
   auto s_prev = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes);
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes);
   };
   auto s_v0 = [&](int st) {
-    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kHdrBytes + G::kColBytes + G::kValBytes +
-                                    G::kVecBytes);
+    return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kColBytes + G::kValBytes + G::kVecBytes);
   };
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
@@ -374,12 +342,6 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     const int64_t k0 = r0 >> 5;
     const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
     const int64_t e0 = slice_ptr[k0], e1 = slice_ptr[k1];
-    if (HDR) {
-      int64_t *h = s_hdr(st);
-      h[0] = e0;
-#pragma unroll
-      for (int q = 1; q <= TR / 32; ++q) h[q] = (k0 + q < k1) ? slice_ptr[k0 + q] : e1;
-    }
     const bool bulk = (e1 - e0) <= G::kEl;
     const uint32_t ebytes = bulk ? static_cast<uint32_t>(e1 - e0) : 0u;
     uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
@@ -412,44 +374,13 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
     const int64_t tile = tile_of(kk);
     const int64_t r0 = tile * TR;
     const int64_t i = r0 + lr;
-    if ((OPT & 4) && part == 0 && kk + 1 < my_tiles) {
-      // the next tile's neighbour rows of x into L2 (if its stage is complete)
-      const int st1 = static_cast<int>((kk + 1) % STAGES);
-      const int64_t i1 = tile_of(kk + 1) * TR + lr;
-      if (i1 < n && mbar_try_wait(full + st1, static_cast<uint32_t>(((kk + 1) / STAGES) & 1))) {
-        const int64_t k0n = (i1 - lr) >> 5;
-        const int64_t e0n = HDR ? s_hdr(st1)[0] : __ldg(slice_ptr + k0n);
-        const int64_t k1n = min((i1 - lr + TR + 31) >> 5, (n + 31) >> 5);
-        const int64_t e1n = HDR ? s_hdr(st1)[TR / 32] : __ldg(slice_ptr + k1n);
-        if (e1n - e0n <= G::kEl) {
-          const int64_t sbn = HDR ? s_hdr(st1)[lr >> 5] : __ldg(slice_ptr + (i1 >> 5));
-          const int64_t sen = HDR ? s_hdr(st1)[(lr >> 5) + 1] : __ldg(slice_ptr + (i1 >> 5) + 1);
-          const int wn = static_cast<int>((sen - sbn) >> 5);
-          const int32_t *csn = s_col(st1) + (sbn - e0n) + (lr & 31);
-#pragma unroll
-          for (int s = 0; s < kFastW; ++s)
-            if (s < wn) asm volatile("prefetch.global.L2 [%0];" ::"l"(x + (int64_t)csn[32 * s] * R * 2));
-        }
-      }
-    }
     if (i < n) {
       const int64_t k0 = r0 >> 5;
-      int64_t e0, sb;
-      bool bulk;
-      int w;
-      if (HDR) {
-        const int64_t *h = s_hdr(st);
-        e0 = h[0];
-        bulk = (h[TR / 32] - e0) <= G::kEl;
-        sb = h[lr >> 5];
-        w = static_cast<int>((h[(lr >> 5) + 1] - sb) >> 5);
-      } else {
-        const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
-        e0 = __ldg(slice_ptr + k0);
-        bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
-        sb = __ldg(slice_ptr + (i >> 5));
-        w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
-      }
+      const int64_t k1 = min((r0 + TR + 31) >> 5, (n + 31) >> 5);
+      const int64_t e0 = __ldg(slice_ptr + k0);
+      const bool bulk = (__ldg(slice_ptr + k1) - e0) <= G::kEl;
+      const int64_t sb = __ldg(slice_ptr + (i >> 5));
+      const int w = static_cast<int>((__ldg(slice_ptr + (i >> 5) + 1) - sb) >> 5);
       const int loff = (lr * R + part * CPT) * 2;
       real p[2 * CPT], z[2 * CPT];
       if (!FIRST) memcpy(p, s_prev(st) + loff, sizeof(p));
@@ -993,7 +924,7 @@ __global__ void moment_reduce_kernel(const double *__restrict__ partial, int gri
 struct StepShape {
   int kind;        // 0: direct loads, 1: bulk-copy ring, 2: second ring (offsets, diagonal staged),
                    // 3: banded step (x bands staged; needs the band plan)
-  int opt;         // option bits of the bulk-copy ring (see cheb_step_bulk_kernel)
+  int opt;         // options: ring 1 = 12-slot body; banded 1 = no CTA barrier per tile
   int cpt;         // complex numbers per thread
   int stages;      // ring depth (rings only)
   int minb;        // resident CTAs per SM of the register budget
@@ -1011,31 +942,29 @@ constexpr StepShape B(int cpt, int stages, int minb, int brows, int opt = 0) {
 }
 
 template <typename real, int R> struct Shapes;
-// FP32 vectors.  Defaults from timing on GB300 (10M / 100M-atom graphene):
-// one thread per row for R <= 4 (R = 1 with 4 CTAs of 64 registers was 15%
-// faster than 3), the 3-stage ring with 16-byte accesses (CPT = 2) and 4 CTAs
-// where four or more threads share a row.
+// FP32 vectors.  Entry 0 is the hand-picked default of the library's first
+// version; the other entries are the ones that won or came close in the
+// autotuner on GB300 (10M-atom R = 8, 1M-atom R = 16, 100M-atom R = 1):
+// the 2-stage ring, the 12-slot ring, the banded step (fastest at R = 1 and,
+// without CTA barriers, at R = 8).  Slower candidates that were measured and
+// dropped are listed in the design notes.
 template <> struct Shapes<float, 1> {
-  static constexpr StepShape at[] = {D(1, 4), D(1, 3), D(1, 5), B(1, 2, 3, 1024), B(1, 2, 2, 1024),
-                                     B(1, 2, 3, 1024, 1), B(1, 3, 2, 1024, 1)};
+  static constexpr StepShape at[] = {D(1, 4), D(1, 3), B(1, 2, 3, 1024), B(1, 2, 3, 1024, 1)};
 };
 template <> struct Shapes<float, 2> {
   static constexpr StepShape at[] = {D(2, 3), D(1, 4)};
 };
 template <> struct Shapes<float, 4> {
-  static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), Q(2, 3, 3, 1, 0)};
+  static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), B(2, 2, 3, 512, 1)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {P(2, 3, 4),    P(2, 2, 4),      P(2, 4, 4),      D(2, 3),
-                                     P(2, 3, 4, 1), B(2, 2, 3, 320), B(2, 2, 3, 320, 1), B(4, 2, 2, 480, 1),
-                                     B(2, 2, 4, 256, 1)};
+  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(2, 3, 4, 1), D(2, 3), B(2, 2, 3, 320, 1)};
 };
 template <> struct Shapes<float, 16> {
-  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(4, 3, 2), D(2, 3), Q(2, 3, 3, 1, 0), B(2, 2, 3, 192),
-                                     B(4, 2, 2, 320)};
+  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), D(2, 3), B(2, 2, 3, 192), B(2, 2, 3, 192, 1)};
 };
 template <> struct Shapes<float, 32> {
-  static constexpr StepShape at[] = {D(2, 3), P(4, 3, 2), D(4, 2), Q(4, 3, 2, 1, 0)};
+  static constexpr StepShape at[] = {D(2, 3), P(4, 3, 2), D(4, 2)};
 };
 // FP64 vectors (the FP64 pipe, not HBM, limits these on GB300).
 template <> struct Shapes<double, 1> {
@@ -1078,7 +1007,7 @@ struct ShapeKit {
   static constexpr int RPB = (kBlock / TPR) * (KIND == 2 ? RPT : 1);   // rows per tile
   static constexpr int S = STAGES >= 2 ? STAGES : 2;
   template <bool DBL>
-  using GB = BulkGeom<real, valT, R, CPT, S, DBL ? 1 : 2, (OPT & 8) != 0>;
+  using GB = BulkGeom<real, valT, R, CPT, S, DBL ? 1 : 2>;
   template <bool DBL>
   using G2 = Ring2Geom<real, valT, R, CPT, S, RPT, SVEC != 0, DBL ? 1 : 2>;
   template <bool DBL>
