@@ -57,10 +57,12 @@ def _shape_key(pipelined, cpt, stages, minb, rows_per_tile, options=0, band_rows
 
 
 MEASURED_TRAFFIC_PER_ROW = {
-    # profiles/traffic_cheb_step_small_cases.md: 2M-row thermal sheet, 560.3 MB per launch
-    ("f32", 8, "doubling", _shape_key(1, 2, 2, 4, 64)): 560_320_768 / 2_000_000,
-    # 8M-row pristine sheet, 764.6 MB per launch
-    ("f32", 1, "doubling", _shape_key(3, 1, 2, 3, 256, 0, 1024)): 764_593_536 / 8_000_000,
+    # profiles/traffic_cheb_step_small_cases.md: 2M-row thermal sheet, 558.3 MB per launch
+    ("f32", 8, "doubling", _shape_key(1, 2, 2, 4, 64)): 558_285_312 / 2_000_000,
+    # 8M-row pristine sheet, 762.9 MB per launch
+    ("f32", 1, "doubling", _shape_key(3, 1, 2, 3, 256, 0, 1024)): 762_949_376 / 8_000_000,
+    # 2M-row thermal sheet, banded step without CTA barriers, 512.9 MB per launch
+    ("f32", 8, "doubling", _shape_key(3, 2, 2, 3, 64, 1, 320)): 512_879_104 / 2_000_000,
 }
 
 
@@ -100,7 +102,58 @@ def parse_args():
                    help="measure FP32 against FP64 vectors on the 1e6-atom sheet, M = 2048, R = 16 (1) or skip (0)")
     p.add_argument("--lsqt-steps", type=int, default=2,
                    help="VAC conductivity time steps of 0.1 fs measured after the main line (0: skip)")
+    p.add_argument("--kernel-case", default=None, metavar="NXxNY",
+                   help="profiling case only (prints no JSON): on an NX x NY-cell graphene sheet, "
+                        "--case-kernel cheb: teacher FP32 H, two kpm_moments calls (M = 64, doubling) with one "
+                        "forced step shape; env: three environment-network H builds (random model); mlp: "
+                        "three learned-H builds (random per-pair MLP)")
+    p.add_argument("--case-kernel", choices=["cheb", "env", "mlp"], default="cheb")
+    p.add_argument("--case-sigma", type=float, default=0.1, help="kernel case: thermal displacement (A)")
+    p.add_argument("--case-shape", type=int, default=-1, help="kernel case: forced shape (-1: autotuned)")
+    p.add_argument("--case-diag", type=int, default=1, help="kernel case: H carries its onsite diagonal (1) or not (0)")
     return p.parse_args()
+
+
+def run_kernel_case(args):
+    """A small fixed case for ncu captures of one Chebyshev-step shape."""
+    import torch
+    from paper_2509_06525_gb300 import build, gputb as g
+    build.build()
+    nx, ny = (int(v) for v in args.kernel_case.lower().split("x"))
+    R = args.R or 8
+    s = synth.graphene_rect(nx, ny, args.case_sigma, 1003)
+    p = synth.teacher_graphene()
+    pos = torch.tensor(s.positions, device="cuda")
+    spc = torch.tensor(s.species, device="cuda")
+    nb = g.build_neighbors(pos, s.box, s.pbc, p.rcut, r_count=p.r_count, max_width=16)
+    if args.case_kernel != "cheb":
+        cm = synth.descriptor_mixing("identity")
+        if args.case_kernel == "env":
+            model = g.EnvModel(synth.init_env_mlp(11, -1.0), cm, np.zeros(3))
+        else:
+            model = g.MLPModel(synth.init_mlp(3), cm, np.zeros(3))
+            model.set_normalisation(torch.zeros(32, device="cuda"), torch.ones(32, device="cuda"))
+        v = g.compute_descriptors(pos, spc, s.box, s.pbc, p.rcut, nb, model.cmix)
+        for _ in range(3):
+            if args.case_kernel == "env":
+                H = g.build_hamiltonian_env(pos, spc, s.box, s.pbc, p.rcut, nb, model, v=v)
+            else:
+                H = g.build_hamiltonian(pos, spc, s.box, s.pbc, p.rcut, nb, model, v=v, dtype=torch.float32)
+        torch.cuda.synchronize()
+        print("kernel case", args.case_kernel, s.n, "rows,", int(nb.total), "slots, val[0]", float(H.val[0]))
+        return
+    H = g.build_hamiltonian_teacher(pos, spc, s.box, s.pbc, nb, p, dtype=torch.float32,
+                                    with_diag=bool(args.case_diag))
+    bd = g.spectral_bounds(H, 64, synth.LANCZOS_SEED)
+    if args.case_shape >= 0:
+        g.kpm_force_shape(R, torch.float32, args.case_shape)
+    else:
+        g.kpm_autotune(H, bd.a, bd.b, R, doubling=True, record=False)
+    for _ in range(2):
+        mu = g.kpm_moments(H, bd.a, bd.b, args.M or 64, R, synth.KPM_SEED, doubling=True)
+    torch.cuda.synchronize()
+    info = g.kpm_shape_info(R, torch.float32, g.kpm_get_shape(s.n, R, torch.float32, doubling=True))
+    print("kernel case", s.n, "rows, R =", R, "shape", info, "mu0", float(mu[:, 0].mean()))
 
 
 # ---------------------------------------------------------------- structure
@@ -170,6 +223,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- peaks
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
 
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -315,6 +376,7 @@ def batched_measurement(torch, g, rank):
     n_pad = sum(-(-s.n // 256) * 256 for s in snaps)
     desc = g.kpm_shape_info(w["R"], torch.float32, best)
     launch_bytes = step_bytes(nnz, atoms, w["R"], 4, 8, True, True, desc)
+    sell_bytes = step_bytes(nnz, atoms, w["R"], 4, 8, True, True, {"pipelined": 0})
     per = ms[0] / launches
     peak, src = hbm_peak()
     return {"workload": "hbn-junction-64", "snapshots": len(snaps), "atoms": atoms, "padded_rows": n_pad,
@@ -326,6 +388,7 @@ def batched_measurement(torch, g, rank):
                          "bytes_per_launch": launch_bytes, "ms_per_launch": per,
                          "achieved": launch_bytes / (per * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": launch_bytes / (per * 1e-3) / 1e9 / peak, "peak_source": src,
+                         "sell_equivalent_frac": sell_bytes / (per * 1e-3) / 1e9 / peak,
                          "note": "ms = the cached graph's launch: the fold of the 64 snapshots, the random "
                                  "phases, every step and the reduction (the first call, which captures and "
                                  "instantiates the graph, is first_call_s); rows padded to 256 per snapshot"},
@@ -376,23 +439,48 @@ def env_measurement(pipe, torch, g, train_steps):
     cm = synth.descriptor_mixing("identity")
     model = g.EnvModel(synth.init_env_mlp(11, -1.0), cm, np.zeros(3))
     v = g.compute_descriptors(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model.cmix)
-    g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    H = g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_h = e0.elapsed_time(e1)
+
+    def time_h(variant):
+        g.env_set_variant(variant)
+        try:
+            g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
+            torch.cuda.synchronize()
+            e0.record()
+            H = g.build_hamiltonian_env(pipe.pos, pipe.spc, s.box, s.pbc, pipe.teacher.rcut, nb, model, v=v)
+            e1.record()
+            torch.cuda.synchronize()
+        finally:
+            g.env_set_variant(0)
+        return e0.elapsed_time(e1), H
+
+    ms_fp32, H32 = time_h(1)
+    ms_h, H = time_h(0)
     nnz = int(nb.cnt.sum().item())
-    # FMAs per bond: 8x32 + 32x8 (environment) + 8x32 + 32x32 + 32x2 (hopping); per atom 8x32 + 32
+    real = H32.val.abs().max().item()
+    dev = (H.val - H32.val).abs().max().item()
+    rel_l2 = ((H.val - H32.val).double().norm() / H32.val.double().norm()).item()
+    del H32
+    # network FMAs per bond: 8x32 + 32x8 (environment) + 8x32 + 32x32 + 32x2 (hopping); per atom 8x32 + 32
     flops = 2 * (nnz * 1856 + s.n * 288)
-    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
+    # issued on the tensor cores per bond: K x N = 16x32 + 32x16 + 16x32 + 32x32 (padded operands)
+    tc_flops = 2 * nnz * 2560
+    bf16_peak = measured_peak("bf16_tflops", 1900.0)
+    # the SiLU epilogue: 96 hardware tanh per bond on the MUFU pipe
+    peak_xu = 152 * 16 * 2.07e9
+    xu_ops = 96 * nnz
     h_out = {"atoms": s.n, "bonds": nnz, "ms": ms_h, "bonds_per_s": nnz / (ms_h * 1e-3),
-             "roofline": {"bound": "alu", "kernel": "env_forward_kernel (from positions)",
-                          "achieved": flops / (ms_h * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
-                          "frac": flops / (ms_h * 1e-3) / 1e12 / peak_alu,
-                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
+             "kernel": "env_hopping_tc_kernel (tcgen05, BF16 operands, FP32 accumulation) + env_onsite_kernel",
+             "fp32_pipes_ms": ms_fp32,
+             "vs_fp32_pipes": {"max_abs_diff": dev, "max_abs_t": real, "rel_l2": rel_l2},
+             "roofline": {"bound": "alu", "unit": "Gop/s", "achieved": xu_ops / (ms_h * 1e-3) / 1e9,
+                          "peak": peak_xu / 1e9, "frac": xu_ops / (ms_h * 1e-3) / peak_xu,
+                          "peak_source": "derived: 152 SMs x 16 MUFU lanes x 2.07 GHz (96 tanh per bond)",
+                          "network_tflops": flops / (ms_h * 1e-3) / 1e12,
+                          "tensor": {"achieved": tc_flops / (ms_h * 1e-3) / 1e12, "peak": bf16_peak,
+                                     "unit": "TFLOP/s", "frac": tc_flops / (ms_h * 1e-3) / 1e12 / bf16_peak,
+                                     "peak_source": "measured (bf16 burst)",
+                                     "note": "MMA flops of the padded operands"}}}
     del H, v
     cells = synth.band_training_cells(64, 5000)
     kpts = synth.band_kgrid(cells[0].box, 4, 4)
@@ -716,6 +804,7 @@ def run_ours(args):
     used_shape = g.kpm_get_shape(n_atoms, R, torch.float32, pipe.doubling)
     used_desc = g.kpm_shape_info(R, torch.float32, used_shape)
     launch_bytes = step_bytes(nnz, n_atoms, R, 4, 8, H.diag is not None, pipe.doubling, used_desc)
+    sell_bytes = step_bytes(nnz, n_atoms, R, 4, 8, H.diag is not None, pipe.doubling, {"pipelined": 0})
     launches_per_kpm = (M - 1) // 2 + 1 if pipe.doubling else M - 1
     launch_ms = sum(pipe.kpm_ms) / (len(pipe.kpm_ms) * launches_per_kpm)
     achieved = launch_bytes / (launch_ms * 1e-3) / 1e9
@@ -742,7 +831,10 @@ def run_ours(args):
                      "kernel": "cheb_step (fused Chebyshev step + moment dots), shape %d" % used_shape,
                      "shape": used_desc,
                      "bytes_per_launch": launch_bytes, "launch_ms": launch_ms, "peak_source": peak_src,
-                     "kpm_share_of_step": kpm_frac_of_step},
+                     "kpm_share_of_step": kpm_frac_of_step,
+                     "sell_equivalent_frac": sell_bytes / (launch_ms * 1e-3) / 1e9 / peak,
+                     "note": "frac counts the bytes of the format the chosen shape reads; "
+                             "sell_equivalent_frac the 4-byte-column SELL bytes of the same step"},
         "gpu_launches": launches,
         "clocks": clocks,
         "autotune": autotune,
@@ -840,7 +932,9 @@ def run_reference(args):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 7
+#define GPUTB_ABI_VERSION 8
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -664,13 +664,26 @@ TB_API tb_status tb_env_forward(int64_t n, const int64_t *slice_ptr, const int32
 
 /* The same H computed straight from positions (inference at any size: no
  * stored bond inputs).  diag may be NULL; col may be NULL when no row has
- * a neighbour. */
+ * a neighbour.  By default (tb_env_set_variant 0) the hopping network runs
+ * on the 5th-generation tensor cores: every layer input (u, h1, e, h2) and
+ * every weight is rounded to BF16, sums accumulate in FP32, the last layer
+ * (32 -> 2) is FP32, and SiLU uses the hardware tanh approximation
+ * (silu(z) = h + h tanh h, h = z/2; h1 and h2 in BF16x2 arithmetic); the
+ * onsite network stays FP32.
+ *   workspace  device, >= 256 bytes, 256-byte aligned (a status word)
+ * Variant 0 synchronises `stream` (TB_ERR_TIMEOUT when a tensor-core
+ * completion wait gave up); variant 1 does not. */
 TB_API tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,
                                           const double *box, const int32_t *pbc, double rcut,
                                           const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
                                           const float *cmix, const float *v, const float *params,
                                           const float *eps0, int32_t precision, void *val, void *diag,
-                                          void *stream);
+                                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Kernel of tb_build_hamiltonian_env: 0 = tensor cores (tcgen05, BF16
+ * operands; default), 1 = the FP32 pipes (the arithmetic of tb_env_forward,
+ * bit for bit).  Process-wide. */
+TB_API tb_status tb_env_set_variant(int32_t variant);
 
 /* Workspace bytes of tb_env_backward. */
 TB_API size_t tb_env_backward_workspace_size(int64_t n, int64_t total_elements);

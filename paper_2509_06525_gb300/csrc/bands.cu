@@ -19,10 +19,14 @@
 // reduced in a fixed order (reproducible).
 #include <cmath>
 #include <cstddef>
+#include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "descriptor.cuh"
 #include "geometry.cuh"
+#include "tcgen05.cuh"
 
 namespace gputb {
 namespace {
@@ -203,6 +207,279 @@ __global__ void __launch_bounds__(128) env_forward_kernel(
       const int z = min(max(species[i], 0), 2);
       diag[i] = (valT)(eps0[z] + onsite_forward(P, vi, z));
     }
+  }
+}
+
+// ------------------------------------------------------------------ tensor cores
+//
+// The hopping network of inference (H straight from positions) on the
+// 5th-generation tensor cores: BF16 operands, FP32 accumulation in TMEM.  A
+// CTA of 4 warps owns tiles of 128 SELL slots (4 slot columns of 32 rows =
+// the 128 TMEM lanes); thread t builds the inputs of slot t and owns row t
+// of every accumulator.  Per tile (biases of the 8-wide inputs ride on a
+// constant-1 column of the K = 16 operand):
+//   [u, 1, 0]  (128 x 16) . [We1 | be1]^T           -> D1 (32 columns)
+//   h1 = silu(D1)  (128 x 32) . We2^T (8 rows + 8 zero rows) -> D2 (16 columns)
+//   e = C (D2[:, :8] + be2);  [e, 1, 0] . [Wh1 | bh1]^T     -> D3 (32 columns)
+//   h2 = silu(D3)  (128 x 32) . Wh2^T                 -> D4 (32 columns)
+//   h3 = silu(D4 + bh2)  (128 x 32) . Wh3^T (2 rows + 14 zero rows) -> D5 (16 columns)
+//   y = D5[:, :2] + bh3;  t = y0 n_z^2 + y1 (1 - n_z^2)  (FP32)
+// SiLU here is h + h tanh(h) with h = z/2 (the hardware tanh approximation);
+// the weights of the layers followed by SiLU are stored times 1/2, so the
+// accumulators hold h directly; h1, h2 and h3 are formed in BF16x2
+// arithmetic (they are BF16 operands of the next MMA anyway).
+// One thread issues each layer's MMAs and commits them to an mbarrier that
+// every thread waits on (bounded; on timeout flags[0] |= 2, the CTA drains
+// its MMAs, frees its TMEM and stops).  D3 and D5 reuse D1's columns and D4
+// D2's once their loads have completed, so a CTA holds 64 TMEM columns; the
+// shared-memory request keeps at most 7 CTAs (448 columns) on an SM.  The
+// onsite network (one per row) stays on the FP32 pipes (env_onsite_kernel).
+using bf16 = __nv_bfloat16;
+
+struct EnvTcSmem {
+  bf16 w1[32 * 16];   // [We1 | be1 | 0]
+  bf16 w2[16 * 32];   // We2, rows 8..15 zero
+  bf16 w3[32 * 16];   // [Wh1 | bh1 | 0]
+  bf16 w4[32 * 32];   // Wh2
+  bf16 w5[16 * 32];   // Wh3, rows 2..15 zero
+  bf16 a16[128 * 16];  // layer 1 and layer 3 inputs
+  bf16 a32[128 * 32];  // layer 2, 4 and 5 inputs
+  float be2[8], bh2[32], bh3[2];   // bh2 holds bh2 / 2
+  float sc[9 * 64];
+  uint64_t bar;
+  uint32_t tmem;
+};
+constexpr int kEnvTcCols = 64;
+constexpr int kEnvTcCtasPerSm = 6;   // 6 x 64 of the 512 TMEM columns
+constexpr size_t kEnvTcSmemBytes = 30 * 1024;   // >= sizeof + alignment; at most 7 CTAs per SM
+static_assert(sizeof(EnvTcSmem) + 128 <= kEnvTcSmemBytes, "env tensor-core shared memory");
+constexpr long long kEnvTcPolls = 1ll << 22;
+
+
+__device__ __forceinline__ uint32_t pack2_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  return u;
+}
+
+// eight values of row r at columns k0 .. k0 + 7 of a K-major core-matrix tile
+__device__ __forceinline__ void env_store8(bf16 *tile, int r, int k0, int kdim, const float (&x)[8]) {
+  const uint4 u = make_uint4(pack2_bf16(x[0], x[1]), pack2_bf16(x[2], x[3]), pack2_bf16(x[4], x[5]),
+                             pack2_bf16(x[6], x[7]));
+  *reinterpret_cast<uint4 *>(tile + tc::core_index(r, k0, kdim)) = u;
+}
+
+// columns 8..15 of a K = 16 row: the constant 1 (bias) and zeros
+__device__ __forceinline__ void env_store_one(bf16 *tile, int r) {
+  const uint4 u = make_uint4(pack2_bf16(1.0f, 0.0f), 0u, 0u, 0u);
+  *reinterpret_cast<uint4 *>(tile + tc::core_index(r, 8, 16)) = u;
+}
+
+__device__ __forceinline__ void env_operands_ready() {
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+__device__ __forceinline__ bool env_layer_wait(EnvTcSmem &S, uint32_t &phase, int *flags) {
+  const bool ok = __syncthreads_and(tc::mbar_wait(&S.bar, phase, kEnvTcPolls)) != 0;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(flags, 2);
+    tc::mbar_wait(&S.bar, phase, kEnvTcPolls);   // drain the MMAs in flight before TMEM is freed
+  }
+  phase ^= 1u;
+  tc::fence_after_sync();
+  return ok;
+}
+
+// SiLU of two pre-activations given as h = z/2 (the layer's weights carry
+// the factor 1/2, exactly), as a packed BF16 pair: h + h tanh h in BF16x2
+// arithmetic (one rounding of h, the hardware tanh, one fused rounding)
+__device__ __forceinline__ uint32_t silu2_half_bf16(float h0, float h1) {
+  const uint32_t h = pack2_bf16(h0, h1);
+  uint32_t t, y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(y) : "r"(h), "r"(t));
+  return y;
+}
+
+// the 32 accumulator columns (h = z/2) at taddr of this thread's lane,
+// plus a bias (already halved) when BIAS, through SiLU, as row r of the
+// K = 32 operand
+template <bool BIAS>
+__device__ __forceinline__ void env_silu_row32(uint32_t taddr, bf16 *a32, int r, const float *bias) {
+#pragma unroll
+  for (int c = 0; c < 32; c += 16) {
+    float d[16];
+    tc::ld16(taddr + (uint32_t)c, d);
+    if (BIAS) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) d[j] += bias[c + j];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint4 u = make_uint4(silu2_half_bf16(d[8 * h], d[8 * h + 1]), silu2_half_bf16(d[8 * h + 2], d[8 * h + 3]),
+                                 silu2_half_bf16(d[8 * h + 4], d[8 * h + 5]),
+                                 silu2_half_bf16(d[8 * h + 6], d[8 * h + 7]));
+      *reinterpret_cast<uint4 *>(a32 + tc::core_index(r, c + 8 * h, 32)) = u;
+    }
+  }
+}
+
+// val of every real SELL element from positions (tensor cores; see above)
+template <typename valT>
+__global__ void __launch_bounds__(128, kEnvTcCtasPerSm) env_hopping_tc_kernel(
+    int64_t n, int64_t n_slices, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ cnt,
+    const double *__restrict__ pos, const int32_t *__restrict__ species, Box B, float rcut,
+    const int32_t *__restrict__ col, const float *__restrict__ cmix, const float *__restrict__ v,
+    const float *__restrict__ params, valT *__restrict__ val, int *__restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char env_raw[];
+  EnvTcSmem &S = *reinterpret_cast<EnvTcSmem *>(env_raw + ((128 - (tc::smem_addr(env_raw) & 127)) & 127));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // layers followed by SiLU carry the factor 1/2 (exact in BF16): their
+  // accumulators hold h = z/2
+  for (int q = tid; q < 32 * 16; q += 128) {
+    const int o = q >> 4, k = q & 15;
+    const float w1 = k < 8 ? params[oWe1 + o * 8 + k] : (k == 8 ? params[obe1 + o] : 0.0f);
+    const float w3 = k < 8 ? params[oWh1 + o * 8 + k] : (k == 8 ? params[obh1 + o] : 0.0f);
+    S.w1[tc::core_index(o, k, 16)] = __float2bfloat16_rn(0.5f * w1);
+    S.w3[tc::core_index(o, k, 16)] = __float2bfloat16_rn(0.5f * w3);
+  }
+  for (int q = tid; q < 16 * 32; q += 128) {
+    const int o = q >> 5, k = q & 31;
+    S.w2[tc::core_index(o, k, 32)] = __float2bfloat16_rn(o < 8 ? params[oWe2 + o * 32 + k] : 0.0f);
+  }
+  for (int q = tid; q < 32 * 32; q += 128)
+    S.w4[tc::core_index(q >> 5, q & 31, 32)] = __float2bfloat16_rn(0.5f * params[oWh2 + q]);
+  for (int q = tid; q < 16 * 32; q += 128) {
+    const int o = q >> 5, k = q & 31;
+    S.w5[tc::core_index(o, k, 32)] = __float2bfloat16_rn(o < 2 ? params[oWh3 + o * 32 + k] : 0.0f);
+  }
+  if (tid < 8) S.be2[tid] = params[obe2 + tid];
+  if (tid < 32) S.bh2[tid] = 0.5f * params[obh2 + tid];
+  if (tid < 2) S.bh3[tid] = params[obh3 + tid];
+  load_mixing(S.sc, cmix);
+  env_store_one(S.a16, tid);   // columns 8..15 of this thread's K = 16 row, for every tile
+  if (tid == 0) tc::mbar_init(&S.bar, 1);
+  if (warp == 0) tc::alloc(&S.tmem, kEnvTcCols);
+  env_operands_ready();
+  const uint32_t tmem = S.tmem;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+  const uint32_t id32 = tc::idesc_bf16(128, 32), id16 = tc::idesc_bf16(128, 16);
+
+  // tiles of 4 slot groups (32 slots of one slice each), contiguous per CTA
+  const int64_t slots = slice_ptr[n_slices];
+  const int64_t tiles = ((slots >> 5) + 3) >> 2;
+  const int64_t t0 = tiles * blockIdx.x / gridDim.x, t1 = tiles * (blockIdx.x + 1) / gridDim.x;
+  // this warp's slice: the last slice starting at or before its first slot
+  int64_t k = 0;
+  {
+    const int64_t e0 = (4 * t0 + warp) * 32;
+    int64_t hi = n_slices;
+    while (hi - k > 1) {
+      const int64_t mid = (k + hi) >> 1;
+      if (slice_ptr[mid] <= e0) k = mid;
+      else hi = mid;
+    }
+  }
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t t = t0; t < t1 && ok; ++t) {
+    const int64_t e0 = (4 * t + warp) * 32;
+    while (k + 1 < n_slices && slice_ptr[k + 1] <= e0) ++k;
+    const int64_t e = e0 + lane;
+    const int64_t i = k * 32 + lane;
+    const int slot = static_cast<int>((e0 - slice_ptr[k]) >> 5);
+    const bool valid = e0 < slots && i < n && slot < cnt[i];
+    float C[8], nz2 = 0.0f;
+    {
+      float u[8];
+      if (valid) {
+        float3 d;
+        bond_inputs(pos, species, B, rcut, S.sc, v, i, col[e], C, u, nz2, d);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) C[j] = u[j] = 0.0f;
+      }
+      env_store8(S.a16, tid, 0, 16, u);
+    }
+    env_operands_ready();
+    if (tid == 0) {
+      tc::mma_bf16(tmem, tc::desc_kmajor(S.a16, 16), tc::desc_kmajor(S.w1, 16), id32, false);
+      tc::commit(&S.bar);
+    }
+    if (!(ok = env_layer_wait(S, phase, flags))) break;
+    env_silu_row32<false>(tl, S.a32, tid, nullptr);   // h1
+    env_operands_ready();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+        tc::mma_bf16(tmem + 32, tc::desc_kmajor(S.a32 + ks * 128, 32), tc::desc_kmajor(S.w2 + ks * 128, 32), id16,
+                     ks > 0);
+      tc::commit(&S.bar);
+    }
+    if (!(ok = env_layer_wait(S, phase, flags))) break;
+    {
+      float d[16], x[8];
+      tc::ld16(tl + 32u, d);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = C[j] * (d[j] + S.be2[j]);
+      env_store8(S.a16, tid, 0, 16, x);   // columns 8..15 still hold [1, 0]
+    }
+    env_operands_ready();
+    if (tid == 0) {
+      tc::mma_bf16(tmem, tc::desc_kmajor(S.a16, 16), tc::desc_kmajor(S.w3, 16), id32, false);
+      tc::commit(&S.bar);
+    }
+    if (!(ok = env_layer_wait(S, phase, flags))) break;
+    env_silu_row32<false>(tl, S.a32, tid, nullptr);   // h2
+    env_operands_ready();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+        tc::mma_bf16(tmem + 32, tc::desc_kmajor(S.a32 + ks * 128, 32), tc::desc_kmajor(S.w4 + ks * 128, 32), id32,
+                     ks > 0);
+      tc::commit(&S.bar);
+    }
+    if (!(ok = env_layer_wait(S, phase, flags))) break;
+    env_silu_row32<true>(tl + 32u, S.a32, tid, S.bh2);   // h3
+    env_operands_ready();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+        tc::mma_bf16(tmem, tc::desc_kmajor(S.a32 + ks * 128, 32), tc::desc_kmajor(S.w5 + ks * 128, 32), id16,
+                     ks > 0);
+      tc::commit(&S.bar);
+    }
+    if (!(ok = env_layer_wait(S, phase, flags))) break;
+    float y[2];
+    tc::ld2(tl, y);
+    y[0] += S.bh3[0];
+    y[1] += S.bh3[1];
+    if (valid) val[e] = (valT)(y[0] * nz2 + y[1] * (1.0f - nz2));
+    tc::fence_before_sync();   // D5 read before the next tile's layer 1 overwrites it
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, kEnvTcCols);
+}
+
+// diag[i] = eps0[Z_i] + MLP_alpha(v_i)[Z_i], one thread per row (FP32)
+template <typename valT>
+__global__ void __launch_bounds__(128) env_onsite_kernel(int64_t n, const float *__restrict__ v,
+                                                         const int32_t *__restrict__ species,
+                                                         const float *__restrict__ params,
+                                                         const float *__restrict__ eps0, valT *__restrict__ diag) {
+  __shared__ __align__(16) float P[kNPs];
+  stage_params(P, params);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float vi[8];
+    load8(v + i * 8, vi);
+    const int z = min(max(species[i], 0), 2);
+    diag[i] = (valT)(eps0[z] + onsite_forward(P, vi, z));
   }
 }
 
@@ -988,26 +1265,82 @@ extern "C" tb_status tb_env_forward(int64_t n, const int64_t *slice_ptr, const i
                                            params, eps0, val, diag, st);
 }
 
+namespace {
+// kernel of tb_build_hamiltonian_env: 0 = tensor cores (default), 1 = FP32 pipes
+int g_env_variant = 0;
+
+template <typename valT>
+tb_status launch_env_tc(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, const double *pos,
+                        const int32_t *species, const Box &B, float rcut, const int32_t *col, const float *cmix,
+                        const float *v, const float *params, const float *eps0, void *val, void *diag, int *flags,
+                        cudaStream_t st) {
+  const int64_t n_slices = (n + 31) / 32;
+  // the whole unified L1/shared array as shared memory: room for 7 CTAs of 30 KB
+  TB_CUDA(cudaFuncSetAttribute(env_hopping_tc_kernel<valT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kEnvTcSmemBytes));
+  TB_CUDA(cudaFuncSetAttribute(env_hopping_tc_kernel<valT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
+  // persistent: 6 CTAs per SM (the register budget of the launch bounds; the
+  // occupancy query reports 1 for this kernel), each taking a contiguous
+  // range of 128-slot tiles (empty for the CTAs beyond the tile count)
+  const unsigned grid = (unsigned)(sm_count() * kEnvTcCtasPerSm);
+  env_hopping_tc_kernel<valT><<<grid, 128, kEnvTcSmemBytes, st>>>(n, n_slices, slice_ptr, cnt, pos, species, B, rcut,
+                                                                   col, cmix, v, params, static_cast<valT *>(val),
+                                                                   flags);
+  TB_CHECK_LAUNCH();
+  if (diag) {
+    const int64_t want = (n + 127) / 128, cap = (int64_t)sm_count() * 8;
+    env_onsite_kernel<valT><<<(unsigned)(want < cap ? want : cap), 128, 0, st>>>(n, v, species, params, eps0,
+                                                                                static_cast<valT *>(diag));
+    TB_CHECK_LAUNCH();
+  }
+  return TB_OK;
+}
+}  // namespace
+
 extern "C" tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,
                                               const double *box, const int32_t *pbc, double rcut,
                                               const int64_t *slice_ptr, const int32_t *col, const int32_t *cnt,
                                               const float *cmix, const float *v, const float *params,
                                               const float *eps0, int32_t precision, void *val, void *diag,
-                                              void *stream) {
+                                              void *workspace, size_t workspace_bytes, void *stream) {
   tb_status s = check_sell(n, slice_ptr, cnt);
   if (s != TB_OK) return s;
   TB_REQUIRE(positions && species && cmix && v && params && eps0 && val,
              "tb_build_hamiltonian_env: null pointer");
   TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian_env: bad precision");
+  TB_REQUIRE(workspace && workspace_bytes >= 256 && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0,
+             "tb_build_hamiltonian_env: workspace must be >= 256 bytes, 256-byte aligned");
   Box B;
   s = make_box(box, pbc, rcut, &B);
   if (s != TB_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (precision == TB_F32)
-    return launch_env_forward<float, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col, cmix,
-                                           v, params, eps0, val, diag, st);
-  return launch_env_forward<double, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col, cmix,
-                                          v, params, eps0, val, diag, st);
+  if (g_env_variant == 1) {
+    if (precision == TB_F32)
+      return launch_env_forward<float, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col,
+                                             cmix, v, params, eps0, val, diag, st);
+    return launch_env_forward<double, true>(n, slice_ptr, cnt, nullptr, positions, species, B, (float)rcut, col,
+                                            cmix, v, params, eps0, val, diag, st);
+  }
+  if (n == 0) return TB_OK;
+  int *flags = static_cast<int *>(workspace);
+  TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
+  s = precision == TB_F32 ? launch_env_tc<float>(n, slice_ptr, cnt, positions, species, B, (float)rcut, col, cmix, v,
+                                                 params, eps0, val, diag, flags, st)
+                          : launch_env_tc<double>(n, slice_ptr, cnt, positions, species, B, (float)rcut, col, cmix,
+                                                  v, params, eps0, val, diag, flags, st);
+  if (s != TB_OK) return s;
+  int h = 0;
+  TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TB_CUDA(cudaStreamSynchronize(st));
+  if (h & 2) return fail(TB_ERR_TIMEOUT, "tb_build_hamiltonian_env: a tensor-core completion wait timed out");
+  return TB_OK;
+}
+
+extern "C" tb_status tb_env_set_variant(int32_t variant) {
+  TB_REQUIRE(variant == 0 || variant == 1, "tb_env_set_variant: variant must be 0 (tcgen05) or 1 (FP32 pipes)");
+  g_env_variant = variant;
+  return TB_OK;
 }
 
 extern "C" size_t tb_env_backward_workspace_size(int64_t n, int64_t total_elements) {

@@ -595,13 +595,15 @@ extern "C" tb_status kpm_moments_batched_autotune(int32_t n_snap, const int64_t 
   if (status == TB_OK) status = enqueue_fold(L, n_snap, slice_ptr, col, val, diag, precision, a, b, F, st);
   if (status != TB_OK) return status;
   int best = 0;
+  // the segmented step, as the batch graph runs it
+  const BatchDesc bd{F.tile, F.row0, F.rows, n_snap};
   const bool ok = precision == TB_F32
                       ? KpmEntry<float>::autotune(R, &status, L.n_pad, F.sp, F.col, F.val, F.diag, 1.0, 0.0, (int)mode,
                                                   (int)reps, F.run_ws, F.run_bytes, st, &best, ms_per_step,
-                                                  ms_capacity)
+                                                  ms_capacity, &bd)
                       : KpmEntry<double>::autotune(R, &status, L.n_pad, F.sp, F.col, F.val, F.diag, 1.0, 0.0,
                                                    (int)mode, (int)reps, F.run_ws, F.run_bytes, st, &best,
-                                                   ms_per_step, ms_capacity);
+                                                   ms_per_step, ms_capacity, &bd);
   if (!ok) return fail(TB_ERR_INVALID_ARG, "kpm_moments_batched_autotune: unsupported R=%d", R);
   if (status != TB_OK) return status;
   *best_shape = best;

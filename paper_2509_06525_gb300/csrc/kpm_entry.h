@@ -43,10 +43,12 @@ struct KpmEntry {
                               const BatchDesc &bt, double *mu, void *ws, size_t ws_bytes, cudaStream_t st,
                               int **flags);
   // time `reps` Chebyshev steps of every candidate shape on this matrix;
-  // ms[shape] receives the mean time per step, *best the fastest shape
+  // ms[shape] receives the mean time per step, *best the fastest shape.
+  // bt != nullptr: the segmented step of that block-diagonal batch
   static bool autotune(int R, tb_status *status, int64_t n, const int64_t *slice_ptr, const int32_t *col,
                        const void *val, const void *diag, double a, double b, int mode, int reps, void *ws,
-                       size_t ws_bytes, cudaStream_t st, int *best, float *ms, int ms_capacity);
+                       size_t ws_bytes, cudaStream_t st, int *best, float *ms, int ms_capacity,
+                       const BatchDesc *bt = nullptr);
 };
 
 }  // namespace kpmdev

@@ -327,36 +327,40 @@ struct KpmRunner {
   // Autotuner: v0 from the random phases, v1 = H~ v0 with the default shape,
   // then for every candidate shape two warm-up steps and `reps` timed steps of
   // the recursion (the same kernels, operands and in-place update as a
-  // kpm_moments call; CUDA events on `st`).
+  // kpm_moments call; CUDA events on `st`).  SEG: the segmented step of a
+  // block-diagonal batch (tables bt), as kpm_moments_batched runs it.
+  template <bool SEG>
   static tb_status autotune(int64_t n, const int64_t *slice_ptr, const int32_t *col, const valT *val,
                             const valT *diag, double a, double b, int mode, int reps, void *ws, size_t ws_bytes,
-                            cudaStream_t st, int *best, float *ms_out, int ms_capacity) {
+                            cudaStream_t st, int *best, float *ms_out, int ms_capacity, const BatchTables &bt) {
     const bool dbl = mode == TB_KPM_DOUBLING;
     const int64_t np = padded_rows(n);
-    const int gmax = Kit::max_grid(n);
+    // partial slots per moment: one per CTA, or (segmented) one per row block
+    auto units = [&](int shape) -> int64_t {
+      return SEG ? (n + Kit::rows_per_block(shape) - 1) / Kit::rows_per_block(shape) : (int64_t)Kit::max_grid(n);
+    };
+    const int64_t umax = SEG ? (n + Kit::min_rows_per_block() - 1) / Kit::min_rows_per_block() : units(0);
     Carver cv(ws, ws_bytes);
     real *v0 = cv.take<real>((size_t)np * R * 2);
     real *A = cv.take<real>((size_t)np * R * 2);
     real *B = cv.take<real>((size_t)np * R * 2);
-    double *partial = cv.take<double>((size_t)3 * gmax * R);
+    double *partial = cv.take<double>((size_t)3 * umax * R);
     int *flags = cv.take<int>(4);
     PlanWs pw;
     carve_plan(cv, n, &pw);
     if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_kpm_autotune: workspace too small (%zu < %zu)", ws_bytes, cv.used);
-    const int64_t ps = (int64_t)gmax * R;
     const real shift = static_cast<real>(b);
     const real inv_a = static_cast<real>(1.0 / a), two_over_a = static_cast<real>(2.0 / a);
-    BatchTables none;
     TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
-    tb_status s = random_phases(0, Kit::grid(0, n, dbl), n, 42, 0, none, false, v0, partial, st);
+    tb_status s = random_phases(0, Kit::grid(0, n, dbl), n, 42, 0, bt, SEG, v0, partial, st);
     if (s != TB_OK) return s;
     for (int shape = 0; shape < Kit::kShapes; ++shape) {
       s = check_alignment(shape, col, val, diag, "tb_kpm_autotune");
       if (s != TB_OK) return s;
     }
     Kit::prepare(0);
-    s = Kit::template step<true, false, false>(0, Kit::grid(0, n, false), n, slice_ptr, col, val, diag, v0, nullptr,
-                                              v0, A, partial, inv_a, shift, flags, ps, none, st);
+    s = Kit::template step<true, false, SEG>(0, Kit::grid(0, n, false), n, slice_ptr, col, val, diag, v0, nullptr,
+                                             v0, A, partial, inv_a, shift, flags, units(0) * R, bt, st);
     if (s != TB_OK) return s;
     TB_CUDA(cudaMemcpyAsync(B, v0, (size_t)np * R * 2 * sizeof(real), cudaMemcpyDeviceToDevice, st));
     cudaEvent_t ev[2];
@@ -370,15 +374,15 @@ struct KpmRunner {
       BandPlan bp;
       s = make_plan(shape, n, slice_ptr, col, pw, st, &bp);
       if (s != TB_OK) break;
+      const int64_t ps = units(shape) * R;
       auto one = [&](int k) {
         // the recursion's in-place update: out = 2 H~ x - out
         real *out = (k & 1) ? A : B;
         const real *x = (k & 1) ? B : A;
-        return dbl ? Kit::template step<false, true, false>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
-                                                            out, partial, two_over_a, shift, flags, ps, none, st, bp)
-                   : Kit::template step<false, false, false>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
-                                                             out, partial, two_over_a, shift, flags, ps, none, st,
-                                                             bp);
+        return dbl ? Kit::template step<false, true, SEG>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
+                                                          out, partial, two_over_a, shift, flags, ps, bt, st, bp)
+                   : Kit::template step<false, false, SEG>(shape, grid, n, slice_ptr, col, val, diag, x, out, v0,
+                                                           out, partial, two_over_a, shift, flags, ps, bt, st, bp);
       };
       for (int k = 0; k < 2 && s == TB_OK; ++k) s = one(k);
       if (s != TB_OK) break;
@@ -505,10 +509,22 @@ template <typename real, typename valT, int R>
 struct TuneOp {
   static void apply(tb_status *status, int64_t n, const int64_t *sp, const int32_t *col, const void *val,
                     const void *diag, double a, double b, int mode, int reps, void *ws, size_t wsb, cudaStream_t st,
-                    int *best, float *ms, int cap) {
-    *status = KpmRunner<real, valT, R>::autotune(n, sp, col, static_cast<const valT *>(val),
-                                                 static_cast<const valT *>(diag), a, b, mode, reps, ws, wsb, st, best,
-                                                 ms, cap);
+                    int *best, float *ms, int cap, const BatchDesc *bd) {
+    using Run = KpmRunner<real, valT, R>;
+    if (bd) {
+      BatchTables bt;
+      bt.tile_snap = bd->tile_snap;
+      bt.row0 = bd->row0;
+      bt.rows = bd->rows;
+      bt.n_snap = bd->n_snap;
+      *status = Run::template autotune<true>(n, sp, col, static_cast<const valT *>(val),
+                                             static_cast<const valT *>(diag), a, b, mode, reps, ws, wsb, st, best, ms,
+                                             cap, bt);
+    } else {
+      *status = Run::template autotune<false>(n, sp, col, static_cast<const valT *>(val),
+                                              static_cast<const valT *>(diag), a, b, mode, reps, ws, wsb, st, best,
+                                              ms, cap, BatchTables());
+    }
   }
 };
 
@@ -561,9 +577,9 @@ struct TuneOp {
   bool KpmEntry<REAL>::autotune(int R, tb_status *status, int64_t n, const int64_t *slice_ptr, const int32_t *col, \
                                 const void *val, const void *diag, double a, double b, int mode, int reps,         \
                                 void *ws, size_t ws_bytes, cudaStream_t st, int *best, float *ms,                  \
-                                int ms_capacity) {                                                                 \
+                                int ms_capacity, const BatchDesc *bt) {                                            \
     return KpmDispatch<REAL, REAL>::call<TuneOp>(R, status, n, slice_ptr, col, val, diag, a, b, mode, reps, ws,   \
-                                                 ws_bytes, st, best, ms, ms_capacity);                             \
+                                                 ws_bytes, st, best, ms, ms_capacity, bt);                         \
   }                                                                                                                \
   }                                                                                                                \
   }

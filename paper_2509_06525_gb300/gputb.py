@@ -104,7 +104,8 @@ SIGNATURES = {
     "tb_env_forward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp,
                                 _c_vp]),
     "tb_build_hamiltonian_env": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp,
-                                          _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp]),
+                                          _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
+    "tb_env_set_variant": (_c_i32, [_c_i32]),
     "tb_env_backward_workspace_size": (_c_sz, [_c_i64, _c_i64]),
     "tb_env_backward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
                                  _c_vp, _c_sz, _c_vp]),
@@ -130,7 +131,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 7   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 8   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -887,11 +888,18 @@ def build_hamiltonian_env(positions, species, box, pbc, rcut, nb: Neighbors, mod
     b, p, bptr, pptr = _host_box(box, pbc)
     val = torch.zeros(max(nb.total, 1), dtype=dtype, device=positions.device)
     diag = torch.empty(nb.n, dtype=dtype, device=positions.device) if with_diag else None
+    ws = _workspace(256, positions.device)
     _check("tb_build_hamiltonian_env", lib().tb_build_hamiltonian_env(
         _ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr), _ptr(nb.col),
         _ptr(nb.cnt), _ptr(model.cmix), _ptr(v), _ptr(model.p), _ptr(model.eps0), precision_of(dtype), _ptr(val),
-        _ptr(diag), _stream(stream)))
+        _ptr(diag), _ptr(ws), ws.numel(), _stream(stream)))
     return SellMatrix(nb.n, nb.slice_ptr, nb.col, val[:nb.total], diag)
+
+
+def env_set_variant(variant: int):
+    """Kernel of build_hamiltonian_env: 0 = tensor cores (BF16 operands,
+    default), 1 = FP32 pipes (bit for bit the arithmetic of env_forward)."""
+    _check("tb_env_set_variant", lib().tb_env_set_variant(int(variant)))
 
 
 def env_backward(n, slice_ptr, cnt, total, feat, v, species, model: EnvModel, g_val, g_diag, grad=None,

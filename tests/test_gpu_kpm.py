@@ -38,14 +38,35 @@ def gputb():
     return g
 
 
-@pytest.fixture(params=range(10), ids=lambda k: f"shape{k}")
-def shape(request, gputb):
-    """Every compiled launch shape of the Chebyshev step (direct loads, or a
-    bulk-copy ring of 2-4 stages, with 1, 2 or 4 complex numbers per thread
-    and several register budgets); a test skips the indices its
-    (R, precision) does not have."""
-    yield request.param
-    gputb.kpm_clear_shapes()
+def _shape_count(R, dtype):
+    """Step shapes compiled for (R, precision), from the library's host-side
+    shape table (no GPU needed); 5, the longest table, when the library
+    cannot be loaded at collection time (then absent indices skip)."""
+    try:
+        from paper_2509_06525_gb300 import gputb as g
+        return g.kpm_shape_count(R, dtype)
+    except Exception:
+        return 5
+
+
+def _dname(dtype):
+    return "f64" if dtype == torch.float64 else "f32"
+
+
+def shape_cases(Rs, dtypes):
+    """(R, dtype, shape) for every compiled launch shape of the Chebyshev
+    step (direct loads, bulk-copy rings, banded steps; several complex
+    numbers per thread, stage counts and register budgets)."""
+    return [pytest.param(R, dt, k, id=f"R{R}-{_dname(dt)}-shape{k}")
+            for R in Rs for dt in dtypes for k in range(_shape_count(R, dt))]
+
+
+@pytest.fixture(autouse=True)
+def _clear_shapes():
+    yield
+    from paper_2509_06525_gb300 import gputb as g
+    if torch.cuda.is_available():
+        g.kpm_clear_shapes()
 
 
 def use_shape(g, shape, R, dtype):
@@ -72,6 +93,7 @@ def cfg800():
     return s, indptr, idx, t, eps, H, a, b, w
 
 
+@pytest.mark.parametrize("shape", range(_shape_count(8, torch.float64)), ids=lambda k: f"shape{k}")
 def test_fp64_moments_match_oracle(gputb, cfg800, shape, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
@@ -95,6 +117,7 @@ def test_doubling_odd_and_tiny_moment_counts(gputb, cfg800, M):
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
 
 
+@pytest.mark.parametrize("shape", range(_shape_count(8, torch.float32)), ids=lambda k: f"shape{k}")
 def test_fp32_moments_match_oracle(gputb, cfg800, shape, doubling):
     s, indptr, idx, t, eps, H, a, b, w = cfg800
     M, R = w["M"], w["R"]
@@ -127,8 +150,7 @@ def test_dos_matches_oracle(gputb, cfg800):
 
 
 
-@pytest.mark.parametrize("R", [1, 2, 4, 8, 16, 32])
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("R,dtype,shape", shape_cases([1, 2, 4, 8, 16, 32], [torch.float64, torch.float32]))
 def test_all_block_widths_ragged_rows(gputb, R, dtype, shape, doubling):
     """Ragged N (not a multiple of 32), an h-BN junction with onsite terms
     (diag present), every supported R, every Chebyshev-step shape."""
@@ -149,8 +171,8 @@ def test_all_block_widths_ragged_rows(gputb, R, dtype, shape, doubling):
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33, 300])
-@pytest.mark.parametrize("R", [2, 8])
-def test_tiny_systems(gputb, n, R, shape):
+@pytest.mark.parametrize("R,dtype,shape", shape_cases([2, 8], [torch.float64]))
+def test_tiny_systems(gputb, n, R, dtype, shape):
     use_shape(gputb, shape, R, torch.float64)
     rng = np.random.default_rng(n)
     dense = np.zeros((n, n))
@@ -178,10 +200,12 @@ def test_bounds_violation_reported(gputb, cfg800):
     assert ei.value.status in (gputb.TB_ERR_BOUNDS, gputb.TB_ERR_NOT_FINITE)
 
 
-def test_wide_rows_fall_back_inside_the_pipeline(gputb, shape):
+@pytest.mark.parametrize("R,dtype,shape", shape_cases([8], [torch.float64, torch.float32]))
+def test_wide_rows_fall_back_inside_the_pipeline(gputb, R, dtype, shape):
     """Rows wider than the pipeline's 16-slot tile budget (dense random
     pattern, 40 neighbours per row) take the direct-load path per tile."""
     import scipy.sparse as sp
+    use_shape(gputb, shape, R, dtype)
     rng = np.random.default_rng(3)
     n = 700
     A = sp.random(n, n, density=40 / n, random_state=rng, format="csr")
@@ -193,10 +217,10 @@ def test_wide_rows_fall_back_inside_the_pipeline(gputb, shape):
     onsite = rng.uniform(-0.3, 0.3, n)
     H = oha.csr_hamiltonian(n, A.indptr, A.indices, A.data, onsite)
     _, _, a, b = obo.spectral_bounds(H, 64, 7)
-    Hd = sell_matrix(A.indptr, A.indices, A.data, onsite, n, torch.float64)
-    mu = gputb.kpm_moments(Hd, a, b, 64, 8, 77).cpu().numpy()
-    _, mu_ref = okpm.kpm_moments(H, a, b, 64, 8, 77)
-    assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
+    Hd = sell_matrix(A.indptr, A.indices, A.data, onsite, n, dtype)
+    mu = gputb.kpm_moments(Hd, a, b, 64, R, 77).cpu().numpy()
+    _, mu_ref = okpm.kpm_moments(H, a, b, 64, R, 77)
+    assert np.max(np.abs(mu - mu_ref)) <= (TOL_F64 if dtype == torch.float64 else TOL_F32)
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
@@ -228,8 +252,8 @@ def test_bounded_wait_gives_up_and_leaves_the_context_usable(gputb, cfg800):
     assert np.max(np.abs(mu - mu_ref)) <= TOL_F64
 
 
-@pytest.mark.parametrize("R,dtype", [(1, torch.float32), (8, torch.float32), (16, torch.float32), (8, torch.float64)])
-def test_scattered_columns_take_the_gather_path(gputb, shape, R, dtype):
+@pytest.mark.parametrize("R,dtype,shape", shape_cases([1, 8, 16], [torch.float32]) + shape_cases([8], [torch.float64]))
+def test_scattered_columns_take_the_gather_path(gputb, R, dtype, shape):
     """A random symmetric pattern (about 10 neighbours per row, anywhere in
     the matrix): slices fit the banded step's 16 slots, but a tile's columns
     fall in far more than 6 bands, so the banded shapes take their
