@@ -263,9 +263,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// the same test, letting the thread sleep up to `ns` nanoseconds for the
+// phase (it wakes when the phase completes)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t kWaitSleepNs = 2000;
+// at most `polls` tests (each may sleep up to kWaitSleepNs): a few seconds
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long polls = kWaitPolls) {
-  for (long long k = 0; k < polls; ++k)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (polls > 0 && mbar_try_wait(bar, parity)) return true;
+  for (long long k = 1; k < polls; ++k)
+    if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
   return false;
 }
 

@@ -105,10 +105,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for the phase of the given parity; true when it completed
+// the same test, letting the thread sleep up to `ns` nanoseconds for the
+// phase (it wakes when the phase completes)
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of the given parity (at most `polls` tests, each
+// sleeping up to 1 us); true when it completed
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long polls) {
-  for (long long k = 0; k < polls; ++k)
-    if (mbar_test(bar, parity)) return true;
+  if (polls > 0 && mbar_test(bar, parity)) return true;
+  for (long long k = 1; k < polls; ++k)
+    if (mbar_test_sleep(bar, parity, 1000)) return true;
   return false;
 }
 
