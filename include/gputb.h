@@ -662,15 +662,22 @@ TB_API tb_status tb_env_forward(int64_t n, const int64_t *slice_ptr, const int32
                                 const float *eps0, int32_t precision, void *val, void *diag,
                                 void *stream);
 
+/* Workspace bytes of tb_build_hamiltonian_env (256 + 32 n: a status word
+ * and the positions as FP32 pairs). */
+TB_API size_t tb_build_hamiltonian_env_workspace_size(int64_t n);
+
 /* The same H computed straight from positions (inference at any size: no
  * stored bond inputs).  diag may be NULL; col may be NULL when no row has
  * a neighbour.  By default (tb_env_set_variant 0) the hopping network runs
  * on the 5th-generation tensor cores: every layer input (u, h1, e, h2) and
  * every weight is rounded to BF16, sums accumulate in FP32, the last layer
  * (32 -> 2) is FP32, and SiLU uses the hardware tanh approximation
- * (silu(z) = h + h tanh h, h = z/2; h1 and h2 in BF16x2 arithmetic); the
- * onsite network stays FP32.
- *   workspace  device, >= 256 bytes, 256-byte aligned (a status word)
+ * (silu(z) = h + h tanh h, h = z/2; h1 to h3 in BF16x2 arithmetic); bond
+ * vectors come from the positions split into FP32 pairs (hi + lo, exact
+ * differences by TwoSum); the onsite network stays FP32.
+ *   workspace  device, 256-byte aligned, at least
+ *              tb_build_hamiltonian_env_workspace_size(n) bytes
+ *              (TB_ERR_WORKSPACE otherwise)
  * Variant 0 synchronises `stream` (TB_ERR_TIMEOUT when a tensor-core
  * completion wait gave up); variant 1 does not. */
 TB_API tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,

@@ -328,12 +328,99 @@ __device__ __forceinline__ void env_silu_row32(uint32_t taddr, bf16 *a32, int r,
   }
 }
 
+// Positions as FP32 pairs (x = hi + lo to about 2^-48 relative), so that the
+// tensor-core kernel forms bond vectors on the FP32 pipes: GB300 issues FP64
+// at a small fraction of the FP32 rate.
+__global__ void pos_pair_kernel(const double *__restrict__ pos, int64_t n, float4 *__restrict__ hi,
+                                float4 *__restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  const float hx = (float)x, hy = (float)y, hz = (float)z;
+  hi[i] = make_float4(hx, hy, hz, 0.0f);
+  lo[i] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.0f);
+}
+
+// the box of `Box` with every lattice component as an FP32 pair
+struct BoxPair {
+  float2 ax, bx, by, cx, cy, cz;
+  float iax, iby, icz;
+  int p1, p2, p3;
+};
+
+BoxPair box_pair(const Box &B) {
+  auto split = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
+  BoxPair P;
+  P.ax = split(B.ax);
+  P.bx = split(B.bx);
+  P.by = split(B.by);
+  P.cx = split(B.cx);
+  P.cy = split(B.cy);
+  P.cz = split(B.cz);
+  P.iax = (float)B.iax;
+  P.iby = (float)B.iby;
+  P.icz = (float)B.icz;
+  P.p1 = B.p1;
+  P.p2 = B.p2;
+  P.p3 = B.p3;
+  return P;
+}
+
+// a + b as an unevaluated pair (s, e), s + e exact (Knuth's TwoSum)
+__device__ __forceinline__ float2 two_sum_f(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+
+// x = (h, l) minus k (Lh, Ll): the high parts through TwoSum, so that a
+// coordinate difference across a periodic seam loses nothing
+__device__ __forceinline__ float2 pair_shift(float2 x, float k, float2 L) {
+  const float2 t = two_sum_f(x.x, -k * L.x);
+  return make_float2(t.x, t.y + (x.y - k * L.y));
+}
+
+// r_j - r_i (minimum image, reduced along a3, a2, a1 as bond_vector_f32)
+// from FP32-pair positions; exact up to the final FP32 rounding, and
+// r_i - r_j is its exact negative (every step is sign-symmetric)
+__device__ __forceinline__ float3 bond_vector_pair(const BoxPair &B, const float4 *__restrict__ ph,
+                                                   const float4 *__restrict__ pl, int64_t i, int64_t j) {
+  const float4 hi = __ldg(ph + i), hj = __ldg(ph + j), li = __ldg(pl + i), lj = __ldg(pl + j);
+  float2 dx = two_sum_f(hj.x, -hi.x), dy = two_sum_f(hj.y, -hi.y), dz = two_sum_f(hj.z, -hi.z);
+  dx.y += lj.x - li.x;
+  dy.y += lj.y - li.y;
+  dz.y += lj.z - li.z;
+  if (B.p3) {
+    const float n3 = rintf((dz.x + dz.y) * B.icz);
+    if (n3 != 0.0f) {
+      dx = pair_shift(dx, n3, B.cx);
+      dy = pair_shift(dy, n3, B.cy);
+      dz = pair_shift(dz, n3, B.cz);
+    }
+  }
+  if (B.p2) {
+    const float n2 = rintf((dy.x + dy.y) * B.iby);
+    if (n2 != 0.0f) {
+      dx = pair_shift(dx, n2, B.bx);
+      dy = pair_shift(dy, n2, B.by);
+    }
+  }
+  if (B.p1) {
+    const float n1 = rintf((dx.x + dx.y) * B.iax);
+    if (n1 != 0.0f) dx = pair_shift(dx, n1, B.ax);
+  }
+  return make_float3(dx.x + dx.y, dy.x + dy.y, dz.x + dz.y);
+}
+
 // val of every real SELL element from positions (tensor cores; see above)
 template <typename valT>
 __global__ void __launch_bounds__(128, kEnvTcCtasPerSm) env_hopping_tc_kernel(
     int64_t n, int64_t n_slices, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ cnt,
-    const double *__restrict__ pos, const int32_t *__restrict__ species, Box B, float rcut,
-    const int32_t *__restrict__ col, const float *__restrict__ cmix, const float *__restrict__ v,
+    const float4 *__restrict__ ph, const float4 *__restrict__ pl, const int32_t *__restrict__ species, BoxPair B,
+    float rcut, const int32_t *__restrict__ col, const float *__restrict__ cmix, const float *__restrict__ v,
     const float *__restrict__ params, valT *__restrict__ val, int *__restrict__ flags) {
   extern __shared__ __align__(128) unsigned char env_raw[];
   EnvTcSmem &S = *reinterpret_cast<EnvTcSmem *>(env_raw + ((128 - (tc::smem_addr(env_raw) & 127)) & 127));
@@ -397,8 +484,17 @@ __global__ void __launch_bounds__(128, kEnvTcCtasPerSm) env_hopping_tc_kernel(
     {
       float u[8];
       if (valid) {
-        float3 d;
-        bond_inputs(pos, species, B, rcut, S.sc, v, i, col[e], C, u, nz2, d);
+        const int32_t j = col[e];
+        const int zi = min(max(species[i], 0), 2), zj = min(max(species[j], 0), 2);
+        const float3 d = bond_vector_pair(B, ph, pl, i, j);
+        const float r2 = bond_r2_f32(d);
+        bond_descriptor(sqrtf(r2), rcut, S.sc + (zi * 3 + zj) * 64, C);
+        float vi[8], vj[8];
+        load8(v + i * 8, vi);
+        load8(v + (int64_t)j * 8, vj);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] = vi[k] + vj[k];
+        nz2 = r2 > 0.0f ? d.z * d.z / r2 : 0.0f;
       } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) C[j] = u[j] = 0.0f;
@@ -1273,8 +1369,10 @@ template <typename valT>
 tb_status launch_env_tc(int64_t n, const int64_t *slice_ptr, const int32_t *cnt, const double *pos,
                         const int32_t *species, const Box &B, float rcut, const int32_t *col, const float *cmix,
                         const float *v, const float *params, const float *eps0, void *val, void *diag, int *flags,
-                        cudaStream_t st) {
+                        float4 *ph, float4 *pl, cudaStream_t st) {
   const int64_t n_slices = (n + 31) / 32;
+  pos_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pos, n, ph, pl);
+  TB_CHECK_LAUNCH();
   // the whole unified L1/shared array as shared memory: room for 7 CTAs of 30 KB
   TB_CUDA(cudaFuncSetAttribute(env_hopping_tc_kernel<valT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kEnvTcSmemBytes));
@@ -1284,9 +1382,9 @@ tb_status launch_env_tc(int64_t n, const int64_t *slice_ptr, const int32_t *cnt,
   // occupancy query reports 1 for this kernel), each taking a contiguous
   // range of 128-slot tiles (empty for the CTAs beyond the tile count)
   const unsigned grid = (unsigned)(sm_count() * kEnvTcCtasPerSm);
-  env_hopping_tc_kernel<valT><<<grid, 128, kEnvTcSmemBytes, st>>>(n, n_slices, slice_ptr, cnt, pos, species, B, rcut,
-                                                                   col, cmix, v, params, static_cast<valT *>(val),
-                                                                   flags);
+  env_hopping_tc_kernel<valT><<<grid, 128, kEnvTcSmemBytes, st>>>(n, n_slices, slice_ptr, cnt, ph, pl, species,
+                                                                   box_pair(B), rcut, col, cmix, v, params,
+                                                                   static_cast<valT *>(val), flags);
   TB_CHECK_LAUNCH();
   if (diag) {
     const int64_t want = (n + 127) / 128, cap = (int64_t)sm_count() * 8;
@@ -1297,6 +1395,11 @@ tb_status launch_env_tc(int64_t n, const int64_t *slice_ptr, const int32_t *cnt,
   return TB_OK;
 }
 }  // namespace
+
+extern "C" size_t tb_build_hamiltonian_env_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  return 256 + (size_t)n * 2 * sizeof(float4);   // status word, then the FP32-pair positions
+}
 
 extern "C" tb_status tb_build_hamiltonian_env(const double *positions, const int32_t *species, int64_t n,
                                               const double *box, const int32_t *pbc, double rcut,
@@ -1309,8 +1412,11 @@ extern "C" tb_status tb_build_hamiltonian_env(const double *positions, const int
   TB_REQUIRE(positions && species && cmix && v && params && eps0 && val,
              "tb_build_hamiltonian_env: null pointer");
   TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian_env: bad precision");
-  TB_REQUIRE(workspace && workspace_bytes >= 256 && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0,
-             "tb_build_hamiltonian_env: workspace must be >= 256 bytes, 256-byte aligned");
+  TB_REQUIRE(workspace && (reinterpret_cast<uintptr_t>(workspace) & 255) == 0,
+             "tb_build_hamiltonian_env: workspace must be 256-byte aligned");
+  if (workspace_bytes < tb_build_hamiltonian_env_workspace_size(n))
+    return fail(TB_ERR_WORKSPACE, "tb_build_hamiltonian_env: workspace too small (%zu < %zu)", workspace_bytes,
+                tb_build_hamiltonian_env_workspace_size(n));
   Box B;
   s = make_box(box, pbc, rcut, &B);
   if (s != TB_OK) return s;
@@ -1324,11 +1430,13 @@ extern "C" tb_status tb_build_hamiltonian_env(const double *positions, const int
   }
   if (n == 0) return TB_OK;
   int *flags = static_cast<int *>(workspace);
+  float4 *ph = reinterpret_cast<float4 *>(static_cast<unsigned char *>(workspace) + 256);
+  float4 *pl = ph + n;
   TB_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
   s = precision == TB_F32 ? launch_env_tc<float>(n, slice_ptr, cnt, positions, species, B, (float)rcut, col, cmix, v,
-                                                 params, eps0, val, diag, flags, st)
+                                                 params, eps0, val, diag, flags, ph, pl, st)
                           : launch_env_tc<double>(n, slice_ptr, cnt, positions, species, B, (float)rcut, col, cmix,
-                                                  v, params, eps0, val, diag, flags, st);
+                                                  v, params, eps0, val, diag, flags, ph, pl, st);
   if (s != TB_OK) return s;
   int h = 0;
   TB_CUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -106,6 +106,7 @@ SIGNATURES = {
     "tb_build_hamiltonian_env": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_vp,
                                           _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_sz, _c_vp]),
     "tb_env_set_variant": (_c_i32, [_c_i32]),
+    "tb_build_hamiltonian_env_workspace_size": (_c_sz, [_c_i64]),
     "tb_env_backward_workspace_size": (_c_sz, [_c_i64, _c_i64]),
     "tb_env_backward": (_c_i32, [_c_i64, _c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp,
                                  _c_vp, _c_sz, _c_vp]),
@@ -888,7 +889,7 @@ def build_hamiltonian_env(positions, species, box, pbc, rcut, nb: Neighbors, mod
     b, p, bptr, pptr = _host_box(box, pbc)
     val = torch.zeros(max(nb.total, 1), dtype=dtype, device=positions.device)
     diag = torch.empty(nb.n, dtype=dtype, device=positions.device) if with_diag else None
-    ws = _workspace(256, positions.device)
+    ws = _workspace(lib().tb_build_hamiltonian_env_workspace_size(nb.n), positions.device)
     _check("tb_build_hamiltonian_env", lib().tb_build_hamiltonian_env(
         _ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr), _ptr(nb.col),
         _ptr(nb.cnt), _ptr(model.cmix), _ptr(v), _ptr(model.p), _ptr(model.eps0), precision_of(dtype), _ptr(val),
