@@ -72,11 +72,11 @@ __device__ __forceinline__ void flush_partials(Acc (&acc)[CPT], Acc (&acc2)[CPT]
 
 // The order in which a CTA visits the tiles (or row blocks): chunks of C
 // consecutive tiles, the chunks dealt out grid-stride.  C = 1 is the plain
-// grid-stride order of the single-matrix path; the segmented (batched) mode
-// takes C = kSegChunk, so that a CTA's run within one snapshot spans up to C
-// tiles (one reduction per run) while the CTAs still stream neighbouring
-// memory at any moment (a window of C x grid tiles).
-constexpr int kSegChunk = 8;
+// grid-stride order of the single-matrix path.  C = 0 gives each CTA one
+// contiguous span of about ntiles / grid tiles: the segmented (batched) mode
+// takes it, so that a CTA's run within one snapshot ends only where the
+// snapshot does (one reduction per snapshot the span meets).
+constexpr int kSegChunk = 0;
 template <int C>
 struct TileWalk {
   int64_t ntiles, nchunks;
@@ -92,6 +92,17 @@ struct TileWalk {
   __device__ __forceinline__ int64_t tile(int64_t kk) const {
     return ((kk / C) * gridDim.x + blockIdx.x) * C + kk % C;
   }
+};
+template <>
+struct TileWalk<0> {
+  int64_t first, n;
+  __device__ __forceinline__ explicit TileWalk(int64_t nt) {
+    const int64_t per = (nt + gridDim.x - 1) / gridDim.x;
+    first = min(nt, (int64_t)blockIdx.x * per);
+    n = min(nt, first + per) - first;
+  }
+  __device__ __forceinline__ int64_t count() const { return n; }
+  __device__ __forceinline__ int64_t tile(int64_t kk) const { return first + kk; }
 };
 
 // Segmented mode: block `blk` of the current run of RPB-row blocks has just
@@ -191,8 +202,9 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_kernel(
   constexpr int RPB = kBlock / TPR;
   const int part = threadIdx.x % TPR;
   DotAcc<real> acc[CPT], acc2[CPT];
-  // SEG (batched): the CTA's blocks (grid-stride) form runs within one
-  // snapshot, reduced where the snapshot changes; other blocks' entries are 0
+  // SEG (batched): the CTA's blocks (one contiguous span) form runs within
+  // one snapshot, reduced where the snapshot changes; other blocks' entries
+  // are 0
   const TileWalk<SEG ? kSegChunk : 1> walk((n + RPB - 1) / RPB);
   const int64_t my_blocks = walk.count();
   int64_t run_head = walk.tile(0);
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_bulk_kernel(
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
   const int lr = threadIdx.x / TPR;
-  // tiles of this CTA: grid-stride (in SEG mode too)
+  // tiles of this CTA: grid-stride (one contiguous span in SEG mode)
   const TileWalk<SEG ? kSegChunk : 1> walk(ntiles);   // this CTA's tiles, in order
   auto tile_of = [&](int64_t kk) { return walk.tile(kk); };
 
