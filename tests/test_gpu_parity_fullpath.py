@@ -7,8 +7,9 @@ Here the structures are large enough that, for every launch shape,
 * a CTA of the bulk-copy ring processes more tiles than the ring has
   stages, so stages are reused and the mbarrier phase parity flips;
 * a CTA of the direct-load kernel iterates its grid-stride loop;
-* in the batched (segmented) form each CTA visits blocks of several
-  snapshots, in runs of one or several blocks per snapshot.
+* in the batched (segmented) form each CTA visits a contiguous span of
+  blocks that crosses snapshot boundaries, so its runs end inside the span
+  (one reduction per snapshot met) and at its end.
 The launch geometry is asserted from the library's own grid query, and the
 moments are compared element by element with the FP64 oracle on the same
 seeded inputs.  Tolerances: FP64 moments <= 1e-12 absolute, FP32 <= 2e-4
@@ -156,12 +157,13 @@ def test_batched_runs_cross_snapshots_and_match_oracle(g, batch, dtype):
             info = g.kpm_shape_info(R, dtype, shape)
             grid = g.kpm_shape_grid(n_pad, R, dtype, doubling, shape)
             blocks = n_pad // info["rows_per_tile"]
-            # every CTA visits several blocks (grid-stride); in the largest
-            # snapshot a CTA's run holds two or more of them, in the smallest
-            # one at most one, so runs of both kinds end at snapshot changes
-            assert blocks // grid >= 3
-            assert largest // info["rows_per_tile"] >= 2 * grid
-            assert smallest // info["rows_per_tile"] < grid
+            # every CTA's span holds several blocks, and the spans are
+            # shorter than the smallest snapshot, so that spans start and end
+            # inside snapshots and some cross a snapshot boundary
+            span = -(-blocks // grid)
+            assert span >= 3
+            assert span < smallest // info["rows_per_tile"]
+            assert largest // info["rows_per_tile"] >= 2 * span
             g.kpm_force_shape(R, dtype, shape)
             mu = g.kpm_moments_batched(mats, a, b, M, R, seed, doubling=doubling).cpu().numpy()
             for k, ref in enumerate(refs):
