@@ -17,7 +17,6 @@
 #include <cmath>
 
 #include "common.cuh"
-#include "kpm_step.cuh"
 
 namespace gputb {
 namespace {
@@ -288,146 +287,6 @@ __global__ void __launch_bounds__(kB, 3) lanczos_spmv_df_kernel(
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// The same SpMV for a matrix with a band plan (kpm_band.cuh, tiles of
-// kLzT rows): per tile, the record, the local indices, the values, the
-// diagonal and the bands of U rows are bulk-copied into a two-stage
-// shared-memory ring (thread 0 produces; waits bounded, flags[0] |= 4 on
-// timeout), and each thread takes its row's operands from shared memory.
-// Tiles without bands (nb < 0) gather from global memory.  The arithmetic
-// and its order are those of lanczos_spmv_df_kernel, so both give the same
-// bits.
-constexpr int kLzT = 256;       // rows per tile: one thread per row
-constexpr int kLzRows = 1024;   // U rows the bands of a stage may hold
-constexpr int kLzStages = 2;
-struct LzGeom {
-  static constexpr size_t kRec = sizeof(BandRec);
-  static constexpr size_t kIdx = (size_t)kLzT * kBandSlots * 2;
-  static constexpr size_t kVal = (size_t)kLzT * kBandSlots * 4;
-  static constexpr size_t kDiag = (size_t)kLzT * 4;
-  static constexpr size_t kX = (size_t)kLzRows * sizeof(float2);
-  static constexpr size_t kStage = kRec + kIdx + kVal + kDiag + kX;
-  static constexpr size_t kSmem = 128 + kLzStages * kStage;   // mbarriers first
-};
-static_assert(LzGeom::kStage % 16 == 0 && LzGeom::kSmem <= 110 * 1024, "Lanczos band stage");
-
-template <bool PREV>
-__global__ void __launch_bounds__(kB, 3) lanczos_spmv_band_kernel(
-    int64_t n, const int32_t *__restrict__ col, const float *__restrict__ val, const float *__restrict__ diag,
-    const float2 *__restrict__ u, const double *__restrict__ s_j, float2 *prev_w, const double *__restrict__ s_prev,
-    const double *__restrict__ beta_prev, double *__restrict__ part, const BandRec *__restrict__ recs,
-    const uint16_t *__restrict__ lidx, int *__restrict__ flags) {
-  using G = LzGeom;
-  extern __shared__ __align__(128) unsigned char lz_smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(lz_smem);
-  unsigned char *ring = lz_smem + 128;
-  auto s_rec = [&](int st) { return reinterpret_cast<BandRec *>(ring + st * G::kStage); };
-  auto s_idx = [&](int st) { return reinterpret_cast<uint16_t *>(ring + st * G::kStage + G::kRec); };
-  auto s_val = [&](int st) { return reinterpret_cast<float *>(ring + st * G::kStage + G::kRec + G::kIdx); };
-  auto s_diag = [&](int st) {
-    return reinterpret_cast<float *>(ring + st * G::kStage + G::kRec + G::kIdx + G::kVal);
-  };
-  auto s_x = [&](int st) {
-    return reinterpret_cast<float2 *>(ring + st * G::kStage + G::kRec + G::kIdx + G::kVal + G::kDiag);
-  };
-  const dfl sj = to_dfl(*s_j);
-  const dfl c = PREV ? to_dfl(-(*beta_prev) * (*s_prev)) : dfl{0.0f, 0.0f};
-  const int64_t ntiles = (n + kLzT - 1) / kLzT;
-  const TileWalk<1> walk(ntiles);
-  const int64_t my_tiles = walk.count();
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kLzStages; ++st) mbar_init(full + st, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  // thread 0: the record of local tile kk into its stage, then the copies
-  auto issue = [&](int64_t kk) {
-    const int64_t tile = walk.tile(kk);
-    const int st = static_cast<int>(kk % kLzStages);
-    const int64_t r0 = tile * kLzT;
-    BandRec *rc = s_rec(st);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) reinterpret_cast<int4 *>(rc)[q] = __ldg(reinterpret_cast<const int4 *>(recs + tile) + q);
-    const int nb = rc->nb;
-    const bool whole = r0 + kLzT <= n;
-    const uint32_t cnt = static_cast<uint32_t>(rc->srel[kLzT / 32]);
-    uint32_t tx = 0;
-    if (nb > 0) {
-      uint32_t xrows = 0;
-      for (int b = 0; b < nb; ++b) xrows += static_cast<uint32_t>(rc->len[b]);
-      tx = cnt * 6u + xrows * static_cast<uint32_t>(sizeof(float2)) + ((diag && whole) ? kLzT * 4u : 0u);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(full + st, tx);
-    if (nb > 0) {
-      for (int b = 0; b < nb; ++b)
-        bulk_g2s(s_x(st) + rc->off[b], u + rc->lo[b], static_cast<uint32_t>(rc->len[b]) * (uint32_t)sizeof(float2),
-                 full + st);
-      if (cnt > 0) {
-        bulk_g2s(s_idx(st), lidx + tile * (int64_t)kLzT * kBandSlots, cnt * 2u, full + st);
-        bulk_g2s(s_val(st), val + rc->e0, cnt * 4u, full + st);
-      }
-      if (diag && whole) bulk_g2s(s_diag(st), diag + r0, kLzT * 4u, full + st);
-    }
-  };
-
-  int64_t issued = 0;
-  if (threadIdx.x == 0)
-    for (; issued < my_tiles && issued < kLzStages; ++issued) issue(issued);
-  dfl acc{0.0f, 0.0f};
-  bool ok = true;
-  int64_t kk = 0;
-  for (; kk < my_tiles; ++kk) {
-    const int st = static_cast<int>(kk % kLzStages);
-    ok = __syncthreads_and(mbar_wait_bounded(full + st, static_cast<uint32_t>((kk / kLzStages) & 1))) != 0;
-    if (!ok) break;
-    const int64_t r0 = walk.tile(kk) * kLzT;
-    const int64_t i = r0 + threadIdx.x;
-    if (i < n) {
-      const BandRec &rc = *s_rec(st);
-      const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      const int sb = rc.srel[q];
-      const int ww = (rc.srel[q + 1] - sb) >> 5;
-      float shi = 0.0f, slo = 0.0f;
-      float2 ui;
-      if (rc.nb > 0) {
-        const float2 *xs = s_x(st);
-        ui = xs[rc.own + threadIdx.x];
-        if (diag) df_axpy_acc(r0 + kLzT <= n ? s_diag(st)[threadIdx.x] : __ldg(diag + i), ui, shi, slo);
-        const uint16_t *li = s_idx(st) + sb + lane;
-        const float *vs = s_val(st) + sb + lane;
-#pragma unroll
-        for (int s = 0; s < kBandSlots; ++s)
-          if (s < ww) df_axpy_acc(vs[32 * s], xs[li[32 * s]], shi, slo);
-      } else {
-        ui = __ldg(u + i);
-        if (diag) df_axpy_acc(__ldg(diag + i), ui, shi, slo);
-        const int64_t e0 = rc.e0 + sb + lane;
-        for (int s = 0; s < ww; ++s) df_axpy_acc(__ldcs(val + e0 + 32 * s), __ldg(u + __ldcs(col + e0 + 32 * s)), shi, slo);
-      }
-      float2 pv = make_float2(0.0f, 0.0f);
-      if (PREV) pv = __ldcs(prev_w + i);
-      dfl y = df_mul(two_sum(shi, slo), sj);
-      if (PREV) y = df_add(y, df_mul(dfl{pv.x, pv.y}, c));
-      prev_w[i] = make_float2(y.hi, y.lo);
-      acc = df_add(acc, df_mul(df_mul(dfl{ui.x, ui.y}, sj), y));
-    }
-    __syncthreads();   // every thread is done with this stage
-    if (threadIdx.x == 0 && issued < my_tiles) issue(issued++);
-  }
-  if (!ok) {
-    if (threadIdx.x == 0) {
-      atomicOr(flags, 4);
-      for (int64_t q = kk; q < issued; ++q)
-        mbar_wait_bounded(full + q % kLzStages, static_cast<uint32_t>((q / kLzStages) & 1));
-    }
-    __syncthreads();
-    acc = dfl{0.0f, 0.0f};
-  }
-  const double s = block_sum(to_double(acc));
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
 // w -= alpha_j s_j U_j; part = sum w.w
 __global__ void lanczos_orth_df_kernel(int64_t n, const float2 *__restrict__ u, const double *__restrict__ s_j,
                                        const double *__restrict__ alpha, float2 *__restrict__ w,
@@ -545,17 +404,12 @@ template <typename valT>
 tb_status run_bounds(int64_t n, const int64_t *sp, const int32_t *col, const valT *val, const valT *diag, int k,
                      uint64_t seed, double *out_host, void *ws, size_t wsb, cudaStream_t st) {
   const int grid = grid_for(n);
-  const int64_t ntiles = (n + kLzT - 1) / kLzT, n_pad = ntiles * kLzT;
   Carver cv(ws, wsb);
-  double *q0 = cv.take<double>(n_pad), *q1 = cv.take<double>(n_pad), *w = cv.take<double>(n);
+  double *q0 = cv.take<double>(n), *q1 = cv.take<double>(n), *w = cv.take<double>(n);
   double *part = cv.take<double>(grid), *glo = cv.take<double>(grid), *ghi = cv.take<double>(grid);
   double *alpha = cv.take<double>(k), *beta = cv.take<double>(k), *norm = cv.take<double>(1);
   double *out = cv.take<double>(8), *inv = cv.take<double>(k + 1);
-  BandRec *recs = cv.take<BandRec>(ntiles);
-  uint16_t *lidx = cv.take<uint16_t>((size_t)n_pad * kBandSlots);
-  int *flags = cv.take<int>(4);
   if (!cv.ok()) return fail(TB_ERR_WORKSPACE, "tb_spectral_bounds: workspace too small");
-  TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
   gershgorin_kernel<valT><<<grid, kB, 0, st>>>(n, sp, col, val, diag, glo, ghi);
   TB_CHECK_LAUNCH();
   if constexpr (sizeof(valT) == 4) {
@@ -568,49 +422,19 @@ tb_status run_bounds(int64_t n, const int64_t *sp, const int32_t *col, const val
                         per_sm <= 0))
       per_sm = 3;
     const int gs = std::min<int64_t>(grid, (int64_t)per_sm * sm_count());
-    // the banded SpMV (plan of kLzT-row tiles, bands of at most kLzRows U
-    // rows) wherever the bulk copies' 16-byte rule holds for val and diag
-    const bool banded = ((reinterpret_cast<uintptr_t>(val) | reinterpret_cast<uintptr_t>(diag)) & 15) == 0;
-    static int per_sm_band = 0;
-    if (banded && per_sm_band == 0) {
-      TB_CUDA(cudaFuncSetAttribute(lanczos_spmv_band_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)LzGeom::kSmem));
-      TB_CUDA(cudaFuncSetAttribute(lanczos_spmv_band_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)LzGeom::kSmem));
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_band, lanczos_spmv_band_kernel<true>, kB,
-                                                        LzGeom::kSmem) != cudaSuccess ||
-          per_sm_band <= 0)
-        per_sm_band = 3;
-    }
-    const int gb = std::min<int64_t>(std::min<int64_t>(grid, ntiles), (int64_t)per_sm_band * sm_count());
-    if (banded) {
-      const int64_t cap = (int64_t)sm_count() * 4;
-      band_plan_kernel<kLzT><<<(unsigned)(ntiles < cap ? ntiles : cap), 256, 0, st>>>(n, sp, col, kLzRows, 2, n_pad,
-                                                                                     recs, lidx);
-      TB_CHECK_LAUNCH();
-    }
     lanczos_start_df_kernel<<<grid, kB, 0, st>>>(n, seed, ua, part);
     TB_CHECK_LAUNCH();
     reduce_norm_kernel<<<1, kB, 0, st>>>(part, grid, nullptr, inv);
     TB_CHECK_LAUNCH();
     for (int j = 0; j < k; ++j) {
-      if (banded) {
-        if (j == 0)
-          lanczos_spmv_band_kernel<false><<<gb, kB, LzGeom::kSmem, st>>>(n, col, val, diag, ua, inv, ub, nullptr,
-                                                                         nullptr, part, recs, lidx, flags);
-        else
-          lanczos_spmv_band_kernel<true><<<gb, kB, LzGeom::kSmem, st>>>(n, col, val, diag, ua, inv + j, ub,
-                                                                        inv + j - 1, beta + j - 1, part, recs, lidx,
-                                                                        flags);
-      } else if (j == 0) {
+      if (j == 0)
         lanczos_spmv_df_kernel<false><<<gs, kB, 0, st>>>(n, sp, col, val, diag, ua, inv, ub, nullptr, nullptr,
                                                          part);
-      } else {
+      else
         lanczos_spmv_df_kernel<true><<<gs, kB, 0, st>>>(n, sp, col, val, diag, ua, inv + j, ub, inv + j - 1,
                                                         beta + j - 1, part);
-      }
       TB_CHECK_LAUNCH();
-      reduce_scalar_kernel<<<1, kB, 0, st>>>(part, banded ? gb : gs, alpha, j, 0);
+      reduce_scalar_kernel<<<1, kB, 0, st>>>(part, gs, alpha, j, 0);
       TB_CHECK_LAUNCH();
       if (j == k - 1) break;
       lanczos_orth_df_kernel<<<grid, kB, 0, st>>>(n, ua, inv + j, alpha + j, ub, part);
@@ -652,10 +476,7 @@ tb_status run_bounds(int64_t n, const int64_t *sp, const int32_t *col, const val
   finish_bounds_kernel<<<1, 32, 0, st>>>(alpha, beta, k, glo, ghi, grid, 0.01, 0.01, out);
   TB_CHECK_LAUNCH();
   TB_CUDA(cudaMemcpyAsync(out_host, out, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  int hflags = 0;
-  TB_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
   TB_CUDA(cudaStreamSynchronize(st));
-  if (hflags & 4) return fail(TB_ERR_TIMEOUT, "tb_spectral_bounds: a shared-memory pipeline wait timed out");
   for (int c = 0; c < 4; ++c)
     if (!std::isfinite(out_host[c])) return fail(TB_ERR_NOT_FINITE, "tb_spectral_bounds: non-finite bound");
   if (!(out_host[2] > 0.0)) return fail(TB_ERR_NOT_FINITE, "tb_spectral_bounds: degenerate spectrum (a <= 0)");
@@ -671,9 +492,8 @@ extern "C" size_t tb_spectral_bounds_workspace_size(int64_t n, int32_t lanczos_s
   if (n <= 0 || lanczos_steps < 1) return 0;
   Carver cv(nullptr, 0);
   const int grid = grid_for(n);
-  const int64_t ntiles = (n + kLzT - 1) / kLzT, n_pad = ntiles * kLzT;
-  cv.take<double>(n_pad);
-  cv.take<double>(n_pad);
+  cv.take<double>(n);
+  cv.take<double>(n);
   cv.take<double>(n);
   cv.take<double>(grid);
   cv.take<double>(grid);
@@ -683,9 +503,6 @@ extern "C" size_t tb_spectral_bounds_workspace_size(int64_t n, int32_t lanczos_s
   cv.take<double>(1);
   cv.take<double>(8);
   cv.take<double>(lanczos_steps + 1);
-  cv.take<BandRec>(ntiles);
-  cv.take<uint16_t>((size_t)n_pad * kBandSlots);
-  cv.take<int>(4);
   return cv.used + 256;
 }
 
