@@ -694,15 +694,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // FREE: no CTA barrier per tile; each warp releases a stage on its "empty"
 // mbarrier (8 arrivals), and warp 0 refills a stage once its previous tile
 // is released by every warp, before waiting on its own next stage.
-template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int ROWS, bool FREE, bool DV,
-          bool FIRST, bool DBL, bool SEG>
+template <typename real, typename valT, int R, int CPT, int STAGES, int MINB, int ROWS, bool FREE, bool FIRST,
+          bool DBL, bool SEG>
 __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     int64_t n, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const valT *__restrict__ val, const valT *__restrict__ diag, const real *__restrict__ x, const real *prev,
     const real *__restrict__ v0, real *out, double *__restrict__ partial, real alpha, real shift,
     int *__restrict__ flags, int64_t slot_stride, BatchTables bt, const BandRec *__restrict__ recs,
     const uint16_t *__restrict__ lidx) {
-  using G = BandGeom<real, valT, R, CPT, STAGES, ROWS, DV ? 0 : (DBL ? 1 : 2)>;
+  using G = BandGeom<real, valT, R, CPT, STAGES, ROWS, DBL ? 1 : 2>;
   constexpr int TPR = G::TPR, TR = G::TR;
   constexpr int RE = R * 2;   // reals per x row
   extern __shared__ __align__(128) unsigned char smem[];
@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
   };
   auto s_x = [&](int st) {
     return reinterpret_cast<real *>(ring + st * G::kStageBytes + G::kRecBytes + G::kIdxBytes + G::kValBytes +
-                                    G::kDiagBytes + (DV ? 0 : (DBL ? 1 : 2)) * G::kVecBytes);
+                                    G::kDiagBytes + (DBL ? 1 : 2) * G::kVecBytes);
   };
   const int64_t ntiles = (n + TR - 1) / TR;
   const int part = threadIdx.x % TPR;
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
     const int64_t e0 = rc.e0;
     __syncwarp();   // every lane has read the ring slot and the stage record is written
     if (lane == 0) {
-      uint32_t tx = DV ? 0u : static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
+      uint32_t tx = static_cast<uint32_t>(G::kVecBytes) * ((FIRST ? 0u : 1u) + (DBL ? 0u : 1u));
       if (banded) {
         uint32_t xrows = 0;
         for (int b = 0; b < nb; ++b) xrows += static_cast<uint32_t>(rc.len[b]);
@@ -801,9 +801,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
       if (lane == 10 && diag && whole) bulk_g2s(s_diag(st), diag + r0, TR * sizeof(valT), full + st);
     }
     const size_t voff = (size_t)r0 * RE;
-    if (!DV && !FIRST && lane == 11)
-      bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
-    if (!DV && !DBL && lane == 12) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    if (!FIRST && lane == 11) bulk_g2s(s_vec(st, 0), prev + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
+    if (!DBL && lane == 12) bulk_g2s(s_vec(st, 1), v0 + voff, static_cast<uint32_t>(G::kVecBytes), full + st);
     return true;
   };
 
@@ -851,13 +850,8 @@ __global__ void __launch_bounds__(kBlock, MINB) cheb_step_band_kernel(
       const int sb = rc.srel[q];
       const int w = (rc.srel[q + 1] - sb) >> 5;
       real p[2 * CPT], z[2 * CPT];
-      if (DV) {   // the vector rows straight from global memory (streamed)
-        if (!FIRST) ld_stream<real, CPT>(prev + off, p);
-        if (!DBL) ld_stream<real, CPT>(v0 + off, z);
-      } else {
-        if (!FIRST) memcpy(p, s_vec(st, 0) + (lr * R + part * CPT) * 2, sizeof(p));
-        if (!DBL) memcpy(z, s_vec(st, 1) + (lr * R + part * CPT) * 2, sizeof(z));
-      }
+      if (!FIRST) memcpy(p, s_vec(st, 0) + (lr * R + part * CPT) * 2, sizeof(p));
+      if (!DBL) memcpy(z, s_vec(st, 1) + (lr * R + part * CPT) * 2, sizeof(z));
       real d = real(0);
       if (diag) d = (banded && r0 + TR <= n) ? static_cast<real>(s_diag(st)[lr]) : static_cast<real>(__ldg(diag + i));
       d -= shift;
@@ -990,8 +984,7 @@ template <> struct Shapes<float, 4> {
   static constexpr StepShape at[] = {D(4, 2), D(2, 3), P(2, 3, 2), B(2, 2, 3, 512, 1)};
 };
 template <> struct Shapes<float, 8> {
-  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(2, 3, 4, 1), D(2, 3), B(2, 2, 3, 320, 1),
-                                     B(2, 3, 3, 288, 5), B(2, 2, 3, 320, 5)};
+  static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), P(2, 3, 4, 1), D(2, 3), B(2, 2, 3, 320, 1)};
 };
 template <> struct Shapes<float, 16> {
   static constexpr StepShape at[] = {P(2, 3, 4), P(2, 2, 4), D(2, 3), B(2, 2, 3, 192), B(2, 2, 3, 192, 1)};
@@ -1044,7 +1037,7 @@ struct ShapeKit {
   template <bool DBL>
   using G2 = Ring2Geom<real, valT, R, CPT, S, RPT, SVEC != 0, DBL ? 1 : 2>;
   template <bool DBL>
-  using GBand = BandGeom<real, valT, R, CPT, S, (BROWS > 0 ? BROWS : 32), (OPT & 4) ? 0 : (DBL ? 1 : 2)>;
+  using GBand = BandGeom<real, valT, R, CPT, S, (BROWS > 0 ? BROWS : 32), (DBL ? 1 : 2)>;
   template <bool DBL>
   static constexpr size_t smem() {
     return KIND == 1 ? GB<DBL>::kSmem : (KIND == 2 ? G2<DBL>::kSmem : (KIND == 3 ? GBand<DBL>::kSmem : 0));
@@ -1063,8 +1056,8 @@ struct ShapeKit {
     else if constexpr (KIND == 2)
       return cheb_step_ring2_kernel<real, valT, R, CPT, S, MINB, RPT, SVEC != 0, FIRST, DBL, SEG>;
     else if constexpr (KIND == 3)
-      return cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0,
-                                   (OPT & 4) != 0, FIRST, DBL, SEG>;
+      return cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0, FIRST, DBL,
+                                   SEG>;
     else
       return cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG>;
   }
@@ -1131,8 +1124,7 @@ struct ShapeKit {
       cheb_step_kernel<real, valT, R, CPT, MINB, FIRST, DBL, SEG><<<grid, kBlock, 0, st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, slot_stride, bt);
     else if constexpr (KIND == 3)
-      cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0, (OPT & 4) != 0,
-                            FIRST, DBL, SEG>
+      cheb_step_band_kernel<real, valT, R, CPT, S, MINB, (BROWS > 0 ? BROWS : 32), (OPT & 1) != 0, FIRST, DBL, SEG>
           <<<grid, kBlock, smem<DBL>(), st>>>(
           n, slice_ptr, col, val, diag, x, prev, v0, out, partial, alpha, shift, flags, slot_stride, bt, bp.recs,
           bp.lidx);
