@@ -412,10 +412,19 @@ def _record_tuned(n: int, R: int, prec: int, mode: int, shape: int):
     key = f"p{prec}-R{R}-m{mode}-c{_size_class(n)}"
     entries[key] = {"precision": prec, "R": int(R), "mode": int(mode), "n": int(n), "shape": int(shape),
                     "desc": kpm_shape_info(R, prec, shape)}
-    tmp = path + ".tmp"
-    with open(tmp, "w") as fh:
-        json.dump(data, fh, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    # a private temporary file and an atomic rename: ranks that tune at the
+    # same time each leave a whole file (the last one wins); the cache is
+    # best-effort, so a failed write is not an error
+    tmp = f"{path}.{os.getpid()}.tmp"
+    try:
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        try:
+            os.remove(tmp)
+        except OSError:
+            pass
 
 
 def load_tuned_shapes(path: Optional[str] = None) -> int:
