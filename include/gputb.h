@@ -478,9 +478,15 @@ TB_API tb_status tb_build_neighbors(const double *positions, int64_t n, const do
  *   hop_prefactor  host double [3][3] P (eV);  onsite  host double [3] (eV)
  *   val            device float/double [slice_ptr[last]] output
  *   diag           device float/double [N] output (onsite), or NULL
- *   workspace      device, >= 256 bytes, 256-byte aligned (the species check)
+ *   workspace      device, 256-byte aligned, at least
+ *                  tb_build_hamiltonian_teacher_workspace_size(n, precision)
+ *                  bytes (the species check; for FP32 values also the
+ *                  positions split into FP32 pairs, from which the bond
+ *                  lengths are formed: r^2 to about 44 bits)
  * Synchronises `stream`.
  * ------------------------------------------------------------------- */
+TB_API size_t tb_build_hamiltonian_teacher_workspace_size(int64_t n, int32_t precision);
+
 TB_API tb_status tb_build_hamiltonian_teacher(const double *positions, const int32_t *species, int64_t n,
                                               const double *box, const int32_t *pbc,
                                               const int64_t *slice_ptr, const int32_t *col,

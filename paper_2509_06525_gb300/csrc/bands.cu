@@ -328,93 +328,6 @@ __device__ __forceinline__ void env_silu_row32(uint32_t taddr, bf16 *a32, int r,
   }
 }
 
-// Positions as FP32 pairs (x = hi + lo to about 2^-48 relative), so that the
-// tensor-core kernel forms bond vectors on the FP32 pipes: GB300 issues FP64
-// at a small fraction of the FP32 rate.
-__global__ void pos_pair_kernel(const double *__restrict__ pos, int64_t n, float4 *__restrict__ hi,
-                                float4 *__restrict__ lo) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  const float hx = (float)x, hy = (float)y, hz = (float)z;
-  hi[i] = make_float4(hx, hy, hz, 0.0f);
-  lo[i] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.0f);
-}
-
-// the box of `Box` with every lattice component as an FP32 pair
-struct BoxPair {
-  float2 ax, bx, by, cx, cy, cz;
-  float iax, iby, icz;
-  int p1, p2, p3;
-};
-
-BoxPair box_pair(const Box &B) {
-  auto split = [](double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-  };
-  BoxPair P;
-  P.ax = split(B.ax);
-  P.bx = split(B.bx);
-  P.by = split(B.by);
-  P.cx = split(B.cx);
-  P.cy = split(B.cy);
-  P.cz = split(B.cz);
-  P.iax = (float)B.iax;
-  P.iby = (float)B.iby;
-  P.icz = (float)B.icz;
-  P.p1 = B.p1;
-  P.p2 = B.p2;
-  P.p3 = B.p3;
-  return P;
-}
-
-// a + b as an unevaluated pair (s, e), s + e exact (Knuth's TwoSum)
-__device__ __forceinline__ float2 two_sum_f(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return make_float2(s, (a - (s - bb)) + (b - bb));
-}
-
-// x = (h, l) minus k (Lh, Ll): the high parts through TwoSum, so that a
-// coordinate difference across a periodic seam loses nothing
-__device__ __forceinline__ float2 pair_shift(float2 x, float k, float2 L) {
-  const float2 t = two_sum_f(x.x, -k * L.x);
-  return make_float2(t.x, t.y + (x.y - k * L.y));
-}
-
-// r_j - r_i (minimum image, reduced along a3, a2, a1 as bond_vector_f32)
-// from FP32-pair positions; exact up to the final FP32 rounding, and
-// r_i - r_j is its exact negative (every step is sign-symmetric)
-__device__ __forceinline__ float3 bond_vector_pair(const BoxPair &B, const float4 *__restrict__ ph,
-                                                   const float4 *__restrict__ pl, int64_t i, int64_t j) {
-  const float4 hi = __ldg(ph + i), hj = __ldg(ph + j), li = __ldg(pl + i), lj = __ldg(pl + j);
-  float2 dx = two_sum_f(hj.x, -hi.x), dy = two_sum_f(hj.y, -hi.y), dz = two_sum_f(hj.z, -hi.z);
-  dx.y += lj.x - li.x;
-  dy.y += lj.y - li.y;
-  dz.y += lj.z - li.z;
-  if (B.p3) {
-    const float n3 = rintf((dz.x + dz.y) * B.icz);
-    if (n3 != 0.0f) {
-      dx = pair_shift(dx, n3, B.cx);
-      dy = pair_shift(dy, n3, B.cy);
-      dz = pair_shift(dz, n3, B.cz);
-    }
-  }
-  if (B.p2) {
-    const float n2 = rintf((dy.x + dy.y) * B.iby);
-    if (n2 != 0.0f) {
-      dx = pair_shift(dx, n2, B.bx);
-      dy = pair_shift(dy, n2, B.by);
-    }
-  }
-  if (B.p1) {
-    const float n1 = rintf((dx.x + dx.y) * B.iax);
-    if (n1 != 0.0f) dx = pair_shift(dx, n1, B.ax);
-  }
-  return make_float3(dx.x + dx.y, dy.x + dy.y, dz.x + dz.y);
-}
-
 // val of every real SELL element from positions (tensor cores; see above)
 template <typename valT>
 __global__ void __launch_bounds__(128, kEnvTcCtasPerSm) env_hopping_tc_kernel(

@@ -96,6 +96,7 @@ SIGNATURES = {
                                _c_vp]),
     "tb_mlp_pack_weights": (_c_i32, [_c_vp, _c_vp, _c_vp]),
     "tb_build_hamiltonian_workspace_size": (_c_sz, [_c_i64]),
+    "tb_build_hamiltonian_teacher_workspace_size": (_c_sz, [_c_i64, _c_i32]),
     "tb_build_hamiltonian": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i64,
                                       _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp,
                                       _c_sz, _c_vp]),
@@ -632,7 +633,7 @@ def build_hamiltonian_teacher(positions: torch.Tensor, species: torch.Tensor, bo
     onsite = np.ascontiguousarray(np.asarray(teacher.onsite, np.float64).reshape(3))
     val = torch.empty(max(nb.total, 1), dtype=dtype, device=dev)
     diag = torch.empty(nb.n, dtype=dtype, device=dev) if with_diag else None
-    ws = _workspace(256, dev)
+    ws = _workspace(L.tb_build_hamiltonian_teacher_workspace_size(nb.n, precision_of(dtype)), dev)
     st = L.tb_build_hamiltonian_teacher(
         _ptr(positions), _ptr(species), nb.n, bptr, pptr, _ptr(nb.slice_ptr), _ptr(nb.col), _ptr(nb.cnt),
         _ptr(nb.ncount), pref.ctypes.data_as(ctypes.c_void_p), onsite.ctypes.data_as(ctypes.c_void_p),
