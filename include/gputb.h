@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GPUTB_ABI_VERSION 8
+#define GPUTB_ABI_VERSION 9
 
 #if defined(__GNUC__)
 #define TB_API __attribute__((visibility("default")))
@@ -607,13 +607,17 @@ TB_API tb_status tb_adamw_step(float *params, const float *grad, float *m, float
 TB_API tb_status tb_mlp_pack_weights(const float *params, void *w_bf16, void *stream);
 
 /* Tuning hook for the forward pass of tb_build_hamiltonian: 0 = 5th-
- * generation tensor cores (tcgen05, accumulators in TMEM; default),
- * 1 = mma.sync tiles.  Both compute the same MLP in BF16 with FP32
- * accumulation (sums in a different order).  Process-wide. */
+ * generation tensor cores (tcgen05, accumulators in TMEM; default; bond
+ * lengths from the positions split into FP32 pairs), 1 = mma.sync tiles
+ * (bond lengths from FP64 coordinate differences).  Both compute the same
+ * MLP in BF16 with FP32 accumulation (sums in a different order).
+ * Process-wide. */
 TB_API tb_status tb_mlp_set_variant(int32_t variant);
 
-/* Workspace bytes of tb_build_hamiltonian. */
-TB_API size_t tb_build_hamiltonian_workspace_size(int64_t total_elements);
+/* Workspace bytes of tb_build_hamiltonian for n atoms and total_elements
+ * SELL elements (the two network outputs per element, status words and the
+ * FP32-pair positions). */
+TB_API size_t tb_build_hamiltonian_workspace_size(int64_t n, int64_t total_elements);
 
 /* Learned Hamiltonian in SELL-32: val (device, `precision`, [total]) and
  * diag (device [N] or NULL).  v from tb_compute_descriptors on the same

@@ -226,6 +226,32 @@ __device__ __forceinline__ void edge_features(const double *__restrict__ pos, co
   }
 }
 
+// the same features with the bond length from FP32-pair positions (r^2 as an
+// FP32 pair: no FP64 instruction; the inference kernel on the tensor cores)
+__device__ __forceinline__ void edge_features_pair(const BoxPair &BP, const float4 *__restrict__ ph,
+                                                   const float4 *__restrict__ pl, const int32_t *__restrict__ species,
+                                                   float rcut, const float *sc, const float *__restrict__ v, int64_t i,
+                                                   int32_t j, float (&x)[32]) {
+  const int zi = min(max(species[i], 0), 2), zj = min(max(species[j], 0), 2);
+  const float2 r2 = bond_r2_pair(BP, ph, pl, i, j);
+  const float r = sqrtf(r2.x + r2.y);
+  float C[8];
+  bond_descriptor(r, rcut, sc + (zi * 3 + zj) * 64, C);
+  const float4 *vi4 = reinterpret_cast<const float4 *>(v + i * 8);
+  const float4 *vj4 = reinterpret_cast<const float4 *>(v + (int64_t)j * 8);
+  float vi[8], vj[8];
+  float4 a = __ldg(vi4), b = __ldg(vi4 + 1), c = __ldg(vj4), d = __ldg(vj4 + 1);
+  vi[0] = a.x; vi[1] = a.y; vi[2] = a.z; vi[3] = a.w; vi[4] = b.x; vi[5] = b.y; vi[6] = b.z; vi[7] = b.w;
+  vj[0] = c.x; vj[1] = c.y; vj[2] = c.z; vj[3] = c.w; vj[4] = d.x; vj[5] = d.y; vj[6] = d.z; vj[7] = d.w;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    x[k] = C[k];
+    x[8 + k] = vi[k];
+    x[16 + k] = vj[k];
+    x[24 + k] = C[k] * (vi[k] + vj[k]);
+  }
+}
+
 // raw FP32 features (and optionally normalised BF16) in SELL element order
 __global__ void edge_feature_kernel(const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n,
                                     int64_t n_slices, Box B, float rcut, const int64_t *__restrict__ slice_ptr,
@@ -840,8 +866,8 @@ __device__ __forceinline__ void tc_operands_ready() {
 }
 
 __global__ void __launch_bounds__(kThreads) mlp_hamiltonian_tc_kernel(
-    const double *__restrict__ pos, const int32_t *__restrict__ species, int64_t n, int64_t n_slices, Box B,
-    float rcut, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
+    const float4 *__restrict__ ph, const float4 *__restrict__ pl, const int32_t *__restrict__ species, int64_t n,
+    int64_t n_slices, BoxPair BP, float rcut, const int64_t *__restrict__ slice_ptr, const int32_t *__restrict__ col,
     const int32_t *__restrict__ cnt, const float *__restrict__ cmix, const float *__restrict__ v,
     const float *__restrict__ mean, const float *__restrict__ inv_std, const bf16 *__restrict__ wb,
     const float *__restrict__ p, float *__restrict__ y0, float *__restrict__ y1, int *__restrict__ flags) {
@@ -881,7 +907,7 @@ __global__ void __launch_bounds__(kThreads) mlp_hamiltonian_tc_kernel(
       {
         float x[32];
         if (valid) {
-          edge_features(pos, species, B, rcut, S.sc, v, i, col[sb + 32 * slot + (tid & 31)], x);
+          edge_features_pair(BP, ph, pl, species, rcut, S.sc, v, i, col[sb + 32 * slot + (tid & 31)], x);
 #pragma unroll
           for (int f = 0; f < 32; ++f) x[f] = (x[f] - S.smean[f]) * S.sinv[f];
         } else {
@@ -1162,9 +1188,11 @@ extern "C" tb_status tb_mlp_pack_weights(const float *params, void *w_bf16, void
   return TB_OK;
 }
 
-extern "C" size_t tb_build_hamiltonian_workspace_size(int64_t total_elements) {
-  if (total_elements < 0) return 0;
-  return 2 * align_up((size_t)(total_elements > 0 ? total_elements : 1) * sizeof(float), 256) + 512;
+extern "C" size_t tb_build_hamiltonian_workspace_size(int64_t n, int64_t total_elements) {
+  if (n < 0 || total_elements < 0) return 0;
+  // y0 and y1 per element, the status words, the FP32-pair positions
+  return 2 * align_up((size_t)(total_elements > 0 ? total_elements : 1) * sizeof(float), 256) + 512 +
+         2 * align_up((size_t)n * sizeof(float4), 256);
 }
 
 extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t *species, int64_t n,
@@ -1179,7 +1207,7 @@ extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t
              "tb_build_hamiltonian: null pointer");
   TB_REQUIRE(total_elements == 0 || (col && val), "tb_build_hamiltonian: col and val are required");
   TB_REQUIRE(precision == TB_F32 || precision == TB_F64, "tb_build_hamiltonian: bad precision");
-  if (workspace_bytes < tb_build_hamiltonian_workspace_size(total_elements))
+  if (workspace_bytes < tb_build_hamiltonian_workspace_size(n, total_elements))
     return fail(TB_ERR_WORKSPACE, "tb_build_hamiltonian: workspace too small");
   Box B;
   tb_status s = make_box(box, pbc, rcut, &B);
@@ -1189,6 +1217,7 @@ extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t
   float *y0 = cv.take<float>(total_elements > 0 ? total_elements : 1);
   float *y1 = cv.take<float>(total_elements > 0 ? total_elements : 1);
   int *flags = cv.take<int>(4);
+  float4 *ph = cv.take<float4>(n), *pl = cv.take<float4>(n);
   TB_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
   const int64_t n_slices = (n + 31) / 32;
   if (g_mlp_variant == 1) {
@@ -1197,9 +1226,11 @@ extern "C" tb_status tb_build_hamiltonian(const double *positions, const int32_t
                                                       col, cnt, cmix, v, mean, inv_std,
                                                       static_cast<const bf16 *>(w_bf16), params, y0, y1);
   } else {
+    pos_pair_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(positions, n, ph, pl);
+    TB_CHECK_LAUNCH();
     const int grid = grid_cap(n_slices, 4);
     mlp_hamiltonian_tc_kernel<<<grid, kThreads, kTcSmemBytes, st>>>(
-        positions, species, n, n_slices, B, (float)rcut, slice_ptr, col, cnt, cmix, v, mean, inv_std,
+        ph, pl, species, n, n_slices, box_pair(B), (float)rcut, slice_ptr, col, cnt, cmix, v, mean, inv_std,
         static_cast<const bf16 *>(w_bf16), params, y0, y1, flags);
   }
   TB_CHECK_LAUNCH();

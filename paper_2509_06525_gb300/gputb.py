@@ -95,7 +95,7 @@ SIGNATURES = {
     "tb_adamw_step": (_c_i32, [_c_vp, _c_vp, _c_vp, _c_vp, _c_i64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_vp,
                                _c_vp]),
     "tb_mlp_pack_weights": (_c_i32, [_c_vp, _c_vp, _c_vp]),
-    "tb_build_hamiltonian_workspace_size": (_c_sz, [_c_i64]),
+    "tb_build_hamiltonian_workspace_size": (_c_sz, [_c_i64, _c_i64]),
     "tb_build_hamiltonian_teacher_workspace_size": (_c_sz, [_c_i64, _c_i32]),
     "tb_build_hamiltonian": (_c_i32, [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp, _c_dbl, _c_vp, _c_vp, _c_vp, _c_i64,
                                       _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_i32, _c_vp, _c_vp, _c_vp,
@@ -133,7 +133,7 @@ class GputbError(RuntimeError):
 _lib: Optional[ctypes.CDLL] = None
 
 
-ABI_VERSION = 8   # GPUTB_ABI_VERSION of include/gputb.h
+ABI_VERSION = 9   # GPUTB_ABI_VERSION of include/gputb.h
 
 
 def lib() -> ctypes.CDLL:
@@ -835,7 +835,7 @@ def build_hamiltonian(positions, species, box, pbc, rcut, nb: Neighbors, model: 
     b, p, bptr, pptr = _host_box(box, pbc)
     val = torch.empty(max(nb.total, 1), dtype=dtype, device=dev)
     diag = torch.empty(nb.n, dtype=dtype, device=dev) if with_diag else None
-    ws = _workspace(L.tb_build_hamiltonian_workspace_size(nb.total), dev)
+    ws = _workspace(L.tb_build_hamiltonian_workspace_size(nb.n, nb.total), dev)
     st = L.tb_build_hamiltonian(_ptr(positions), _ptr(species), nb.n, bptr, pptr, float(rcut), _ptr(nb.slice_ptr),
                                 _ptr(nb.col), _ptr(nb.cnt), nb.total, _ptr(model.cmix), _ptr(v), _ptr(model.mean),
                                 _ptr(model.inv_std), _ptr(model.wb), _ptr(model.p), _ptr(model.eps0),

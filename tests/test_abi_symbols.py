@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_binding_signatures_cover_header(libpath):
     from paper_2509_06525_gb300 import gputb
     assert sorted(gputb.SIGNATURES) == declared_symbols()
-    assert gputb.lib().tb_abi_version() == gputb.ABI_VERSION == 8
+    assert gputb.lib().tb_abi_version() == gputb.ABI_VERSION == 9
 
 
 def test_workspace_query_needs_no_gpu_for_invalid_sizes(libpath):
