@@ -234,3 +234,22 @@ def test_neighbors_full_size_sampled_rows(g):
         got = nb.col[torch.tensor(pos_e, device="cuda")].cpu().numpy()
         np.testing.assert_array_equal(got, ref)
     assert int(nb.cnt.max()) <= 16
+
+
+@pytest.mark.parametrize("name,params", [("prim800", synth.teacher_graphene()),
+                                         ("junction", synth.teacher_hbn_graphene())])
+def test_teacher_fp32_symmetric_bit_for_bit(g, name, params):
+    """The FP32 teacher forms bond lengths from FP32-pair positions; every
+    step is sign-symmetric, so H_ij and H_ji agree bit for bit, across the
+    periodic seams of the triclinic primitive sheet too."""
+    s = STRUCTS[name]()
+    pos, spc = _dev(s)
+    nb = g.build_neighbors(pos, s.box, s.pbc, params.rcut, r_count=params.r_count)
+    H = g.build_hamiltonian_teacher(pos, spc, s.box, s.pbc, nb, params, dtype=torch.float32)
+    indptr, idx, t, eps = _oracle_teacher(s, params)
+    v = _sell_values(H, nb)
+    rows = np.repeat(np.arange(s.n), np.diff(indptr))
+    for e in range(len(idx)):
+        i, j = rows[e], idx[e]
+        back = indptr[j] + int(np.searchsorted(idx[indptr[j]:indptr[j + 1]], i))
+        assert idx[back] == i and v[e] == v[back], (i, j)
