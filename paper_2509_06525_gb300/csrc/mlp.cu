@@ -991,6 +991,7 @@ __global__ void __launch_bounds__(kThreads) mlp_hamiltonian_tc_kernel(
 }
 
 // val = (y0(i->j) + y0(j->i)) / 2, diag = eps0[Z_i] + sum_j y1(i->j)
+constexpr int kAsmW = 16;   // rows of slices at most this wide search their mirrors together
 template <typename valT>
 __global__ void learned_assemble_kernel(int64_t n, int64_t n_slices, const int64_t *__restrict__ slice_ptr,
                                         const int32_t *__restrict__ col, const int32_t *__restrict__ cnt,
@@ -1004,6 +1005,57 @@ __global__ void learned_assemble_kernel(int64_t n, int64_t n_slices, const int64
   const int w = static_cast<int>((slice_ptr[k + 1] - slice_ptr[k]) >> 5);
   const int m = i < n ? cnt[i] : 0;
   double eps = i < n ? (double)eps0[min(max(species[i], 0), 2)] : 0.0;
+  if (w <= kAsmW) {
+    // the row's mirror searches advance together, one level per round, so
+    // that their dependent loads overlap (same results as one at a time)
+    int32_t jj[kAsmW];
+    int64_t f0[kAsmW];
+    int lo[kAsmW], hi[kAsmW], found[kAsmW];
+#pragma unroll
+    for (int s = 0; s < kAsmW; ++s) {
+      found[s] = -1;
+      lo[s] = 0;
+      hi[s] = -1;
+      if (s < m) {
+        jj[s] = col[e0 + 32 * s];
+        f0[s] = slice_ptr[jj[s] >> 5] + (jj[s] & 31);
+        hi[s] = cnt[jj[s]] - 1;
+      }
+    }
+    for (int round = 0; round < 32; ++round) {
+      bool active = false;
+#pragma unroll
+      for (int s = 0; s < kAsmW; ++s) {
+        if (s < m && found[s] < 0 && lo[s] <= hi[s]) {
+          const int mid = (lo[s] + hi[s]) >> 1;
+          const int32_t cj = col[f0[s] + 32 * mid];
+          if (cj == i) found[s] = mid;
+          else if (cj < i) lo[s] = mid + 1;
+          else hi[s] = mid - 1;
+          active = true;
+        }
+      }
+      if (!active) break;
+    }
+#pragma unroll
+    for (int s = 0; s < kAsmW; ++s) {
+      if (s >= w) break;
+      const int64_t e = e0 + 32 * s;
+      double h = 0.0;
+      if (s < m) {
+        if (found[s] < 0) {
+          atomicOr(flags, 1);
+          h = y0[e];
+        } else {
+          h = 0.5 * ((double)y0[e] + (double)y0[f0[s] + 32 * found[s]]);
+        }
+        eps += (double)y1[e];
+      }
+      val[e] = static_cast<valT>(h);
+    }
+    if (i < n && diag) diag[i] = static_cast<valT>(eps);
+    return;
+  }
   for (int s = 0; s < w; ++s) {
     const int64_t e = e0 + 32 * s;
     double h = 0.0;
