@@ -74,7 +74,21 @@ __global__ void gershgorin_kernel(int64_t n, const int64_t *__restrict__ sp, con
     const int64_t sb = sp[i >> 5];
     const int w = static_cast<int>((sp[(i >> 5) + 1] - sb) >> 5);
     double r = 0.0;
-    for (int s = 0; s < w; ++s) r += fabs((double)val[sb + (i & 31) + 32 * s]);
+    if constexpr (sizeof(valT) == 4) {
+      // FP32 values: the row sum as an FP32 pair (TwoSum per term; about 47
+      // bits), one conversion to FP64 per row instead of one per element
+      float rh = 0.0f, rl = 0.0f;
+      for (int s = 0; s < w; ++s) {
+        const float a = fabsf(val[sb + (i & 31) + 32 * s]);
+        const float t = rh + a;
+        const float bb = t - rh;
+        rl += (rh - (t - bb)) + (a - bb);
+        rh = t;
+      }
+      r = (double)rh + (double)rl;
+    } else {
+      for (int s = 0; s < w; ++s) r += fabs((double)val[sb + (i & 31) + 32 * s]);
+    }
     const double d = diag ? (double)diag[i] : 0.0;
     lo = fmin(lo, d - r);
     hi = fmax(hi, d + r);
